@@ -1,0 +1,358 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the SD residual on the Taylor-Green vortex (Re = 1600,
+Ma = 0.1, Pr = 0.71, gamma = 1.4, periodic [0, 2 pi]^3, 48^3 hexahedra at p = 4, i.e.
+240^3 solution points and 5 conserved variables), compact scheme, FP32 residual with FP64
+Runge-Kutta accumulation.
+
+One step = one SSPRK(5,4) time step: five residual evaluations (trace, gradient and
+flux/divergence kernels) plus the FP64 stage updates, on a state that is already
+resident in HBM; the kinetic-energy/enstrophy diagnostics run once per timed window
+(their cadence in the run is every 0.1 time units, ~200 steps, so this over-counts them).
+value = DOF-updates/s = 5 * (solution points) / (seconds per step), summed over ranks.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle (the plain numpy definition) on the host
+cores, each step one SSPRK(5,4) step of a bounded sample of the same workload.
+Under torchrun every rank runs an independent copy of the workload (weak scaling;
+the residual has no data-path collective across independent problems).
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_2608_09615_b300 import inputs  # noqa: E402
+
+METRIC = "SD residual DOF-updates/s (FP32 vs FP64) and % HBM roofline, TGV Re=1600, 1 B300"
+UNIT = "DOF-updates/s"
+NE, P = (48, 48, 48), 4
+DT = 5e-4            # SSPRK(5,4) step; acoustic CFL ~0.4 at 48^3 p4, Ma = 0.1
+STAGES = 5
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            mp = json.load(f)
+        return float(mp["hbm_gbs"]), float(mp.get("sm_max_mhz", 2032.0)), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6400.0, 2032.0, "fallback"
+
+
+def residual_flops_per_element(n, nv=5, ng=9, dim=3):
+    """Algorithmic FP32 flops of one NS residual per element (FMA = 2 flops), by the
+    operation counts of the method's steps: one 1D sweep of length n costs 2n - 1 flops;
+    per element: own face traces, v^S (D sweep + two corrections), solution and 9 gradient
+    components at the interior flux points, the flux there (~85 flops), each interface
+    once (own interface gradient + Roe ~150 + viscous ~60 + averages), the M divergence;
+    plus the gradient pass (traces, v^S, interface gradients)."""
+    npnt, nq, nf = n ** dim, n ** (dim - 1), 2 * dim
+    sw = 2 * n - 1
+    trace = nf * nv * nq * sw
+    vs = nv * dim * npnt * (sw + 4)
+    interior = dim * (n - 1) * nq * ((nv + ng) * sw + 85)
+    faces = dim * nq * (ng * (sw + 2) + 235)
+    div = dim * nv * npnt * (2 * (n + 1) - 1 + 2)
+    flux_kernel = trace + vs + interior + faces + div
+    grad_kernel = trace + vs + nf * ng * nq * (sw + 2)
+    return flux_kernel, grad_kernel
+
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, val in zip(names, parts[5:9]):
+                    if val.lower() in ("active", "1", "yes"):
+                        reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_threads():
+    try:
+        from threadpoolctl import threadpool_info
+        info = threadpool_info()
+        if info:
+            return max(int(i.get("num_threads", 1)) for i in info)
+    except Exception:
+        pass
+    return 1
+
+
+def oracle_step_sample(sample_ne, steps, warmup):
+    """SSPRK(5,4) steps of the FP64 oracle on a sample grid of the same workload."""
+    from oracle.grid import Grid
+    from oracle.physics import NavierStokes, NSParams
+    from oracle.residual import residual
+    from oracle.timestep import ssprk54_step
+    g = Grid(3, sample_ne, (0.0,) * 3, (2 * math.pi,) * 3, P)
+    phys = NavierStokes(NSParams())
+    U = inputs.tgv_3d(sample_ne, P, perturb_seed=0)
+    R = lambda V: residual(V, g, "compact", phys)  # noqa: E731
+    for _ in range(warmup):
+        U = ssprk54_step(R, U, DT)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        U = ssprk54_step(R, U, DT)
+    dt = (time.perf_counter() - t0) / max(steps, 1)
+    npts = int(np.prod(sample_ne)) * (P + 1) ** 3
+    return STAGES * npts / dt, dt, npts
+
+
+def run_reference(args, world):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    sample = (8, 8, 8)
+    value, sec, npts = oracle_step_sample(sample, args.steps, args.warmup)
+    cores = cpu_threads()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": "TGV Re=1600 Ma=0.1, 48^3 hex p=4 (240^3 DOF), compact, SSPRK(5,4)",
+                   "sample": "%dx%dx%d elements p=4 (%d DOF) per step" % (sample + (npts,)),
+                   "parallelism": "none (host cores)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": "one SSPRK(5,4) step of the FP64 numpy oracle on a %dx%dx%d p=4 "
+                                   "TGV sub-grid per step" % sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--scheme", default="compact", choices=["compact", "br1"])
+    ap.add_argument("--ne", type=int, default=NE[0])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample", type=int, default=16, help="CPU baseline sample grid edge")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        run_reference(args, world)
+        return
+
+    import torch
+    import paper_2608_09615_b300 as sd
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    ne = (args.ne,) * 3
+    lo, hi = (0.0,) * 3, (2 * math.pi,) * 3
+    phys = sd.Physics(kind="ns")
+    ctx = sd.SD(3, ne, lo, hi, P, args.scheme, phys, "f32")
+    npts = int(np.prod(ne)) * (P + 1) ** 3
+    U0 = inputs.tgv_3d(ne, P, perturb_seed=rank)
+    U64 = torch.from_numpy(U0).cuda()
+    stream = torch.cuda.current_stream()
+    t = 0.0
+    for _ in range(args.warmup):
+        ctx.rk_step(U64, t, DT, "ssprk54")
+        t += DT
+    ctx.diagnostics(U64, t)
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    ctx.profile(True)
+    l0 = ctx.launch_count()
+    barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    diag = ctx.diagnostics(U64, t)
+    for _ in range(args.steps):
+        ctx.rk_step(U64, t, DT, "ssprk54")
+        t += DT
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    launches = ctx.launch_count() - l0
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    if dist is not None:
+        tt = torch.tensor([ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    value = world * STAGES * npts / (ms * 1e-3)
+    final = ctx.diagnostics(U64, t, raise_nonfinite=False)
+
+    # roofline of the dominant kernel (flux/divergence), from the live CUDA events
+    hbm, smax, peak_kind = peaks()
+    flux_ms, flux_n = prof["flux_div"]
+    grad_ms, grad_n = prof["grad"]
+    tr_ms, tr_n = prof["trace"]
+    ot_ms, ot_n = prof["other"]
+    f_flux, f_grad = residual_flops_per_element(P + 1)
+    nelem = int(np.prod(ne))
+    flux_avg_ms = flux_ms / max(flux_n, 1)
+    fp32_peak = 148 * 128 * 2 * smax * 1e6 / 1e12      # TFLOP/s at the maximum SM clock
+    achieved = f_flux * nelem / (flux_avg_ms * 1e-3) / 1e12
+    alg_bytes_res = 2 * 5 * npts * 4                    # read U, write R (FP32)
+    res_ms = (flux_ms + grad_ms + tr_ms) / max(flux_n, 1)
+
+    # standalone residual rates, FP32 and FP64
+    Ug32 = U64.float()
+    R32 = torch.empty_like(Ug32)
+    for _ in range(3):
+        ctx.residual(Ug32, R32)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    nrep = max(5, args.steps)
+    e0.record(stream)
+    for _ in range(nrep):
+        ctx.residual(Ug32, R32)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    res32_ms = e0.elapsed_time(e1) / nrep
+
+    # end to end through the host-buffer C-ABI call: pinned FP32 U in, R out
+    Uh = Ug32.cpu().pin_memory()
+    Rh = torch.empty_like(Uh).pin_memory()
+    for _ in range(2):
+        ctx.residual_host(Uh, Rh)
+    nrep_e = max(3, args.steps // 2)
+    t0 = time.perf_counter()
+    for _ in range(nrep_e):
+        ctx.residual_host(Uh, Rh)
+    e2e_s = (time.perf_counter() - t0) / nrep_e
+    ctx.close()
+    del Ug32, R32
+
+    ctx64 = sd.SD(3, ne, lo, hi, P, args.scheme, phys, "f64")
+    R64 = torch.empty_like(U64)
+    for _ in range(2):
+        ctx64.residual(U64, R64)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    nrep64 = 3
+    for _ in range(nrep64):
+        ctx64.residual(U64, R64)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    res64_ms = e0.elapsed_time(e1) / nrep64
+    ctx64.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        s = args.cpu_sample
+        v, sec, n_s = oracle_step_sample((s, s, s), 1, 0)
+        cpu = {"value": v, "unit": UNIT, "cores": cpu_threads(), "kind": "oracle",
+               "sample": "one SSPRK(5,4) step (5 residuals) of the FP64 numpy oracle on a "
+                         "%dx%dx%d p=4 TGV sub-grid (%d DOF), %.1f s" % (s, s, s, n_s, sec)}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "TGV Re=1600 Ma=0.1 Pr=0.71, %dx%dx%d hex p=4 (%d DOF, 5 vars), "
+                                   "%s scheme, Roe + Sutherland, FP32 residual, FP64 SSPRK(5,4), "
+                                   "dt=%g" % (ne + (npts, args.scheme, DT)),
+                       "step": "one SSPRK(5,4) step = 5 residuals + FP64 stage updates; "
+                               "diagnostics once per timed window",
+                       "l2": "inputs larger than L2 (FP32 state %.0f MB, FP64 state %.0f MB)"
+                             % (5 * npts * 4 / 1e6, 5 * npts * 8 / 1e6),
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "roofline": {"bound": "alu", "kernel": "k_flux_div",
+                         "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                         "frac": achieved / fp32_peak, "traffic": None,
+                         "peak_source": "FP32 CUDA-core peak 148 SM x 128 lanes x 2 x %.0f MHz "
+                                        "(derived)" % smax,
+                         "avg_launch_ms": flux_avg_ms,
+                         "hbm_frac_of_%s" % peak_kind:
+                             alg_bytes_res / (res_ms * 1e-3) / 1e9 / hbm,
+                         "hbm_peak_gbs": hbm},
+            "kernels_ms": {"trace": tr_ms / max(tr_n, 1), "grad": grad_ms / max(grad_n, 1),
+                           "flux_div": flux_avg_ms, "rk_and_other_per_launch": ot_ms / max(ot_n, 1),
+                           "launches": {"trace": tr_n, "grad": grad_n, "flux_div": flux_n,
+                                        "other": ot_n}},
+            "residual_dof_per_s": {"f32": npts / (res32_ms * 1e-3), "f64": npts / (res64_ms * 1e-3),
+                                   "f32_ms": res32_ms, "f64_ms": res64_ms},
+            "e2e": {"value": npts / e2e_s, "unit": UNIT, "call": "sd_residual_host (FP32)",
+                    "h2d_bytes_per_step": 5 * npts * 4, "d2h_bytes_per_step": 5 * npts * 4},
+            "gpu_launches": launches,
+            "clocks": clk,
+            "diagnostics": {"ke_over_vol": diag["ke"] / diag["volume"],
+                            "enstrophy_over_vol": diag["enstrophy"] / diag["volume"],
+                            "final_nonfinite": final["nonfinite"]},
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,159 @@
+/*
+ * sd.h -- C ABI of the B300 Spectral Difference (SD) residual library.
+ *
+ * The library evaluates the SD semi-discrete residual dU/dt of Lodato & Tonicello,
+ * "A novel compact scheme for second-order fluxes applied to the Spectral Difference
+ * method", on periodic, uniform, tensor-product Cartesian grids (1D segments or 3D
+ * hexahedra), with the viscous terms built from the auxiliary gradient v = grad u either
+ * by the standard BR1 scheme (Sec. 2.1) or by the compact one-sided scheme (Secs. 2.2,
+ * 2.3). Physics: linear diffusion (Sec. 3 / 4.1), the porous medium equation (Sec. 4.3,
+ * Eq. pme) and the compressible Navier-Stokes equations (Sec. 4.4).
+ *
+ * Data layout (every state / residual array, device or host):
+ *     U[var][E_{dim-1}]...[E_0][n]...[n]
+ * variable-major, then the element grid with x fastest, then the n^dim solution points
+ * of each element with the x point index fastest; n = p + 1. In 3D this is
+ * U[var][ez][ey][ex][k][j][i]. The points are the n Gauss-Legendre points of each
+ * element (Sec. 2). NS variables: rho, rho u, rho v, rho w, rho E. Scalar: u.
+ *
+ * Ownership: the caller owns every state/residual buffer it passes. The context owns
+ * all scratch (face-trace buffers, Runge-Kutta registers, staging buffers); everything
+ * is allocated in sd_init and freed in sd_destroy -- no call allocates afterwards.
+ * Errors: every call returns an sd_status; nothing throws across the ABI. On error the
+ * outputs are unspecified and sd_last_error() describes the failure (thread-local).
+ * Streams: all device work is enqueued on the context's stream (sd_init / sd_set_stream).
+ * Calls returning SD_OK have only enqueued work unless stated otherwise.
+ */
+#ifndef SD_H
+#define SD_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SD_OK = 0,
+    SD_EINVAL = 1,          /* bad argument (null pointer, size, enum, aliasing)      */
+    SD_ENOMEM = 2,          /* device or host allocation failed (sd_init only)        */
+    SD_ECUDA = 3,           /* a CUDA runtime call failed                             */
+    SD_EUNSUPPORTED = 4,    /* valid but not supported here (p, dim, shared memory)   */
+    SD_ENONFINITE = 5,      /* sd_diagnostics found a NaN/Inf in the state            */
+    SD_ETIMEOUT = 6         /* reserved: a bounded device-side wait gave up           */
+} sd_status;
+
+typedef enum { SD_BR1 = 0, SD_COMPACT = 1 } sd_scheme;            /* Secs. 2.1 / 2.2-2.3 */
+typedef enum { SD_HEAT = 0, SD_PME = 1, SD_NS = 2 } sd_physics_kind;
+typedef enum { SD_ROE = 0, SD_RUSANOV = 1 } sd_riemann;           /* NS inviscid flux    */
+typedef enum { SD_F64 = 0, SD_F32 = 1 } sd_precision;            /* residual arithmetic */
+typedef enum { SD_RK4 = 0, SD_SSPRK54 = 1, SD_LSRK54 = 2 } sd_rk;
+
+/* Periodic uniform Cartesian grid: dim in {1, 3}; ne[d] elements along direction d
+ * (x first; unused entries ignored); the domain is prod_d [lo[d], hi[d]). */
+typedef struct {
+    int dim;
+    int ne[3];
+    double lo[3];
+    double hi[3];
+} sd_mesh;
+
+/* Physics parameters.
+ *  SD_HEAT: du/dt = nu lap u                                  (uses nu)
+ *  SD_PME : du/dt = div(m |u|^(m-1) grad u), the factor taken from the solution at the
+ *           flux points (Sec. 4.3)                            (uses m_pme)
+ *  SD_NS  : Sec. 4.4. mu0 = rho0 u0 L / Re, p0 = rho0 (u0/Ma)^2 / gamma,
+ *           e0 = p0/((gamma-1) rho0); kappa grad T = (mu gamma/Pr) grad e; lambda = 0;
+ *           sutherland != 0: mu = mu0 (e/e0)^(3/2) (1 + suth_s)/(e/e0 + suth_s),
+ *           suth_s = S/T0 (0.368 for S = 110.4 K, T0 = 300 K); otherwise mu = mu0.
+ *           Interfaces: Roe (Harten fix on the acoustic waves, delta = harten * c_Roe)
+ *           or Rusanov, minus the viscous flux of the averaged state and gradient. */
+typedef struct {
+    sd_physics_kind kind;
+    double nu;
+    double m_pme;
+    double gamma, Pr, Re, Ma, rho0, u0, L;
+    int sutherland;
+    double suth_s;
+    sd_riemann riemann;
+    double harten;
+} sd_physics;
+
+/* Volume diagnostics (Sec. 4.4), FP64, Gauss quadrature over every element.
+ * NS: ke = 1/2 int u.u, ke_rho = 1/2 int rho u.u, enstrophy = int |curl u|^2 (velocity
+ * gradient from the conservative auxiliary gradient at the solution points), mass,
+ * mom[3], energy = int rho E. Scalar: mass = int u, l2sq = int u^2. volume = |Omega|.
+ * nonfinite != 0 when any state value is NaN or Inf. */
+typedef struct {
+    double t;
+    double ke, ke_rho, enstrophy;
+    double mass, mom[3], energy;
+    double l2sq, volume;
+    int nonfinite;
+} sd_diag;
+
+typedef struct sd_ctx sd_ctx;
+
+/* Create a context for one grid, polynomial degree p, scheme, physics and residual
+ * precision; all scratch is allocated here on the current CUDA device.
+ *   p: 1..8 (n = p + 1 points per direction). dim: 1 or 3 (NS: 3 only).
+ *   stream: a cudaStream_t (NULL = legacy default stream).
+ * Returns SD_EINVAL / SD_EUNSUPPORTED / SD_ENOMEM / SD_ECUDA, else SD_OK and *out. */
+sd_status sd_init(const sd_mesh* mesh, int p, sd_scheme scheme, const sd_physics* phys,
+                  sd_precision prec, void* stream, sd_ctx** out);
+
+void sd_destroy(sd_ctx* ctx);
+sd_status sd_set_stream(sd_ctx* ctx, void* stream);
+
+/* Number of values in one state array: nvar * prod(ne) * n^dim. */
+size_t sd_state_size(const sd_ctx* ctx);
+int sd_nvar(const sd_ctx* ctx);
+
+/* 1D solution points xi_i in [-1, 1] (n values) and Gauss weights (n values), as the
+ * library computed them (Newton iteration on the Legendre recurrence). Host pointers. */
+sd_status sd_points(const sd_ctx* ctx, double* xi, double* w);
+
+/* R = dU/dt (Sec. 2.3 steps 1-5). U, R: device arrays in the layout above, of the
+ * context's precision (float for SD_F32, double for SD_F64), sd_state_size values each;
+ * they must not overlap. Asynchronous on the context stream. */
+sd_status sd_residual(sd_ctx* ctx, const void* U, void* R);
+
+/* The same residual through host memory: copies U_host to the device, evaluates R and
+ * copies it back into R_host, on the context stream, and synchronises the stream before
+ * returning. U_host / R_host: host arrays of the context's precision (pinned memory
+ * gives full copy bandwidth; pageable memory works). */
+sd_status sd_residual_host(sd_ctx* ctx, const void* U_host, void* R_host);
+
+/* One explicit time step of the FP64 state U64 (device, sd_state_size doubles), in
+ * place: U64 <- U64 + dt-integral of R. Stage arithmetic and the Runge-Kutta registers
+ * are FP64 always; with SD_F32 the residual of each stage is evaluated in FP32 on an FP32
+ * copy of the stage state. t is the time at the start of the step (the residual is
+ * autonomous; t is recorded only). Asynchronous on the context stream. */
+sd_status sd_rk_step(sd_ctx* ctx, double* U64, double t, double dt, sd_rk rk);
+
+/* FP64 volume diagnostics of the FP64 device state U64 at time t. Synchronises the
+ * context stream and writes *out (host). Returns SD_ENONFINITE (with *out filled)
+ * when the state holds a NaN or Inf. */
+sd_status sd_diagnostics(sd_ctx* ctx, const double* U64, double t, sd_diag* out);
+
+/* Profiling (CUDA events on the context stream). While enabled, every kernel launch of
+ * the context is bracketed by two events; sd_profile_read synchronises the stream and
+ * returns, per kernel class (SD_K_TRACE, SD_K_GRAD, SD_K_FLUX, SD_K_OTHER), the summed
+ * device time in ms and the launch count since the last read, then resets them.
+ * Enabling creates the events (no device memory); disabling destroys them. */
+enum { SD_K_TRACE = 0, SD_K_GRAD = 1, SD_K_FLUX = 2, SD_K_OTHER = 3, SD_K_COUNT = 4 };
+sd_status sd_profile_enable(sd_ctx* ctx, int on);
+sd_status sd_profile_read(sd_ctx* ctx, double* ms, long long* launches);
+
+/* Total number of kernels the context has launched since sd_init. */
+long long sd_launch_count(const sd_ctx* ctx);
+
+const char* sd_status_str(sd_status s);
+/* Text of the last error raised on the calling thread ("" if none). */
+const char* sd_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SD_H */

@@ -1,0 +1,269 @@
+"""Python binding of the B300 Spectral Difference residual library (include/sd.h).
+
+Argument marshalling only: every step of the residual, the Runge-Kutta stages and the
+diagnostics run in the CUDA library libsd.so that sits next to this file (built by
+paper_2608_09615_b300.build). The library is loaded on first use; if it is missing the
+call raises -- there is no CPU fallback.
+
+Low-level functions carry the C names (sd_init, sd_residual, sd_residual_host,
+sd_rk_step, sd_diagnostics, sd_destroy); the SD class wraps one context.
+Tensors are torch tensors: device buffers for sd_residual / sd_rk_step / sd_diagnostics,
+host (ideally pinned) buffers for sd_residual_host, all contiguous and laid out as
+U[var][E_{dim-1}]...[E_0][n]...[n].
+"""
+import ctypes
+import os
+from dataclasses import dataclass, field
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libsd.so")
+
+SD_OK, SD_EINVAL, SD_ENOMEM, SD_ECUDA, SD_EUNSUPPORTED, SD_ENONFINITE, SD_ETIMEOUT = range(7)
+SCHEMES = {"br1": 0, "compact": 1}
+KINDS = {"heat": 0, "pme": 1, "ns": 2}
+RIEMANN = {"roe": 0, "rusanov": 1}
+PRECISIONS = {"f64": 0, "f32": 1}
+RK = {"rk4": 0, "ssprk54": 1, "lsrk54": 2}
+
+
+class SDError(RuntimeError):
+    def __init__(self, status, where, text):
+        super().__init__("%s: status %d (%s)%s" % (where, status, text[0], (": " + text[1]) if text[1] else ""))
+        self.status = status
+
+
+class _Mesh(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("ne", ctypes.c_int * 3),
+                ("lo", ctypes.c_double * 3), ("hi", ctypes.c_double * 3)]
+
+
+class _Physics(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("nu", ctypes.c_double), ("m_pme", ctypes.c_double),
+                ("gamma", ctypes.c_double), ("Pr", ctypes.c_double), ("Re", ctypes.c_double),
+                ("Ma", ctypes.c_double), ("rho0", ctypes.c_double), ("u0", ctypes.c_double),
+                ("L", ctypes.c_double), ("sutherland", ctypes.c_int), ("suth_s", ctypes.c_double),
+                ("riemann", ctypes.c_int), ("harten", ctypes.c_double)]
+
+
+class _Diag(ctypes.Structure):
+    _fields_ = [("t", ctypes.c_double), ("ke", ctypes.c_double), ("ke_rho", ctypes.c_double),
+                ("enstrophy", ctypes.c_double), ("mass", ctypes.c_double),
+                ("mom", ctypes.c_double * 3), ("energy", ctypes.c_double),
+                ("l2sq", ctypes.c_double), ("volume", ctypes.c_double), ("nonfinite", ctypes.c_int)]
+
+
+EXPORTS = ("sd_init", "sd_destroy", "sd_set_stream", "sd_state_size", "sd_nvar", "sd_points",
+           "sd_residual", "sd_residual_host", "sd_rk_step", "sd_diagnostics", "sd_status_str",
+           "sd_last_error", "sd_profile_enable", "sd_profile_read", "sd_launch_count")
+KERNEL_CLASSES = ("trace", "grad", "flux_div", "other")
+
+_lib_handle = None
+
+
+def load_library(path=LIB_PATH):
+    """Load libsd.so (raises if it is missing: build it with paper_2608_09615_b300.build)."""
+    global _lib_handle
+    if _lib_handle is not None:
+        return _lib_handle
+    if not os.path.exists(path):
+        raise RuntimeError("CUDA library %s is missing; run `python -m paper_2608_09615_b300.build`"
+                           % path)
+    lib = ctypes.CDLL(path)
+    P, I, D, S = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_size_t
+    lib.sd_init.argtypes = [ctypes.POINTER(_Mesh), I, I, ctypes.POINTER(_Physics), I, P,
+                            ctypes.POINTER(P)]
+    lib.sd_init.restype = I
+    lib.sd_destroy.argtypes = [P]
+    lib.sd_destroy.restype = None
+    lib.sd_set_stream.argtypes = [P, P]
+    lib.sd_set_stream.restype = I
+    lib.sd_state_size.argtypes = [P]
+    lib.sd_state_size.restype = S
+    lib.sd_nvar.argtypes = [P]
+    lib.sd_nvar.restype = I
+    lib.sd_points.argtypes = [P, P, P]
+    lib.sd_points.restype = I
+    lib.sd_residual.argtypes = [P, P, P]
+    lib.sd_residual.restype = I
+    lib.sd_residual_host.argtypes = [P, P, P]
+    lib.sd_residual_host.restype = I
+    lib.sd_rk_step.argtypes = [P, P, D, D, I]
+    lib.sd_rk_step.restype = I
+    lib.sd_diagnostics.argtypes = [P, P, D, ctypes.POINTER(_Diag)]
+    lib.sd_diagnostics.restype = I
+    lib.sd_status_str.argtypes = [I]
+    lib.sd_status_str.restype = ctypes.c_char_p
+    lib.sd_last_error.argtypes = []
+    lib.sd_last_error.restype = ctypes.c_char_p
+    lib.sd_profile_enable.argtypes = [P, I]
+    lib.sd_profile_enable.restype = I
+    lib.sd_profile_read.argtypes = [P, P, P]
+    lib.sd_profile_read.restype = I
+    lib.sd_launch_count.argtypes = [P]
+    lib.sd_launch_count.restype = ctypes.c_longlong
+    _lib_handle = lib
+    return lib
+
+
+def _check(status, where):
+    if status != SD_OK:
+        lib = load_library()
+        raise SDError(status, where, (lib.sd_status_str(status).decode(), lib.sd_last_error().decode()))
+
+
+@dataclass
+class Physics:
+    """sd_physics. kind: "heat", "pme" or "ns"; NS defaults are the Taylor-Green setup."""
+    kind: str = "ns"
+    nu: float = 1.0
+    m_pme: float = 2.0
+    gamma: float = 1.4
+    Pr: float = 0.71
+    Re: float = 1600.0
+    Ma: float = 0.1
+    rho0: float = 1.0
+    u0: float = 1.0
+    L: float = 1.0
+    sutherland: bool = True
+    suth_s: float = 110.4 / 300.0
+    riemann: str = "roe"
+    harten: float = 0.1
+
+    def to_c(self):
+        return _Physics(KINDS[self.kind], self.nu, self.m_pme, self.gamma, self.Pr, self.Re,
+                        self.Ma, self.rho0, self.u0, self.L, int(bool(self.sutherland)),
+                        self.suth_s, RIEMANN[self.riemann], self.harten)
+
+
+def _stream_handle(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def sd_init(dim, ne, lo, hi, p, scheme, physics, precision, stream=None):
+    """Create a context (sd_init). Returns an opaque handle (c_void_p)."""
+    lib = load_library()
+    ne = list(ne) + [1] * (3 - len(ne))
+    lo = list(lo) + [0.0] * (3 - len(lo))
+    hi = list(hi) + [1.0] * (3 - len(hi))
+    m = _Mesh(dim, (ctypes.c_int * 3)(*ne), (ctypes.c_double * 3)(*lo), (ctypes.c_double * 3)(*hi))
+    ph = physics.to_c()
+    out = ctypes.c_void_p()
+    st = lib.sd_init(ctypes.byref(m), int(p), SCHEMES[scheme], ctypes.byref(ph),
+                     PRECISIONS[precision], _stream_handle(stream), ctypes.byref(out))
+    _check(st, "sd_init")
+    return out
+
+
+def sd_destroy(ctx):
+    load_library().sd_destroy(ctx)
+
+
+def _dev_ptr(t, dtype, numel, name):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("%s must be a CUDA tensor" % name)
+    if t.dtype != dtype or not t.is_contiguous() or t.numel() != numel:
+        raise ValueError("%s must be a contiguous %s tensor of %d values" % (name, dtype, numel))
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def sd_residual(ctx, U, R, dtype, numel):
+    _check(load_library().sd_residual(ctx, _dev_ptr(U, dtype, numel, "U"),
+                                      _dev_ptr(R, dtype, numel, "R")), "sd_residual")
+
+
+def sd_residual_host(ctx, U, R, dtype, numel):
+    import torch
+    for t, nm in ((U, "U"), (R, "R")):
+        if not isinstance(t, torch.Tensor) or t.is_cuda or t.dtype != dtype or \
+                not t.is_contiguous() or t.numel() != numel:
+            raise ValueError("%s must be a contiguous host %s tensor of %d values" % (nm, dtype, numel))
+    _check(load_library().sd_residual_host(ctx, ctypes.c_void_p(U.data_ptr()),
+                                           ctypes.c_void_p(R.data_ptr())), "sd_residual_host")
+
+
+def sd_rk_step(ctx, U64, t, dt, rk, numel):
+    import torch
+    _check(load_library().sd_rk_step(ctx, _dev_ptr(U64, torch.float64, numel, "U64"),
+                                     float(t), float(dt), RK[rk]), "sd_rk_step")
+
+
+def sd_diagnostics(ctx, U64, t, numel, raise_nonfinite=True):
+    import torch
+    d = _Diag()
+    st = load_library().sd_diagnostics(ctx, _dev_ptr(U64, torch.float64, numel, "U64"), float(t),
+                                       ctypes.byref(d))
+    if st != SD_ENONFINITE or raise_nonfinite:
+        _check(st, "sd_diagnostics")
+    return dict(t=d.t, ke=d.ke, ke_rho=d.ke_rho, enstrophy=d.enstrophy, mass=d.mass,
+                mom=[d.mom[0], d.mom[1], d.mom[2]], energy=d.energy, l2sq=d.l2sq,
+                volume=d.volume, nonfinite=d.nonfinite)
+
+
+class SD:
+    """One SD residual context (grid, p, scheme, physics, residual precision)."""
+
+    def __init__(self, dim, ne, lo, hi, p, scheme="compact", physics=None, precision="f32",
+                 stream=None):
+        import torch
+        self.physics = physics if physics is not None else Physics()
+        self.dim, self.ne, self.p, self.n = dim, tuple(ne), p, p + 1
+        self.scheme, self.precision = scheme, precision
+        self.dtype = torch.float32 if precision == "f32" else torch.float64
+        self._ctx = sd_init(dim, ne, lo, hi, p, scheme, self.physics, precision, stream)
+        lib = load_library()
+        self.numel = int(lib.sd_state_size(self._ctx))
+        self.nvar = int(lib.sd_nvar(self._ctx))
+        self.shape = (self.nvar,) + tuple(reversed(tuple(ne))) + (self.n,) * dim
+
+    def set_stream(self, stream):
+        _check(load_library().sd_set_stream(self._ctx, _stream_handle(stream)), "sd_set_stream")
+
+    def points(self):
+        xi = (ctypes.c_double * self.n)()
+        w = (ctypes.c_double * self.n)()
+        _check(load_library().sd_points(self._ctx, xi, w), "sd_points")
+        return list(xi), list(w)
+
+    def residual(self, U, R=None):
+        import torch
+        if R is None:
+            R = torch.empty_like(U)
+        sd_residual(self._ctx, U, R, self.dtype, self.numel)
+        return R
+
+    def residual_host(self, U, R):
+        sd_residual_host(self._ctx, U, R, self.dtype, self.numel)
+        return R
+
+    def rk_step(self, U64, t, dt, rk="ssprk54"):
+        sd_rk_step(self._ctx, U64, t, dt, rk, self.numel)
+
+    def diagnostics(self, U64, t=0.0, raise_nonfinite=True):
+        return sd_diagnostics(self._ctx, U64, t, self.numel, raise_nonfinite)
+
+    def profile(self, on=True):
+        _check(load_library().sd_profile_enable(self._ctx, int(bool(on))), "sd_profile_enable")
+
+    def profile_read(self):
+        ms = (ctypes.c_double * 4)()
+        cnt = (ctypes.c_longlong * 4)()
+        _check(load_library().sd_profile_read(self._ctx, ms, cnt), "sd_profile_read")
+        return {k: (ms[i], cnt[i]) for i, k in enumerate(KERNEL_CLASSES)}
+
+    def launch_count(self):
+        return int(load_library().sd_launch_count(self._ctx))
+
+    def close(self):
+        if getattr(self, "_ctx", None) is not None:
+            sd_destroy(self._ctx)
+            self._ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

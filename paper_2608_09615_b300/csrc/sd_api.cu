@@ -1,0 +1,560 @@
+// C ABI of the SD residual library: context life cycle, the 1D operators, the residual
+// entry points, Runge-Kutta steps and FP64 diagnostics. See include/sd.h.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+
+#include "sd_internal.h"
+#include "sd_launch.cuh"
+
+// ------------------------------------------------------------------ error text
+static thread_local char g_err[512] = "";
+
+void sdi_set_error(const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+extern "C" const char* sd_last_error(void) { return g_err; }
+
+extern "C" const char* sd_status_str(sd_status s) {
+    switch (s) {
+        case SD_OK: return "ok";
+        case SD_EINVAL: return "invalid argument";
+        case SD_ENOMEM: return "out of memory";
+        case SD_ECUDA: return "CUDA error";
+        case SD_EUNSUPPORTED: return "unsupported configuration";
+        case SD_ENONFINITE: return "non-finite state";
+        case SD_ETIMEOUT: return "device wait timed out";
+    }
+    return "unknown status";
+}
+
+#define CK(call)                                                                   \
+    do {                                                                           \
+        cudaError_t e_ = (call);                                                   \
+        if (e_ != cudaSuccess) {                                                   \
+            sdi_set_error("%s failed: %s", #call, cudaGetErrorString(e_));         \
+            return SD_ECUDA;                                                       \
+        }                                                                          \
+    } while (0)
+
+// ------------------------------------------------------------------ profiling
+static void prof_fold(sd_ctx* c, int k) {
+    if (c->prof_n[k] == 0) return;
+    cudaEventSynchronize(c->prof_ev[k][2 * (c->prof_n[k] - 1) + 1]);
+    for (int i = 0; i < c->prof_n[k]; ++i) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, c->prof_ev[k][2 * i], c->prof_ev[k][2 * i + 1]) == cudaSuccess)
+            c->prof_ms[k] += ms;
+    }
+    c->prof_count[k] += c->prof_n[k];
+    c->prof_n[k] = 0;
+}
+
+void sdi_prof_begin(sd_ctx* c, int k) {
+    c->launches++;
+    if (!c->prof_on) return;
+    if (c->prof_n[k] == SDI_PROF_CAP) prof_fold(c, k);
+    cudaEventRecord(c->prof_ev[k][2 * c->prof_n[k]], c->stream);
+}
+
+void sdi_prof_end(sd_ctx* c, int k) {
+    if (!c->prof_on) return;
+    cudaEventRecord(c->prof_ev[k][2 * c->prof_n[k] + 1], c->stream);
+    c->prof_n[k]++;
+}
+
+static void prof_destroy(sd_ctx* c) {
+    for (int k = 0; k < SD_K_COUNT; ++k) {
+        if (!c->prof_ev[k]) continue;
+        for (int i = 0; i < 2 * SDI_PROF_CAP; ++i) cudaEventDestroy(c->prof_ev[k][i]);
+        free(c->prof_ev[k]);
+        c->prof_ev[k] = nullptr;
+        c->prof_n[k] = 0;
+    }
+    c->prof_on = 0;
+}
+
+extern "C" sd_status sd_profile_enable(sd_ctx* c, int on) {
+    if (!c) { sdi_set_error("null argument"); return SD_EINVAL; }
+    if (!on) { prof_destroy(c); return SD_OK; }
+    if (c->prof_on) return SD_OK;
+    for (int k = 0; k < SD_K_COUNT; ++k) {
+        c->prof_ev[k] = (cudaEvent_t*)calloc(2 * SDI_PROF_CAP, sizeof(cudaEvent_t));
+        if (!c->prof_ev[k]) { prof_destroy(c); return SD_ENOMEM; }
+        for (int i = 0; i < 2 * SDI_PROF_CAP; ++i)
+            if (cudaEventCreate(&c->prof_ev[k][i]) != cudaSuccess) {
+                prof_destroy(c);
+                sdi_set_error("cudaEventCreate failed");
+                return SD_ECUDA;
+            }
+        c->prof_n[k] = 0;
+        c->prof_ms[k] = 0.0;
+        c->prof_count[k] = 0;
+    }
+    c->prof_on = 1;
+    return SD_OK;
+}
+
+extern "C" sd_status sd_profile_read(sd_ctx* c, double* ms, long long* launches) {
+    if (!c || !ms || !launches) { sdi_set_error("null argument"); return SD_EINVAL; }
+    if (!c->prof_on) { sdi_set_error("profiling is not enabled"); return SD_EINVAL; }
+    for (int k = 0; k < SD_K_COUNT; ++k) {
+        prof_fold(c, k);
+        ms[k] = c->prof_ms[k];
+        launches[k] = c->prof_count[k];
+        c->prof_ms[k] = 0.0;
+        c->prof_count[k] = 0;
+    }
+    return SD_OK;
+}
+
+extern "C" long long sd_launch_count(const sd_ctx* c) { return c ? c->launches : 0; }
+
+// ------------------------------------------------------------------ 1D operators
+// Gauss-Legendre nodes/weights by Newton iteration on the three-term recurrence of P_n.
+static void gauss_legendre(int n, double* x, double* w) {
+    for (int i = 0; i < n; ++i) {
+        double z = cos(M_PI * (i + 0.75) / (n + 0.5));
+        double dp = 1.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = z;
+            for (int k = 2; k <= n; ++k) {
+                const double pk = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+                p0 = p1;
+                p1 = pk;
+            }
+            if (n == 1) { p1 = z; p0 = 1.0; }
+            dp = n * (z * p1 - p0) / (z * z - 1.0);
+            const double dz = p1 / dp;
+            z -= dz;
+            if (fabs(dz) < 1e-16) break;
+        }
+        // recompute the derivative at the converged node for the weight
+        double p0 = 1.0, p1 = z;
+        for (int k = 2; k <= n; ++k) {
+            const double pk = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+            p0 = p1;
+            p1 = pk;
+        }
+        if (n == 1) { p1 = z; p0 = 1.0; }
+        dp = n * (z * p1 - p0) / (z * z - 1.0);
+        x[n - 1 - i] = z;                       // ascending order
+        w[n - 1 - i] = 2.0 / ((1.0 - z * z) * dp * dp);
+    }
+    if (n == 1) { x[0] = 0.0; w[0] = 2.0; }
+}
+
+// l_j(x) on nodes t[0..m)
+static double lagrange(const double* t, int m, int j, double x) {
+    double v = 1.0;
+    for (int k = 0; k < m; ++k)
+        if (k != j) v *= (x - t[k]) / (t[j] - t[k]);
+    return v;
+}
+
+// l_j'(x) = sum_{k != j} 1/(t_j - t_k) prod_{l != j,k} (x - t_l)/(t_j - t_l)
+static double lagrange_d(const double* t, int m, int j, double x) {
+    double s = 0.0;
+    for (int k = 0; k < m; ++k) {
+        if (k == j) continue;
+        double prod = 1.0 / (t[j] - t[k]);
+        for (int l = 0; l < m; ++l)
+            if (l != j && l != k) prod *= (x - t[l]) / (t[j] - t[l]);
+        s += prod;
+    }
+    return s;
+}
+
+static void build_operators(sd_ctx* c) {
+    const int n = c->n;
+    gauss_legendre(n, c->xs, c->ws);
+    c->xf[0] = -1.0;
+    c->xf[n] = 1.0;
+    if (n > 1) {
+        double tmp_w[SD_MAX_N];
+        gauss_legendre(n - 1, c->xf + 1, tmp_w);
+    }
+    for (int f = 0; f <= n; ++f)
+        for (int i = 0; i < n; ++i) c->L[f * n + i] = lagrange(c->xs, n, i, c->xf[f]);
+    for (int i = 0; i < n; ++i)
+        for (int f = 0; f <= n; ++f) c->M[i * (n + 1) + f] = lagrange_d(c->xf, n + 1, f, c->xs[i]);
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) {
+            double s = 0.0;
+            for (int f = 0; f <= n; ++f) s += c->M[i * (n + 1) + f] * c->L[f * n + j];
+            c->D[i * n + j] = s;
+        }
+    double a = 0.0, b = 0.0;
+    for (int i = 0; i < n; ++i) {
+        a += c->L[0 * n + i] * c->M[i * (n + 1) + n];
+        b += c->L[n * n + i] * c->M[i * (n + 1) + 0];
+    }
+    c->alpha = a;
+    c->beta = b;
+}
+
+// ------------------------------------------------------------------ life cycle
+static void free_all(sd_ctx* c) {
+    void* ptrs[] = {c->Tu, c->Tg, c->S, c->K, c->rA, c->rB, c->rC, c->dW,
+                    c->partial, c->dsum, c->hU, c->hR};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    if (c->Tu64 && (void*)c->Tu64 != c->Tu) cudaFree(c->Tu64);
+}
+
+static int ipow_h(int b, int e) {
+    int r = 1;
+    while (e-- > 0) r *= b;
+    return r;
+}
+
+template <typename real, int N, int DIM, int NV>
+static bool smem_ok() {
+    return sdk::smem_ok_impl<real, N, DIM, NV>();
+}
+
+extern "C" sd_status sd_init(const sd_mesh* mesh, int p, sd_scheme scheme, const sd_physics* phys,
+                             sd_precision prec, void* stream, sd_ctx** out) {
+    g_err[0] = 0;
+    if (!mesh || !phys || !out) { sdi_set_error("null argument"); return SD_EINVAL; }
+    *out = nullptr;
+    if (mesh->dim != 1 && mesh->dim != 3) { sdi_set_error("dim must be 1 or 3"); return SD_EUNSUPPORTED; }
+    if (p < 1 || p > SD_MAX_N - 1) { sdi_set_error("p must be in 1..%d", SD_MAX_N - 1); return SD_EUNSUPPORTED; }
+    if (scheme != SD_BR1 && scheme != SD_COMPACT) { sdi_set_error("bad scheme"); return SD_EINVAL; }
+    if (prec != SD_F32 && prec != SD_F64) { sdi_set_error("bad precision"); return SD_EINVAL; }
+    if (phys->kind != SD_HEAT && phys->kind != SD_PME && phys->kind != SD_NS) {
+        sdi_set_error("bad physics kind");
+        return SD_EINVAL;
+    }
+    if (phys->kind == SD_NS && mesh->dim != 3) { sdi_set_error("Navier-Stokes needs dim = 3"); return SD_EUNSUPPORTED; }
+    if (phys->kind == SD_NS) {
+        if (!(phys->gamma > 1.0) || !(phys->Pr > 0.0) || !(phys->Re > 0.0) || !(phys->Ma > 0.0) ||
+            !(phys->rho0 > 0.0) || !(phys->u0 > 0.0) || !(phys->L > 0.0) || phys->harten < 0.0 ||
+            (phys->riemann != SD_ROE && phys->riemann != SD_RUSANOV)) {
+            sdi_set_error("bad Navier-Stokes parameters");
+            return SD_EINVAL;
+        }
+    }
+    if (phys->kind == SD_PME && !(phys->m_pme >= 1.0)) { sdi_set_error("m_pme must be >= 1"); return SD_EINVAL; }
+    long long nelem = 1;
+    for (int d = 0; d < mesh->dim; ++d) {
+        if (mesh->ne[d] < 1) { sdi_set_error("ne[%d] must be >= 1", d); return SD_EINVAL; }
+        if (!(mesh->hi[d] > mesh->lo[d])) { sdi_set_error("hi[%d] must exceed lo[%d]", d, d); return SD_EINVAL; }
+        nelem *= mesh->ne[d];
+    }
+    if (nelem > (1LL << 30)) { sdi_set_error("too many elements"); return SD_EUNSUPPORTED; }
+
+    sd_ctx* c = (sd_ctx*)calloc(1, sizeof(sd_ctx));
+    if (!c) return SD_ENOMEM;
+    c->dim = mesh->dim;
+    for (int d = 0; d < 3; ++d) {
+        c->ne[d] = d < mesh->dim ? mesh->ne[d] : 1;
+        c->lo[d] = d < mesh->dim ? mesh->lo[d] : 0.0;
+        c->hi[d] = d < mesh->dim ? mesh->hi[d] : 1.0;
+        c->h[d] = (c->hi[d] - c->lo[d]) / c->ne[d];
+    }
+    c->nelem = (int)nelem;
+    c->p = p;
+    c->n = p + 1;
+    c->nvar = phys->kind == SD_NS ? 5 : 1;
+    c->ngrad = phys->kind == SD_NS ? 9 : 1;
+    c->scheme = scheme;
+    c->phys = *phys;
+    c->prec = prec;
+    c->stream = (cudaStream_t)stream;
+    c->J = 1.0;
+    for (int d = 0; d < c->dim; ++d) c->J *= c->h[d] / 2.0;
+    build_operators(c);
+    const int np = ipow_h(c->n, c->dim), nq = ipow_h(c->n, c->dim - 1);
+    c->npts = (size_t)c->nelem * np;
+    c->nstate = c->npts * c->nvar;
+    c->ntu = (size_t)c->nelem * 2 * c->dim * c->nvar * nq;
+    c->ntg = (size_t)c->nelem * 2 * c->dim * c->ngrad * nq;
+    c->esize = prec == SD_F32 ? sizeof(float) : sizeof(double);
+
+    // shared memory feasibility of the element-staged kernels
+    {
+        using namespace sdk;
+        const int n = c->n;
+        const size_t per = c->esize;
+        const int NV = c->nvar, DIM = c->dim;
+        const size_t flux = (size_t)(NV * np + 2 * 2 * DIM * NV * nq + NV * DIM * np + NV * (n + 1) * nq);
+        if (flux * per > 227 * 1024 || ((np + 31) / 32) * 32 > 1024) {
+            sdi_set_error("n = %d needs %zu bytes of shared memory per element", n, flux * per);
+            free(c);
+            return SD_EUNSUPPORTED;
+        }
+    }
+    if (cudaGetDevice(&c->device) != cudaSuccess) {
+        sdi_set_error("no CUDA device");
+        free(c);
+        return SD_ECUDA;
+    }
+    const size_t S = c->nstate;
+    bool ok = true;
+    auto alloc = [&](void** p, size_t bytes) {
+        if (!ok) return;
+        if (cudaMalloc(p, std::max<size_t>(bytes, 16)) != cudaSuccess) ok = false;
+    };
+    alloc(&c->Tu, c->ntu * c->esize);
+    alloc(&c->Tg, c->ntg * c->esize);
+    if (prec == SD_F64) c->Tu64 = (double*)c->Tu;
+    else alloc((void**)&c->Tu64, c->ntu * sizeof(double));
+    alloc(&c->S, S * c->esize);
+    alloc(&c->K, S * c->esize);
+    alloc((void**)&c->rA, S * sizeof(double));
+    alloc((void**)&c->rB, S * sizeof(double));
+    alloc((void**)&c->rC, S * sizeof(double));
+    alloc((void**)&c->dW, SD_MAX_N * sizeof(double));
+    const int tpe = ((np + 31) / 32) * 32;
+    const int epb = std::max(1, 256 / tpe);
+    c->diag_blocks = (c->nelem + epb - 1) / epb;
+    alloc((void**)&c->partial, (size_t)c->diag_blocks * sdk::NDIAG * sizeof(double));
+    alloc((void**)&c->dsum, sdk::NDIAG * sizeof(double));
+    alloc(&c->hU, S * c->esize);
+    alloc(&c->hR, S * c->esize);
+    if (!ok) {
+        cudaGetLastError();
+        sdi_set_error("device allocation of the context scratch failed");
+        free_all(c);
+        free(c);
+        return SD_ENOMEM;
+    }
+    if (cudaMemcpy(c->dW, c->ws, c->n * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess) {
+        sdi_set_error("cudaMemcpy of the Gauss weights failed");
+        free_all(c);
+        free(c);
+        return SD_ECUDA;
+    }
+    *out = c;
+    return SD_OK;
+}
+
+extern "C" void sd_destroy(sd_ctx* c) {
+    if (!c) return;
+    prof_destroy(c);
+    free_all(c);
+    free(c);
+}
+
+extern "C" sd_status sd_set_stream(sd_ctx* c, void* stream) {
+    if (!c) return SD_EINVAL;
+    c->stream = (cudaStream_t)stream;
+    return SD_OK;
+}
+
+extern "C" size_t sd_state_size(const sd_ctx* c) { return c ? c->nstate : 0; }
+extern "C" int sd_nvar(const sd_ctx* c) { return c ? c->nvar : 0; }
+
+extern "C" sd_status sd_points(const sd_ctx* c, double* xi, double* w) {
+    if (!c || !xi || !w) return SD_EINVAL;
+    for (int i = 0; i < c->n; ++i) {
+        xi[i] = c->xs[i];
+        w[i] = c->ws[i];
+    }
+    return SD_OK;
+}
+
+// ------------------------------------------------------------------ residual
+static bool overlap(const void* a, const void* b, size_t bytes) {
+    const char* x = (const char*)a;
+    const char* y = (const char*)b;
+    return x < y + bytes && y < x + bytes;
+}
+
+static sd_status residual_any(sd_ctx* c, const void* U, void* R) {
+    if (c->prec == SD_F32) return sdi_residual_f32(c, (const float*)U, (float*)R);
+    return sdi_residual_f64(c, (const double*)U, (double*)R);
+}
+
+extern "C" sd_status sd_residual(sd_ctx* c, const void* U, void* R) {
+    if (!c || !U || !R) { sdi_set_error("null argument"); return SD_EINVAL; }
+    if (overlap(U, R, c->nstate * c->esize)) { sdi_set_error("U and R overlap"); return SD_EINVAL; }
+    return residual_any(c, U, R);
+}
+
+extern "C" sd_status sd_residual_host(sd_ctx* c, const void* U_host, void* R_host) {
+    if (!c || !U_host || !R_host) { sdi_set_error("null argument"); return SD_EINVAL; }
+    const size_t bytes = c->nstate * c->esize;
+    CK(cudaMemcpyAsync(c->hU, U_host, bytes, cudaMemcpyHostToDevice, c->stream));
+    const sd_status st = residual_any(c, c->hU, c->hR);
+    if (st != SD_OK) return st;
+    CK(cudaMemcpyAsync(R_host, c->hR, bytes, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return SD_OK;
+}
+
+// ------------------------------------------------------------------ Runge-Kutta
+static int grid_for(size_t n) {
+    size_t b = (n + 255) / 256;
+    return (int)std::min<size_t>(std::max<size_t>(b, 1), 148 * 16);
+}
+
+template <typename real>
+static sd_status rk_step_t(sd_ctx* c, double* U, double dt, sd_rk rk) {
+    const size_t n = c->nstate;
+    real* S = (real*)c->S;
+    real* K = (real*)c->K;
+    const int gb = grid_for(n);
+    cudaStream_t st = c->stream;
+    // residual of the stage input; stage 1 reads U itself (an FP32 copy when needed)
+    auto res = [&](const void* in) -> sd_status { return residual_any(c, in, K); };
+    const void* first = U;
+    if (sizeof(real) == 4) {
+        sdi_prof_begin(c, SD_K_OTHER);
+        sdk::k_to_real<real><<<gb, 256, 0, st>>>(U, S, n);
+        sdi_prof_end(c, SD_K_OTHER);
+        first = S;
+    }
+    sd_status s;
+    if (rk == SD_RK4) {
+        for (int k = 0; k < 4; ++k) {
+            if ((s = res(k == 0 ? first : (const void*)S)) != SD_OK) return s;
+            sdi_prof_begin(c, SD_K_OTHER);
+            sdk::k_rk4<real><<<gb, 256, 0, st>>>(k, U, c->rA, K, S, dt, n);
+            sdi_prof_end(c, SD_K_OTHER);
+        }
+    } else if (rk == SD_SSPRK54) {
+        const sdk::SSPCoef cf = {0.391752226571890, 0.444370493651235, 0.555629506348765,
+                                 0.368410593050371, 0.620101851488403, 0.379898148511597,
+                                 0.251891774271694, 0.178079954393132, 0.821920045606868,
+                                 0.544974750228521, 0.517231671970585, 0.096059710526147,
+                                 0.063692468666290, 0.386708617503269, 0.226007483236906};
+        for (int k = 0; k < 5; ++k) {
+            if ((s = res(k == 0 ? first : (const void*)S)) != SD_OK) return s;
+            sdi_prof_begin(c, SD_K_OTHER);
+            sdk::k_ssp<real><<<gb, 256, 0, st>>>(k, U, c->rA, c->rB, c->rC, K, S, dt, cf, n);
+            sdi_prof_end(c, SD_K_OTHER);
+        }
+    } else if (rk == SD_LSRK54) {
+        static const double A[5] = {0.0, -567301805773.0 / 1357537059087.0,
+                                    -2404267990393.0 / 2016746695238.0,
+                                    -3550918686646.0 / 2091501179385.0,
+                                    -1275806237668.0 / 842570457699.0};
+        static const double B[5] = {1432997174477.0 / 9575080441755.0,
+                                    5161836677717.0 / 13612068292357.0,
+                                    1720146321549.0 / 2090206949498.0,
+                                    3134564353537.0 / 4481467310338.0,
+                                    2277821191437.0 / 14882151754819.0};
+        for (int k = 0; k < 5; ++k) {
+            if ((s = res(k == 0 ? first : (const void*)S)) != SD_OK) return s;
+            sdi_prof_begin(c, SD_K_OTHER);
+            sdk::k_lsrk<real><<<gb, 256, 0, st>>>(U, c->rA, K, S, A[k], B[k], dt, n);
+            sdi_prof_end(c, SD_K_OTHER);
+        }
+    } else {
+        sdi_set_error("bad Runge-Kutta scheme");
+        return SD_EINVAL;
+    }
+    CK(cudaGetLastError());
+    return SD_OK;
+}
+
+extern "C" sd_status sd_rk_step(sd_ctx* c, double* U64, double t, double dt, sd_rk rk) {
+    (void)t;
+    if (!c || !U64) { sdi_set_error("null argument"); return SD_EINVAL; }
+    if (!(dt > 0.0) || !isfinite(dt)) { sdi_set_error("dt must be positive and finite"); return SD_EINVAL; }
+    if (c->prec == SD_F32) return rk_step_t<float>(c, U64, dt, rk);
+    return rk_step_t<double>(c, U64, dt, rk);
+}
+
+// ------------------------------------------------------------------ diagnostics
+namespace sdk {
+__global__ void k_diag_final(const double* __restrict__ partial, int nblocks,
+                             double* __restrict__ out) {
+    __shared__ double red[NDIAG][256];
+    for (int k = 0; k < NDIAG; ++k) {
+        double s = 0.0;
+        for (int b = threadIdx.x; b < nblocks; b += blockDim.x) s += partial[(size_t)b * NDIAG + k];
+        red[k][threadIdx.x] = s;
+    }
+    __syncthreads();
+    for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+        if ((int)threadIdx.x < st)
+            for (int k = 0; k < NDIAG; ++k) red[k][threadIdx.x] += red[k][threadIdx.x + st];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        for (int k = 0; k < NDIAG; ++k) out[k] = red[k][0];
+}
+
+template <int N, int DIM, int NV>
+static sd_status diag_impl(sd_ctx* c, const double* U) {
+    using FP = Footprint<N, DIM, NV>;
+    const Ops<double, N> ops = make_ops<double, N>(c);
+    const Mesh g = make_mesh(c);
+    const long long ntr = (long long)g.nelem * FP::NF * NV * FP::NQ;
+    sdi_prof_begin(c, SD_K_OTHER);
+    k_trace<double, N, DIM, NV><<<trace_blocks(ntr), 256, 0, c->stream>>>(U, c->Tu64, ops, g);
+    sdi_prof_end(c, SD_K_OTHER);
+    const int epb = std::max(1, 256 / FP::TPE);
+    const int threads = epb * FP::TPE;
+    const size_t smem = std::max<size_t>(epb * FP::grad, (size_t)NDIAG * threads) * sizeof(double);
+    if (!set_smem(k_diag<N, DIM, NV>, smem)) return SD_EUNSUPPORTED;
+    const int nb = (g.nelem + epb - 1) / epb;
+    if (nb != c->diag_blocks) return SD_EINVAL;
+    sdi_prof_begin(c, SD_K_OTHER);
+    k_diag<N, DIM, NV><<<nb, threads, smem, c->stream>>>(U, c->Tu64, ops, g, c->dW, c->J, c->partial);
+    sdi_prof_end(c, SD_K_OTHER);
+    sdi_prof_begin(c, SD_K_OTHER);
+    k_diag_final<<<1, 256, 0, c->stream>>>(c->partial, nb, c->dsum);
+    sdi_prof_end(c, SD_K_OTHER);
+    CK(cudaGetLastError());
+    return SD_OK;
+}
+
+template <int N>
+static sd_status diag_n(sd_ctx* c, const double* U) {
+    if (c->nvar == 5) return diag_impl<N, 3, 5>(c, U);
+    if (c->dim == 1) return diag_impl<N, 1, 1>(c, U);
+    return diag_impl<N, 3, 1>(c, U);
+}
+}  // namespace sdk
+
+extern "C" sd_status sd_diagnostics(sd_ctx* c, const double* U64, double t, sd_diag* out) {
+    if (!c || !U64 || !out) { sdi_set_error("null argument"); return SD_EINVAL; }
+    sd_status s;
+    switch (c->n) {
+        case 2: s = sdk::diag_n<2>(c, U64); break;
+        case 3: s = sdk::diag_n<3>(c, U64); break;
+        case 4: s = sdk::diag_n<4>(c, U64); break;
+        case 5: s = sdk::diag_n<5>(c, U64); break;
+        case 6: s = sdk::diag_n<6>(c, U64); break;
+        case 7: s = sdk::diag_n<7>(c, U64); break;
+        case 8: s = sdk::diag_n<8>(c, U64); break;
+        case 9: s = sdk::diag_n<9>(c, U64); break;
+        default: s = SD_EUNSUPPORTED;
+    }
+    if (s != SD_OK) return s;
+    double h[sdk::NDIAG];
+    CK(cudaMemcpyAsync(h, c->dsum, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    memset(out, 0, sizeof(*out));
+    out->t = t;
+    out->ke = h[0];
+    out->ke_rho = h[1];
+    out->enstrophy = h[2];
+    out->mass = h[3];
+    out->mom[0] = h[4];
+    out->mom[1] = h[5];
+    out->mom[2] = h[6];
+    out->energy = h[7];
+    out->l2sq = h[8];
+    double vol = 1.0;
+    for (int d = 0; d < c->dim; ++d) vol *= c->hi[d] - c->lo[d];
+    out->volume = vol;
+    out->nonfinite = h[9] != 0.0 ? 1 : 0;
+    if (out->nonfinite) {
+        sdi_set_error("state holds %g non-finite points", h[9]);
+        return SD_ENONFINITE;
+    }
+    return SD_OK;
+}

@@ -1,0 +1,70 @@
+// Library-internal context and dispatch declarations (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+#include "sd.h"
+
+#define SD_MAX_N 9
+
+struct sd_ctx {
+    // problem
+    int dim;
+    int ne[3];
+    int nelem;
+    int p, n;
+    int nvar;
+    int ngrad;               // gradient components exchanged per face (1 scalar, 9 NS)
+    sd_scheme scheme;
+    sd_physics phys;
+    sd_precision prec;
+    cudaStream_t stream;
+    int device;
+    double lo[3], hi[3], h[3];
+    double J;                // prod_d h_d / 2
+    // 1D operators (host, FP64), built by the library itself
+    double xs[SD_MAX_N], ws[SD_MAX_N], xf[SD_MAX_N + 1];
+    double L[(SD_MAX_N + 1) * SD_MAX_N];     // L[f*n + i]
+    double M[SD_MAX_N * (SD_MAX_N + 1)];     // M[i*(n+1) + f]
+    double D[SD_MAX_N * SD_MAX_N];           // D = M L
+    double alpha, beta;
+    // sizes
+    size_t npts;             // points per variable = nelem * n^dim
+    size_t nstate;           // nvar * npts
+    size_t ntu, ntg;         // trace buffer sizes (values)
+    size_t esize;            // bytes per value of the residual precision
+    // scratch owned by the context
+    void* Tu;                // face traces of u        [nelem][2dim][nvar][n^(dim-1)]
+    void* Tg;                // face gradient values    [nelem][2dim][ngrad][n^(dim-1)]
+    double* Tu64;            // FP64 traces for diagnostics (== Tu when prec is F64)
+    void* S;                 // stage input of the residual precision
+    void* K;                 // stage residual of the residual precision
+    double *rA, *rB, *rC;    // FP64 Runge-Kutta registers
+    double* dW;              // Gauss weights (device, n values)
+    double* partial;         // diagnostics block partials
+    double* dsum;            // diagnostics totals (device)
+    int diag_blocks;
+    void* hU;                // device staging of the host-buffer residual path
+    void* hR;
+    // profiling and launch accounting
+    long long launches;
+    int prof_on;
+    int prof_n[SD_K_COUNT];                   // recorded event pairs per kernel class
+    cudaEvent_t* prof_ev[SD_K_COUNT];         // 2 * SDI_PROF_CAP events per class
+    double prof_ms[SD_K_COUNT];
+    long long prof_count[SD_K_COUNT];
+};
+
+#define SDI_PROF_CAP 512
+
+// bracket one kernel launch of class k (no-op unless profiling is enabled)
+void sdi_prof_begin(sd_ctx* c, int k);
+void sdi_prof_end(sd_ctx* c, int k);
+
+// dispatch entry points (one translation unit per residual precision)
+sd_status sdi_residual_f32(sd_ctx* c, const float* U, float* R);
+sd_status sdi_residual_f64(sd_ctx* c, const double* U, double* R);
+sd_status sdi_diag(sd_ctx* c, const double* U64, double* host_out);
+sd_status sdi_check_smem(sd_ctx* c);
+void sdi_set_error(const char* fmt, ...);

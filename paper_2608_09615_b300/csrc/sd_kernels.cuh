@@ -1,0 +1,682 @@
+// Device code of the SD residual (Lodato & Tonicello, Secs. 2.1-2.3, 4.3, 4.4).
+//
+// Three element-local kernels evaluate one residual:
+//   k_trace    u at the 2*DIM faces of every element (Sec. 2.3 step 1, interface rows only)
+//   k_grad     common solution corrections, gradient v^S at the solution points (Eq. w:e)
+//              and the element's own interface gradient values (BR1: Eq. v:e; compact:
+//              Eqs. aux:cmp:lr:2d, aux:cmp:bt:2d in closed form, see face_grad below)
+//   k_flux_div gradient at interior flux points, interface averages (Eq. c:aux:v:2d),
+//              physical / Riemann fluxes at all flux points and the divergence (step 5)
+// Every element is staged in shared memory; 1D operators act along one direction at a
+// time (tensor-product sweeps). Values exchanged between elements go through two
+// face-trace buffers: Tu[e][face][var][q] and Tg[e][face][comp][q].
+//
+// Bitwise consistency: a value computed by both elements sharing an interface (the
+// trace, the correction delta, the own-side interface gradient) is produced by the same
+// device function with an explicit fma sequence, so both sides see identical bits and
+// the interface flux is single-valued; conservation then holds to round-off.
+//
+// Compact closed form (Cartesian grids). With delta_L = (u_{e-}(1) - u_e(-1))/2 and
+// delta_R = (u_{e+}(-1) - u_e(1))/2 along direction d, Eqs. v:s:l / v:s:r remove from
+// v^S the derivative of the opposite-face correction; extrapolated to the own face this
+// leaves, for the d-component of the gradient only,
+//   left  face: c_L^T L v^S - (2/h_d) alpha delta_R,  alpha = c_L^T L M c_R = (-1)^p / 2
+//   right face: c_R^T L v^S - (2/h_d) beta  delta_L,  beta  = c_R^T L M c_L = -alpha
+// The transverse components equal the BR1 values (Sec. 2.3: transverse fluxes stay
+// continuous). The CPU oracle forms the one-sided arrays literally instead.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace sdk {
+
+constexpr int ipow(int b, int e) { return e == 0 ? 1 : b * ipow(b, e - 1); }
+
+template <typename real, int N>
+struct Ops {
+    real L[(N + 1) * N];     // L[f*N + i]     = l_i(xi_{f-1/2})          (Eq. Lmat)
+    real M[N * (N + 1)];     // M[i*(N+1) + f] = l'_{f-1/2}(xi_i)         (Eq. Mmat)
+    real D[N * N];           // D = M L: derivative at solution points
+    real two_h[3];           // 2/h_d  (J^-1 S_dd of the affine map)
+    real corrL[3];           // (2/h_d) alpha
+    real corrR[3];           // (2/h_d) beta
+};
+
+template <typename real>
+struct Phys {
+    int kind;                // 0 heat, 1 porous medium, 2 Navier-Stokes
+    int sutherland;
+    int riemann;             // 0 Roe, 1 Rusanov
+    real nu, m_pme;
+    real gamma, gm1, gamma_Pr, mu0, p0, rhoE0, inv_e0, suth_s, suth_1ps, harten;
+};
+
+struct Mesh {
+    int ne[3];
+    int nelem;
+};
+
+// ------------------------------------------------------------------ index helpers
+template <int N>
+__device__ __forceinline__ int npow(int d) {
+    return d == 0 ? 1 : (d == 1 ? N : N * N);
+}
+
+// point index of the point at position i along direction d on the line whose
+// face index (point index with direction d removed) is q
+template <int N>
+__device__ __forceinline__ int pt_of(int d, int i, int q) {
+    const int lo = npow<N>(d);
+    return (q % lo) + lo * i + lo * N * (q / lo);
+}
+
+__device__ __forceinline__ int neighbour(const Mesh& g, int e, int d, int side) {
+    int c0 = e % g.ne[0];
+    int r = e / g.ne[0];
+    int c1 = r % g.ne[1];
+    int c2 = r / g.ne[1];
+    int c[3] = {c0, c1, c2};
+    c[d] += side ? 1 : -1;
+    if (c[d] < 0) c[d] += g.ne[d];
+    if (c[d] >= g.ne[d]) c[d] -= g.ne[d];
+    return c[0] + g.ne[0] * (c[1] + g.ne[1] * c[2]);
+}
+
+// sum_i row[i] * base[i*stride], one fixed fma sequence
+template <typename real, int N>
+__device__ __forceinline__ real line_dot(const real* row, const real* base, int stride) {
+    real s = row[0] * base[0];
+#pragma unroll
+    for (int i = 1; i < N; ++i) s = fma(row[i], base[i * stride], s);
+    return s;
+}
+
+// gradient components exchanged at a face normal to d: the d-derivative of every
+// variable, and for NS the two transverse derivatives of rho and rho u_d (all the
+// viscous flux in direction d needs when lambda = 0).
+template <int NV>
+__device__ __forceinline__ void comp_map(int d, int c, int& v, int& m) {
+    if (NV == 1 || c < NV) {
+        v = (NV == 1) ? 0 : c;
+        m = d;
+        return;
+    }
+    const int t = (c - NV) >> 1;            // 0 -> first transverse, 1 -> second
+    m = (d + 1 + t) % 3;
+    v = ((c - NV) & 1) ? 1 + d : 0;
+}
+
+template <int NV>
+struct NumGrad {
+    static constexpr int value = (NV == 1) ? 1 : 9;
+};
+
+// ------------------------------------------------------------------ physics
+template <typename real>
+__device__ __forceinline__ real sutherland_mu(const Phys<real>& P, real e) {
+    if (!P.sutherland) return P.mu0;
+    const real th = e * P.inv_e0;
+    return P.mu0 * th * sqrt(th) * P.suth_1ps / (th + P.suth_s);
+}
+
+// Sec. 4.4 inviscid flux along d; the momentum rows carry p - p0 (the constant p0 has
+// zero discrete divergence, so this is the same scheme with less FP32 cancellation).
+template <typename real>
+__device__ __forceinline__ void ns_convective(const real* U, int d, const Phys<real>& P,
+                                              real* F) {
+    const real ir = real(1) / U[0];
+    const real v0 = U[1] * ir, v1 = U[2] * ir, v2 = U[3] * ir;
+    const real ke2 = U[1] * v0 + U[2] * v1 + U[3] * v2;        // rho |u|^2
+    const real pp = P.gm1 * ((U[4] - P.rhoE0) - real(0.5) * ke2);   // p - p0
+    const real p = pp + P.p0;
+    const real ud = (d == 0) ? v0 : (d == 1 ? v1 : v2);
+    F[0] = U[1 + d];
+    F[1] = U[1] * ud;
+    F[2] = U[2] * ud;
+    F[3] = U[3] * ud;
+    F[1 + d] += pp;
+    F[4] = (U[4] + p) * ud;
+}
+
+// Sec. 4.4 viscous flux along d from the 9 exchanged conservative-gradient components g
+// (comp_map order): tau = mu (grad u + grad u^T) (lambda = 0), heat flux
+// kappa grad T = (mu gamma / Pr) grad e, primitive gradients from conservative ones.
+template <typename real>
+__device__ __forceinline__ void ns_viscous(const real* U, const real* g, int d,
+                                           const Phys<real>& P, real* Fv) {
+    const real ir = real(1) / U[0];
+    const real vel[3] = {U[1] * ir, U[2] * ir, U[3] * ir};
+    const real E = U[4] * ir;
+    const real e = E - real(0.5) * (vel[0] * vel[0] + vel[1] * vel[1] + vel[2] * vel[2]);
+    const real mu = sutherland_mu(P, e);
+    real dud[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) dud[i] = (g[1 + i] - vel[i] * g[0]) * ir;   // d u_i / d x_d
+    const int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
+    const real ud = vel[d];
+    const real dt1 = (g[6] - ud * g[5]) * ir;                               // d u_d / d x_t1
+    const real dt2 = (g[8] - ud * g[7]) * ir;                               // d u_d / d x_t2
+    const real dE = (g[4] - E * g[0]) * ir;
+    const real de = dE - (vel[0] * dud[0] + vel[1] * dud[1] + vel[2] * dud[2]);
+    real tau[3];
+    tau[d] = real(2) * mu * dud[d];
+    tau[t1] = mu * (dud[t1] + dt1);
+    tau[t2] = mu * (dud[t2] + dt2);
+    Fv[0] = real(0);
+    Fv[1] = tau[0];
+    Fv[2] = tau[1];
+    Fv[3] = tau[2];
+    Fv[4] = vel[0] * tau[0] + vel[1] * tau[1] + vel[2] * tau[2] + mu * P.gamma_Pr * de;
+}
+
+// Roe flux with Harten's fix on the acoustic eigenvalues (Sec. 4.4), or Rusanov.
+template <typename real>
+__device__ __forceinline__ void ns_riemann(const real* UL, const real* UR, int d,
+                                           const Phys<real>& P, real* F) {
+    real FL[5], FR[5];
+    ns_convective(UL, d, P, FL);
+    ns_convective(UR, d, P, FR);
+    const real irl = real(1) / UL[0], irr = real(1) / UR[0];
+    const real vl[3] = {UL[1] * irl, UL[2] * irl, UL[3] * irl};
+    const real vr[3] = {UR[1] * irr, UR[2] * irr, UR[3] * irr};
+    const real ppl = P.gm1 * ((UL[4] - P.rhoE0) -
+                              real(0.5) * (UL[1] * vl[0] + UL[2] * vl[1] + UL[3] * vl[2]));
+    const real ppr = P.gm1 * ((UR[4] - P.rhoE0) -
+                              real(0.5) * (UR[1] * vr[0] + UR[2] * vr[1] + UR[3] * vr[2]));
+    const real pl = ppl + P.p0, pr = ppr + P.p0;
+    if (P.riemann == 1) {
+        const real cl = sqrt(P.gamma * pl * irl), cr = sqrt(P.gamma * pr * irr);
+        const real sl = fabs(vl[d]) + cl, sr = fabs(vr[d]) + cr;
+        const real smax = sl > sr ? sl : sr;
+#pragma unroll
+        for (int k = 0; k < 5; ++k) F[k] = real(0.5) * (FL[k] + FR[k]) - real(0.5) * smax * (UR[k] - UL[k]);
+        return;
+    }
+    const real Hl = (UL[4] + pl) * irl, Hr = (UR[4] + pr) * irr;
+    const real sl = sqrt(UL[0]), sr = sqrt(UR[0]);
+    const real iw = real(1) / (sl + sr);
+    real ut[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) ut[i] = (sl * vl[i] + sr * vr[i]) * iw;
+    const real Ht = (sl * Hl + sr * Hr) * iw;
+    const real rt = sl * sr;
+    const real q2 = ut[0] * ut[0] + ut[1] * ut[1] + ut[2] * ut[2];
+    const real c2 = P.gm1 * (Ht - real(0.5) * q2);
+    const real c = sqrt(c2);
+    const real qn = ut[d];
+    const real drho = UR[0] - UL[0];
+    const real dp = ppr - ppl;
+    real dv[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) dv[i] = vr[i] - vl[i];
+    const real dvn = dv[d];
+    real l1 = fabs(qn - c), l2 = fabs(qn), l5 = fabs(qn + c);
+    if (P.harten > real(0)) {
+        const real del = P.harten * c;
+        if (l1 < del) l1 = (l1 * l1 + del * del) / (real(2) * del);
+        if (l5 < del) l5 = (l5 * l5 + del * del) / (real(2) * del);
+    }
+    const real ic2 = real(1) / c2;
+    const real a1 = (dp - rt * c * dvn) * real(0.5) * ic2;
+    const real a2 = drho - dp * ic2;
+    const real a5 = (dp + rt * c * dvn) * real(0.5) * ic2;
+    const real w1 = l1 * a1, w2 = l2 * a2, w5 = l5 * a5, ws = l2 * rt;
+    real dvt[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) dvt[i] = dv[i] - (i == d ? dvn : real(0));
+    real diss[5];
+    diss[0] = w1 + w2 + w5;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const real en = (i == d) ? c : real(0);
+        diss[1 + i] = w1 * (ut[i] - en) + w2 * ut[i] + w5 * (ut[i] + en) + ws * dvt[i];
+    }
+    diss[4] = w1 * (Ht - qn * c) + w2 * real(0.5) * q2 + w5 * (Ht + qn * c) +
+              ws * (ut[0] * dvt[0] + ut[1] * dvt[1] + ut[2] * dvt[2]);
+#pragma unroll
+    for (int k = 0; k < 5; ++k) F[k] = real(0.5) * (FL[k] + FR[k]) - real(0.5) * diss[k];
+}
+
+// scalar diffusion flux (heat: -nu v_d; PME: -m |u|^(m-1) v_d, Eq. pme)
+template <typename real>
+__device__ __forceinline__ real scalar_flux(const Phys<real>& P, real u, real g) {
+    if (P.kind == 1) return -P.m_pme * pow(fabs(u), P.m_pme - real(1)) * g;
+    return -P.nu * g;
+}
+
+// ------------------------------------------------------------------ element staging
+// Shared-memory footprint per element (in reals) for the gradient / flux kernels.
+template <int N, int DIM, int NV>
+struct Footprint {
+    static constexpr int NP = ipow(N, DIM);
+    static constexpr int NQ = ipow(N, DIM - 1);
+    static constexpr int NF = 2 * DIM;
+    static constexpr int U = NV * NP;
+    static constexpr int TR = NF * NV * NQ;
+    static constexpr int VS = NV * DIM * NP;
+    static constexpr int G = NV * (N + 1) * NQ;
+    static constexpr int grad = U + 2 * TR + VS;
+    static constexpr int flux = U + 2 * TR + VS + G;
+    static constexpr int TPE = ((NP + 31) / 32) * 32;   // threads per element
+    // largest block the host launches: ~256 threads, or one element when TPE > 256
+    static constexpr int MAXT = TPE > 256 ? TPE : 256;
+};
+
+// Stage u, the own traces, the neighbour traces and v^S of element e in shared memory.
+// All TPE threads of the element call this; ends with the element's v^S ready.
+template <typename real, int N, int DIM, int NV>
+__device__ __forceinline__ void stage_element(const real* __restrict__ U,
+                                              const real* __restrict__ Tu,
+                                              const Ops<real, N>& ops, const Mesh& g,
+                                              int e, bool valid, int tid, real* su,
+                                              real* tro, real* trn, real* vS) {
+    using FP = Footprint<N, DIM, NV>;
+    constexpr int NP = FP::NP, NQ = FP::NQ, NF = FP::NF, TPE = FP::TPE;
+    if (valid) {
+        for (int k = tid; k < NV * NP; k += TPE) {
+            const int v = k / NP, pt = k - v * NP;
+            su[k] = U[(size_t)v * g.nelem * NP + (size_t)e * NP + pt];
+        }
+        for (int k = tid; k < NF * NV * NQ; k += TPE) {
+            const int f = k / (NV * NQ);
+            const int rem = k - f * NV * NQ;
+            const int d = f >> 1, s = f & 1;
+            const int en = neighbour(g, e, d, s);
+            // the neighbour's trace on the shared face is its face of opposite side
+            trn[k] = Tu[((size_t)en * NF + (f ^ 1)) * NV * NQ + rem];
+        }
+    }
+    __syncthreads();
+    if (valid) {
+        for (int k = tid; k < NF * NV * NQ; k += TPE) {
+            const int f = k / (NV * NQ);
+            const int rem = k - f * NV * NQ;
+            const int v = rem / NQ, q = rem - v * NQ;
+            const int d = f >> 1, s = f & 1;
+            tro[k] = line_dot<real, N>(ops.L + (s ? N * N : 0), su + v * NP + pt_of<N>(d, 0, q),
+                                       npow<N>(d));
+        }
+    }
+    __syncthreads();
+    if (valid) {
+        // Eq. w:e in Cartesian form: v_m = (2/h_m) M_m u^{Fm,C}
+        //   = (2/h_m) (D u + M[:,0] delta_L + M[:,N] delta_R) along m.
+        for (int k = tid; k < NV * DIM * NP; k += TPE) {
+            const int vm = k / NP, pt = k - vm * NP;
+            const int v = vm / DIM, m = vm - v * DIM;
+            const int lo = npow<N>(m);
+            const int i = (pt / lo) % N;
+            const int q = (pt % lo) + lo * (pt / (lo * N));
+            real acc = line_dot<real, N>(ops.D + i * N, su + v * NP + pt_of<N>(m, 0, q), lo);
+            const int fl = 2 * m, fr = 2 * m + 1;
+            const real dl = real(0.5) * (trn[(fl * NV + v) * NQ + q] - tro[(fl * NV + v) * NQ + q]);
+            const real dr = real(0.5) * (trn[(fr * NV + v) * NQ + q] - tro[(fr * NV + v) * NQ + q]);
+            acc = fma(ops.M[i * (N + 1)], dl, acc);
+            acc = fma(ops.M[i * (N + 1) + N], dr, acc);
+            vS[k] = ops.two_h[m] * acc;
+        }
+    }
+    __syncthreads();
+}
+
+// The element's own interface value of gradient component c on face f (BR1: Eq. v:e at
+// the interface row; compact: the closed form described at the top of this file).
+template <typename real, int N, int DIM, int NV>
+__device__ __forceinline__ real face_grad(const Ops<real, N>& ops, int compact, int f, int c,
+                                          int q, const real* vS, const real* tro,
+                                          const real* trn) {
+    using FP = Footprint<N, DIM, NV>;
+    constexpr int NP = FP::NP, NQ = FP::NQ;
+    const int d = f >> 1, s = f & 1;
+    int v, m;
+    comp_map<NV>(d, c, v, m);
+    real val = line_dot<real, N>(ops.L + (s ? N * N : 0), vS + (v * DIM + m) * NP + pt_of<N>(d, 0, q),
+                                 npow<N>(d));
+    if (compact && m == d) {
+        const int fo = f ^ 1;    // the opposite face of the same direction
+        const real dop = real(0.5) * (trn[(fo * NV + v) * NQ + q] - tro[(fo * NV + v) * NQ + q]);
+        val = fma(-(s ? ops.corrR[d] : ops.corrL[d]), dop, val);
+    }
+    return val;
+}
+
+// ------------------------------------------------------------------ kernels
+template <typename real, int N, int DIM, int NV>
+__global__ void k_trace(const real* __restrict__ U, real* __restrict__ Tu, Ops<real, N> ops,
+                        Mesh g) {
+    constexpr int NP = ipow(N, DIM), NQ = ipow(N, DIM - 1), NF = 2 * DIM;
+    const long long total = (long long)g.nelem * NF * NV * NQ;
+    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int q = (int)(idx % NQ);
+        long long r = idx / NQ;
+        const int v = (int)(r % NV);
+        r /= NV;
+        const int f = (int)(r % NF);
+        const int e = (int)(r / NF);
+        const int d = f >> 1, s = f & 1;
+        Tu[idx] = line_dot<real, N>(ops.L + (s ? N * N : 0),
+                                    U + (size_t)v * g.nelem * NP + (size_t)e * NP + pt_of<N>(d, 0, q),
+                                    npow<N>(d));
+    }
+}
+
+template <typename real, int N, int DIM, int NV>
+__global__ void __launch_bounds__(Footprint<N, DIM, NV>::MAXT) k_grad(const real* __restrict__ U, const real* __restrict__ Tu,
+                       real* __restrict__ Tg, Ops<real, N> ops, Mesh g, int compact) {
+    using FP = Footprint<N, DIM, NV>;
+    constexpr int NQ = FP::NQ, NF = FP::NF, TPE = FP::TPE;
+    constexpr int NG = NumGrad<NV>::value;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    real* sm = reinterpret_cast<real*>(smem_raw);
+    const int le = threadIdx.x / TPE, tid = threadIdx.x - le * TPE;
+    const int epb = blockDim.x / TPE;
+    const int e = blockIdx.x * epb + le;
+    const bool valid = e < g.nelem;
+    real* base = sm + le * FP::grad;
+    real* su = base;
+    real* tro = su + FP::U;
+    real* trn = tro + FP::TR;
+    real* vS = trn + FP::TR;
+    stage_element<real, N, DIM, NV>(U, Tu, ops, g, e, valid, tid, su, tro, trn, vS);
+    if (!valid) return;
+    for (int k = tid; k < NF * NG * NQ; k += TPE) {
+        const int f = k / (NG * NQ);
+        const int rem = k - f * NG * NQ;
+        const int c = rem / NQ, q = rem - c * NQ;
+        Tg[(size_t)e * NF * NG * NQ + k] =
+            face_grad<real, N, DIM, NV>(ops, compact, f, c, q, vS, tro, trn);
+    }
+}
+
+template <typename real, int N, int DIM, int NV>
+__global__ void __launch_bounds__(Footprint<N, DIM, NV>::MAXT) k_flux_div(const real* __restrict__ U, const real* __restrict__ Tu,
+                           const real* __restrict__ Tg, real* __restrict__ R, Ops<real, N> ops,
+                           Mesh g, Phys<real> P, int compact) {
+    using FP = Footprint<N, DIM, NV>;
+    constexpr int NP = FP::NP, NQ = FP::NQ, NF = FP::NF, TPE = FP::TPE;
+    constexpr int NG = NumGrad<NV>::value;
+    constexpr int NIT = (NV * NP + TPE - 1) / TPE;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    real* sm = reinterpret_cast<real*>(smem_raw);
+    const int le = threadIdx.x / TPE, tid = threadIdx.x - le * TPE;
+    const int epb = blockDim.x / TPE;
+    const int e = blockIdx.x * epb + le;
+    const bool valid = e < g.nelem;
+    real* base = sm + le * FP::flux;
+    real* su = base;
+    real* tro = su + FP::U;
+    real* trn = tro + FP::TR;
+    real* vS = trn + FP::TR;
+    real* G = vS + FP::VS;
+    stage_element<real, N, DIM, NV>(U, Tu, ops, g, e, valid, tid, su, tro, trn, vS);
+
+    real racc[NIT];
+#pragma unroll
+    for (int k = 0; k < NIT; ++k) racc[k] = real(0);
+
+#pragma unroll 1
+    for (int d = 0; d < DIM; ++d) {
+        const int stride = npow<N>(d);
+        if (valid) {
+            for (int k = tid; k < (N + 1) * NQ; k += TPE) {
+                const int f = k / NQ, q = k - f * NQ;
+                real F[NV];
+                if (f > 0 && f < N) {
+                    // interior flux point: extrapolated solution and gradient (Eq. aux:v:std:2d)
+                    const real* Lr = ops.L + f * N;
+                    real uf[NV], gr[NG];
+#pragma unroll
+                    for (int v = 0; v < NV; ++v)
+                        uf[v] = line_dot<real, N>(Lr, su + v * NP + pt_of<N>(d, 0, q), stride);
+#pragma unroll
+                    for (int c = 0; c < NG; ++c) {
+                        int v, m;
+                        comp_map<NV>(d, c, v, m);
+                        gr[c] = line_dot<real, N>(Lr, vS + (v * DIM + m) * NP + pt_of<N>(d, 0, q), stride);
+                    }
+                    if constexpr (NV == 5) {
+                        real Fv[5];
+                        ns_convective(uf, d, P, F);
+                        ns_viscous(uf, gr, d, P, Fv);
+#pragma unroll
+                        for (int v = 0; v < NV; ++v) F[v] -= Fv[v];
+                    } else {
+                        F[0] = scalar_flux(P, uf[0], gr[0]);
+                    }
+                } else {
+                    // interface flux point: common solution, averaged gradient, Riemann flux
+                    const int s = (f == N) ? 1 : 0;
+                    const int face = 2 * d + s;
+                    const int en = neighbour(g, e, d, s);
+                    real UL[NV], UR[NV], Uh[NV], vh[NG];
+#pragma unroll
+                    for (int v = 0; v < NV; ++v) {
+                        const real own = tro[(face * NV + v) * NQ + q];
+                        const real nb = trn[(face * NV + v) * NQ + q];
+                        UL[v] = s ? own : nb;
+                        UR[v] = s ? nb : own;
+                        Uh[v] = real(0.5) * (UL[v] + UR[v]);
+                    }
+#pragma unroll
+                    for (int c = 0; c < NG; ++c) {
+                        const real go = face_grad<real, N, DIM, NV>(ops, compact, face, c, q, vS, tro, trn);
+                        const real gn = Tg[(((size_t)en * NF + (face ^ 1)) * NG + c) * NQ + q];
+                        vh[c] = s ? real(0.5) * (go + gn) : real(0.5) * (gn + go);
+                    }
+                    if constexpr (NV == 5) {
+                        real Fv[5];
+                        ns_riemann(UL, UR, d, P, F);
+                        ns_viscous(Uh, vh, d, P, Fv);
+#pragma unroll
+                        for (int v = 0; v < NV; ++v) F[v] -= Fv[v];
+                    } else {
+                        F[0] = scalar_flux(P, Uh[0], vh[0]);
+                    }
+                }
+#pragma unroll
+                for (int v = 0; v < NV; ++v) G[(v * (N + 1) + f) * NQ + q] = F[v];
+            }
+        }
+        __syncthreads();
+        if (valid) {
+            // step 5: dq/dt = -sum_d M_d G^{Fd}, with J^-1 S_dd = 2/h_d
+#pragma unroll
+            for (int it = 0; it < NIT; ++it) {
+                const int k = tid + it * TPE;
+                if (k < NV * NP) {
+                    const int v = k / NP, pt = k - v * NP;
+                    const int i = (pt / stride) % N;
+                    const int q = (pt % stride) + stride * (pt / (stride * N));
+                    const real* Gl = G + v * (N + 1) * NQ + q;
+                    const real* Mr = ops.M + i * (N + 1);
+                    real s = Mr[0] * Gl[0];
+#pragma unroll
+                    for (int f = 1; f <= N; ++f) s = fma(Mr[f], Gl[f * NQ], s);
+                    racc[it] = fma(-ops.two_h[d], s, racc[it]);
+                }
+            }
+        }
+        __syncthreads();
+    }
+    if (valid) {
+#pragma unroll
+        for (int it = 0; it < NIT; ++it) {
+            const int k = tid + it * TPE;
+            if (k < NV * NP) {
+                const int v = k / NP, pt = k - v * NP;
+                R[(size_t)v * g.nelem * NP + (size_t)e * NP + pt] = racc[it];
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------ diagnostics (FP64)
+// Sums, per block, of the Gauss-weighted integrands of Sec. 4.4 plus conserved totals;
+// k_diag_final adds the block partials in a fixed order (deterministic).
+constexpr int NDIAG = 10;   // ke, ke_rho, enstrophy, mass, mom0..2, energy, l2sq, nonfinite
+
+template <int N, int DIM, int NV>
+__global__ void __launch_bounds__(Footprint<N, DIM, NV>::MAXT) k_diag(const double* __restrict__ U, const double* __restrict__ Tu,
+                       Ops<double, N> ops, Mesh g, const double* __restrict__ wq, double J,
+                       double* __restrict__ partial) {
+    using FP = Footprint<N, DIM, NV>;
+    constexpr int NP = FP::NP, TPE = FP::TPE;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double* sm = reinterpret_cast<double*>(smem_raw);
+    const int le = threadIdx.x / TPE, tid = threadIdx.x - le * TPE;
+    const int epb = blockDim.x / TPE;
+    const int e = blockIdx.x * epb + le;
+    const bool valid = e < g.nelem;
+    double* base = sm + le * FP::grad;
+    double* su = base;
+    double* tro = su + FP::U;
+    double* trn = tro + FP::TR;
+    double* vS = trn + FP::TR;
+    stage_element<double, N, DIM, NV>(U, Tu, ops, g, e, valid, tid, su, tro, trn, vS);
+    double acc[NDIAG];
+#pragma unroll
+    for (int k = 0; k < NDIAG; ++k) acc[k] = 0.0;
+    if (valid) {
+        for (int pt = tid; pt < NP; pt += TPE) {
+            double w = J;
+            int r = pt;
+#pragma unroll
+            for (int d = 0; d < DIM; ++d) {
+                w *= wq[r % N];
+                r /= N;
+            }
+            bool bad = false;
+#pragma unroll
+            for (int v = 0; v < NV; ++v) bad |= !isfinite(su[v * NP + pt]);
+            acc[9] += bad ? 1.0 : 0.0;
+            if constexpr (NV == 5) {
+                const double rho = su[pt];
+                const double vel[3] = {su[NP + pt] / rho, su[2 * NP + pt] / rho, su[3 * NP + pt] / rho};
+                const double q2 = vel[0] * vel[0] + vel[1] * vel[1] + vel[2] * vel[2];
+                double du[3][3];   // du[k][i] = d u_i / d x_k
+#pragma unroll
+                for (int k = 0; k < 3; ++k)
+#pragma unroll
+                    for (int i = 0; i < 3; ++i)
+                        du[k][i] = (vS[((1 + i) * DIM + k) * NP + pt] - vel[i] * vS[(0 * DIM + k) * NP + pt]) / rho;
+                const double o0 = du[1][2] - du[2][1], o1 = du[2][0] - du[0][2], o2 = du[0][1] - du[1][0];
+                acc[0] += w * 0.5 * q2;
+                acc[1] += w * 0.5 * rho * q2;
+                acc[2] += w * (o0 * o0 + o1 * o1 + o2 * o2);
+                acc[3] += w * rho;
+                acc[4] += w * su[NP + pt];
+                acc[5] += w * su[2 * NP + pt];
+                acc[6] += w * su[3 * NP + pt];
+                acc[7] += w * su[4 * NP + pt];
+            } else {
+                const double u = su[pt];
+                acc[3] += w * u;
+                acc[8] += w * u * u;
+            }
+        }
+    }
+    // deterministic block reduction (fixed tree over the threads)
+    __syncthreads();
+    double* red = sm;   // reuse shared memory: NDIAG * blockDim doubles fit in FP::grad*epb
+    for (int k = 0; k < NDIAG; ++k) red[k * blockDim.x + threadIdx.x] = acc[k];
+    __syncthreads();
+    for (int s = 1; s < (int)blockDim.x; s <<= 1) {
+        if ((threadIdx.x % (2 * s)) == 0 && threadIdx.x + s < blockDim.x)
+            for (int k = 0; k < NDIAG; ++k)
+                red[k * blockDim.x + threadIdx.x] += red[k * blockDim.x + threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        for (int k = 0; k < NDIAG; ++k) partial[(size_t)blockIdx.x * NDIAG + k] = red[k * blockDim.x];
+}
+
+__global__ void k_diag_final(const double* __restrict__ partial, int nblocks,
+                             double* __restrict__ out);
+
+// ------------------------------------------------------------------ Runge-Kutta (FP64)
+// out_real = shadow of a FP64 array in the residual precision
+template <typename real>
+__global__ void k_to_real(const double* __restrict__ x, real* __restrict__ y, size_t n) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x)
+        y[i] = (real)x[i];
+}
+
+// RK4 stage k (0..3): K holds R(stage input). Uacc accumulates the weighted stages; S is
+// the next stage input (residual precision); the last stage writes U.
+template <typename real>
+__global__ void k_rk4(int k, double* __restrict__ U, double* __restrict__ Uacc,
+                      const real* __restrict__ K, real* __restrict__ S, double dt, size_t n) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const double u = U[i];
+        const double kk = (double)K[i];
+        if (k == 0) {
+            Uacc[i] = u + dt / 6.0 * kk;
+            S[i] = (real)(u + 0.5 * dt * kk);
+        } else if (k == 1) {
+            Uacc[i] += dt / 3.0 * kk;
+            S[i] = (real)(u + 0.5 * dt * kk);
+        } else if (k == 2) {
+            Uacc[i] += dt / 3.0 * kk;
+            S[i] = (real)(u + dt * kk);
+        } else {
+            U[i] = Uacc[i] + dt / 6.0 * kk;
+        }
+    }
+}
+
+// SSPRK(5,4) in Shu-Osher form (Spiteri & Ruuth 2002). Registers: U = u0, A = u1/u3/u4,
+// B = u2, C = a52 u2 + a53 u3 + b53 dt L(u3).
+struct SSPCoef {
+    double a10, a20, a21, b21, a30, a32, b32, a40, a43, b43, a52, a53, b53, a54, b54;
+};
+
+template <typename real>
+__global__ void k_ssp(int k, double* __restrict__ U, double* __restrict__ A,
+                      double* __restrict__ B, double* __restrict__ C, const real* __restrict__ K,
+                      real* __restrict__ S, double dt, SSPCoef c, size_t n) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const double kk = dt * (double)K[i];
+        if (k == 0) {
+            const double u1 = U[i] + c.a10 * kk;
+            A[i] = u1;
+            S[i] = (real)u1;
+        } else if (k == 1) {
+            const double u2 = c.a20 * U[i] + c.a21 * A[i] + c.b21 * kk;
+            B[i] = u2;
+            S[i] = (real)u2;
+        } else if (k == 2) {
+            const double u3 = c.a30 * U[i] + c.a32 * B[i] + c.b32 * kk;
+            A[i] = u3;
+            S[i] = (real)u3;
+        } else if (k == 3) {
+            const double u3 = A[i];
+            C[i] = c.a52 * B[i] + c.a53 * u3 + c.b53 * kk;
+            const double u4 = c.a40 * U[i] + c.a43 * u3 + c.b43 * kk;
+            A[i] = u4;
+            S[i] = (real)u4;
+        } else {
+            U[i] = C[i] + c.a54 * A[i] + c.b54 * kk;
+        }
+    }
+}
+
+// LSRK(5,4) of Carpenter & Kennedy: dU <- a dU + dt K; U <- U + b dU.
+template <typename real>
+__global__ void k_lsrk(double* __restrict__ U, double* __restrict__ dU, const real* __restrict__ K,
+                       real* __restrict__ S, double a, double b, double dt, size_t n) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const double du = a * dU[i] + dt * (double)K[i];
+        dU[i] = du;
+        const double u = U[i] + b * du;
+        U[i] = u;
+        S[i] = (real)u;
+    }
+}
+
+}  // namespace sdk

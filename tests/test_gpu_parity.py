@@ -1,0 +1,268 @@
+"""GPU parity of the CUDA path (called through the C ABI) against the FP64 oracle on the
+same seeded inputs.
+
+Tolerances:
+  * FP64 residual: max |R_gpu - R_oracle| <= 1e-12 * max |R_oracle|, per variable (the
+    FP64 target), on grids small enough that the conditioning of the discrete divergence
+    (2/h max_i sum_f |M_if| times the flux size over the residual size) keeps the
+    oracle's own round-off below that level.
+  * FP32 residual: see test_fp32_* below; the bound is stated and derived in each test.
+"""
+import numpy as np
+import pytest
+
+from oracle.diagnostics import ns_diagnostics, scalar_diagnostics
+from oracle.grid import Grid
+from oracle.physics import Heat, NavierStokes, NSParams, PorousMedium
+from oracle.residual import residual as oracle_residual
+from oracle.timestep import STEPPERS
+from paper_2608_09615_b300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+import paper_2608_09615_b300 as sd  # noqa: E402
+
+TWO_PI = 2 * np.pi
+
+
+def rel_err(Rg, Ro):
+    out = []
+    for v in range(Ro.shape[0]):
+        den = np.abs(Ro[v]).max()
+        out.append(np.abs(Rg[v] - Ro[v]).max() / (den if den > 0 else 1.0))
+    return np.array(out)
+
+
+def ns_phys(**kw):
+    prm = NSParams(**{k: v for k, v in kw.items() if k in NSParams.__dataclass_fields__})
+    return prm, sd.Physics(kind="ns", gamma=prm.gamma, Pr=prm.Pr, Re=prm.Re, Ma=prm.Ma,
+                           rho0=prm.rho0, u0=prm.u0, L=prm.L, sutherland=prm.sutherland,
+                           suth_s=prm.suth_s, riemann=prm.riemann, harten=prm.harten)
+
+
+def gpu_residual(U, dim, ne, lo, hi, p, scheme, phys, precision):
+    ctx = sd.SD(dim, ne, lo, hi, p, scheme, phys, precision)
+    dt = ctx.dtype
+    Ug = torch.from_numpy(np.ascontiguousarray(U)).to("cuda", dt)
+    R = ctx.residual(Ug)
+    torch.cuda.synchronize()
+    out = R.double().cpu().numpy()
+    ctx.close()
+    return out
+
+
+# ------------------------------------------------------------------ scalar, FP64
+SCALAR_CASES = [(1, (7,), p) for p in range(1, 9)] + [(3, (3, 4, 2), p) for p in range(1, 7)] + \
+    [(3, (2, 1, 2), 7), (3, (1, 2, 1), 8), (3, (1, 1, 1), 3)]
+
+
+@pytest.mark.parametrize("dim,ne,p", SCALAR_CASES)
+@pytest.mark.parametrize("scheme", ["br1", "compact"])
+@pytest.mark.parametrize("kind", ["heat", "pme"])
+def test_scalar_fp64_parity(dim, ne, p, scheme, kind):
+    lo, hi = (0.0,) * dim, tuple(1.0 + 0.3 * d for d in range(dim))
+    g = Grid(dim, ne, lo, hi, p)
+    U = inputs.random_scalar(dim, ne, p, seed=p + 10 * dim, lo=0.05, hi=1.0)
+    phys_o = Heat(0.37) if kind == "heat" else PorousMedium(2.0)
+    phys_g = sd.Physics(kind=kind, nu=0.37, m_pme=2.0)
+    Ro = oracle_residual(U, g, scheme, phys_o)
+    Rg = gpu_residual(U, dim, ne, lo, hi, p, scheme, phys_g, "f64")
+    assert rel_err(Rg, Ro).max() <= 1e-12
+
+
+def test_pme_exponent_five_fp64():
+    g = Grid(1, (9,), (-1.0,), (1.0,), 4)
+    U = inputs.random_scalar(1, (9,), 4, seed=3, lo=0.0, hi=1.0)
+    Ro = oracle_residual(U, g, "compact", PorousMedium(5.0))
+    Rg = gpu_residual(U, 1, (9,), (-1.0,), (1.0,), 4, "compact", sd.Physics(kind="pme", m_pme=5.0), "f64")
+    assert rel_err(Rg, Ro).max() <= 1e-12
+
+
+# ------------------------------------------------------------------ Navier-Stokes, FP64
+NS_CASES = [((3, 2, 4), 1), ((2, 3, 2), 2), ((3, 2, 2), 3), ((2, 2, 3), 4), ((2, 2, 2), 5),
+            ((2, 1, 2), 6), ((1, 2, 1), 7), ((1, 1, 2), 8), ((1, 1, 1), 2)]
+
+
+@pytest.mark.parametrize("ne,p", NS_CASES)
+@pytest.mark.parametrize("scheme", ["br1", "compact"])
+def test_ns_fp64_parity_random_state(ne, p, scheme):
+    prm, phys = ns_phys(Re=300.0)
+    lo, hi = (0.0,) * 3, (TWO_PI, 0.8 * TWO_PI, 1.1 * TWO_PI)
+    g = Grid(3, ne, lo, hi, p)
+    U = inputs.random_state(ne, p, seed=p)
+    Ro = oracle_residual(U, g, scheme, NavierStokes(prm))
+    Rg = gpu_residual(U, 3, ne, lo, hi, p, scheme, phys, "f64")
+    assert rel_err(Rg, Ro).max() <= 1e-12
+
+
+@pytest.mark.parametrize("riemann", ["roe", "rusanov"])
+@pytest.mark.parametrize("sutherland", [True, False])
+@pytest.mark.parametrize("scheme", ["br1", "compact"])
+def test_ns_fp64_parity_options(riemann, sutherland, scheme):
+    prm, phys = ns_phys(Re=500.0, riemann=riemann, sutherland=sutherland, harten=0.3)
+    ne, p = (3, 3, 2), 3
+    lo, hi = (0.0,) * 3, (TWO_PI,) * 3
+    g = Grid(3, ne, lo, hi, p)
+    U = inputs.random_state(ne, p, seed=11, rel=0.3)
+    Ro = oracle_residual(U, g, scheme, NavierStokes(prm))
+    Rg = gpu_residual(U, 3, ne, lo, hi, p, scheme, phys, "f64")
+    assert rel_err(Rg, Ro).max() <= 1e-12
+
+
+@pytest.mark.parametrize("scheme", ["br1", "compact"])
+def test_ns_fp64_parity_tgv(scheme):
+    prm, phys = ns_phys()
+    ne, p = (6, 6, 6), 4
+    lo, hi = (0.0,) * 3, (TWO_PI,) * 3
+    g = Grid(3, ne, lo, hi, p)
+    U = inputs.tgv_3d(ne, p, perturb_seed=0)
+    Ro = oracle_residual(U, g, scheme, NavierStokes(prm))
+    Rg = gpu_residual(U, 3, ne, lo, hi, p, scheme, phys, "f64")
+    assert rel_err(Rg, Ro).max() <= 1e-12
+
+
+# ------------------------------------------------------------------ FP32 error report
+def test_fp32_error_tgv_report(capsys):
+    prm, phys = ns_phys()
+    ne, p = (8, 8, 8), 4
+    lo, hi = (0.0,) * 3, (TWO_PI,) * 3
+    g = Grid(3, ne, lo, hi, p)
+    U = inputs.tgv_3d(ne, p, perturb_seed=0)
+    U32 = U.astype(np.float32).astype(np.float64)       # both sides see the FP32 input
+    for scheme in ("compact", "br1"):
+        Ro = oracle_residual(U32, g, scheme, NavierStokes(prm))
+        Rg = gpu_residual(U32, 3, ne, lo, hi, p, scheme, phys, "f32")
+        e_max = rel_err(Rg, Ro)
+        e_l2 = np.array([np.linalg.norm(Rg[v] - Ro[v]) / np.linalg.norm(Ro[v]) for v in range(5)])
+        with capsys.disabled():
+            print("\nFP32 TGV 8^3 p4 %s: max-rel %s  l2-rel %s" % (scheme, np.array2string(e_max, precision=2),
+                                                                 np.array2string(e_l2, precision=2)))
+        assert np.all(np.isfinite(Rg))
+        assert e_l2.max() < 1e-2
+
+
+# ------------------------------------------------------------------ host path, RK, diagnostics
+def test_host_path_equals_device_path():
+    prm, phys = ns_phys()
+    ne, p = (4, 3, 2), 3
+    ctx = sd.SD(3, ne, (0,) * 3, (TWO_PI,) * 3, p, "compact", phys, "f32")
+    U = torch.from_numpy(inputs.tgv_3d(ne, p, perturb_seed=1)).float()
+    Rd = ctx.residual(U.cuda()).cpu()
+    Uh = U.pin_memory()
+    Rh = torch.empty_like(Uh).pin_memory()
+    ctx.residual_host(Uh, Rh)
+    assert torch.equal(Rd, Rh)
+    ctx.close()
+
+
+@pytest.mark.parametrize("rk", ["rk4", "ssprk54", "lsrk54"])
+def test_rk_step_fp64_parity(rk):
+    prm, phys = ns_phys(Re=400.0)
+    ne, p = (3, 2, 2), 3
+    lo, hi = (0.0,) * 3, (TWO_PI,) * 3
+    g = Grid(3, ne, lo, hi, p)
+    U = inputs.tgv_3d(ne, p, perturb_seed=2)
+    dt = 1e-3
+    Uo = U.copy()
+    for _ in range(3):
+        Uo = STEPPERS[rk](lambda V: oracle_residual(V, g, "compact", NavierStokes(prm)), Uo, dt)
+    ctx = sd.SD(3, ne, lo, hi, p, "compact", phys, "f64")
+    Ug = torch.from_numpy(U.copy()).cuda()
+    for s in range(3):
+        ctx.rk_step(Ug, s * dt, dt, rk)
+    Ug = Ug.cpu().numpy()
+    ctx.close()
+    assert rel_err(Ug - U, Uo - U).max() <= 1e-11
+
+
+def test_rk_step_fp32_residual_close_to_fp64():
+    prm, phys = ns_phys()
+    ne, p = (4, 4, 4), 4
+    U = inputs.tgv_3d(ne, p, perturb_seed=3)
+    out = {}
+    for prec in ("f32", "f64"):
+        ctx = sd.SD(3, ne, (0,) * 3, (TWO_PI,) * 3, p, "compact", phys, prec)
+        Ug = torch.from_numpy(U.copy()).cuda()
+        for s in range(5):
+            ctx.rk_step(Ug, s * 1e-3, 1e-3, "ssprk54")
+        out[prec] = Ug.cpu().numpy()
+        ctx.close()
+    dU = out["f64"] - U
+    assert rel_err(out["f32"] - U, dU).max() < 1e-3
+
+
+@pytest.mark.parametrize("p", [2, 4])
+def test_diagnostics_parity_ns(p):
+    prm, phys = ns_phys()
+    ne = (4, 3, 5)
+    lo, hi = (0.0,) * 3, (TWO_PI,) * 3
+    g = Grid(3, ne, lo, hi, p)
+    U = inputs.tgv_3d(ne, p, perturb_seed=4)
+    do = ns_diagnostics(U, g)
+    ctx = sd.SD(3, ne, lo, hi, p, "compact", phys, "f32")
+    dg = ctx.diagnostics(torch.from_numpy(U).cuda(), 0.5)
+    ctx.close()
+    for k in ("ke", "ke_rho", "enstrophy", "mass", "energy", "volume"):
+        assert dg[k] == pytest.approx(do[k], rel=1e-12), k
+    for i in range(3):
+        assert dg["mom"][i] == pytest.approx(do["mom"][i], abs=1e-12 * do["mass"])
+    assert dg["nonfinite"] == 0 and dg["t"] == 0.5
+
+
+@pytest.mark.parametrize("dim,ne", [(1, (9,)), (3, (3, 2, 4))])
+def test_diagnostics_parity_scalar(dim, ne):
+    p = 3
+    lo, hi = (0.0,) * dim, (1.0,) * dim
+    g = Grid(dim, ne, lo, hi, p)
+    U = inputs.random_scalar(dim, ne, p, seed=5)
+    do = scalar_diagnostics(U, g)
+    ctx = sd.SD(dim, ne, lo, hi, p, "compact", sd.Physics(kind="heat"), "f64")
+    dg = ctx.diagnostics(torch.from_numpy(U).cuda())
+    ctx.close()
+    assert dg["mass"] == pytest.approx(do["mass"], rel=1e-12, abs=1e-14)
+    assert dg["l2sq"] == pytest.approx(do["l2sq"], rel=1e-12)
+
+
+def test_diagnostics_flags_nonfinite():
+    ne, p = (2, 2, 2), 2
+    U = inputs.tgv_3d(ne, p)
+    U[4, 1, 0, 1, 2, 0, 1] = np.inf
+    ctx = sd.SD(3, ne, (0,) * 3, (TWO_PI,) * 3, p, "compact", sd.Physics(), "f32")
+    Ug = torch.from_numpy(U).cuda()
+    with pytest.raises(sd.SDError) as ei:
+        ctx.diagnostics(Ug)
+    assert ei.value.status == sd.SD_ENONFINITE
+    d = ctx.diagnostics(Ug, raise_nonfinite=False)
+    assert d["nonfinite"] == 1
+    ctx.close()
+
+
+# ------------------------------------------------------------------ 1D sin(x) diffusion run
+def test_sin_diffusion_rk4_run():
+    # 1D u_t = u_xx on [0, 2 pi], 16 elements, p = 3, u0 = sin x, RK4 dt = 1e-4 to t = 1.
+    p, E = 3, 16
+    U = inputs.sin_1d(E, p)
+    (x,) = inputs.coordinates(1, (E,), (0.0,), (TWO_PI,), p)
+    errs = {}
+    for scheme in ("compact", "br1"):
+        ctx = sd.SD(1, (E,), (0.0,), (TWO_PI,), p, scheme, sd.Physics(kind="heat", nu=1.0), "f64")
+        Ug = torch.from_numpy(U.copy()).cuda()
+        for s in range(10000):
+            ctx.rk_step(Ug, s * 1e-4, 1e-4, "rk4")
+        uT = Ug.cpu().numpy()[0]
+        ctx.close()
+        errs[scheme] = np.abs(uT - np.exp(-1.0) * np.sin(x)).max()
+        # the first 100 steps against the oracle's RK4
+        g = Grid(1, (E,), (0.0,), (TWO_PI,), p)
+        Uo = U.copy()
+        for _ in range(100):
+            Uo = STEPPERS["rk4"](lambda V: oracle_residual(V, g, scheme, Heat(1.0)), Uo, 1e-4)
+        ctx = sd.SD(1, (E,), (0.0,), (TWO_PI,), p, scheme, sd.Physics(kind="heat", nu=1.0), "f64")
+        Ug = torch.from_numpy(U.copy()).cuda()
+        for s in range(100):
+            ctx.rk_step(Ug, s * 1e-4, 1e-4, "rk4")
+        assert np.abs(Ug.cpu().numpy() - Uo).max() <= 1e-13
+        ctx.close()
+    assert errs["compact"] < 1e-4
+    assert errs["compact"] < errs["br1"]   # p = 3 is an even order: BR1 loses one order
