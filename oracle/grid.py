@@ -18,7 +18,7 @@ from .operators import operators
 
 
 class Grid:
-    def __init__(self, dim, ne, lo, hi, p):
+    def __init__(self, dim, ne, lo, hi, p, dtype=np.float64):
         if dim not in (1, 2, 3):
             raise ValueError("dim must be 1, 2 or 3")
         ne = tuple(int(v) for v in ne)
@@ -30,14 +30,18 @@ class Grid:
         self.hi = tuple(float(v) for v in hi)
         self.p = int(p)
         self.n = self.p + 1
-        self.h = tuple((self.hi[d] - self.lo[d]) / self.ne[d] for d in range(dim))
-        self.ops = operators(self.n)
+        self.dtype = np.dtype(dtype)
+        self.ops = operators(self.n, dtype)
+        T = self.dtype.type
+        self.h = tuple((T(self.hi[d]) - T(self.lo[d])) / self.ne[d] for d in range(dim))
         # metric terms of the affine map (Eq. adj:f)
-        self.J = float(np.prod([hd / 2.0 for hd in self.h]))
-        self.Jinv = 1.0 / self.J
-        self.S = np.zeros((dim, dim))
+        self.J = T(1)
+        for hd in self.h:
+            self.J = self.J * (hd / 2)
+        self.Jinv = 1 / self.J
+        self.S = np.zeros((dim, dim), dtype=dtype)
         for d in range(dim):
-            self.S[d, d] = self.J / (self.h[d] / 2.0)
+            self.S[d, d] = self.J / (self.h[d] / 2)
 
     # ----- axis bookkeeping -------------------------------------------------------
     def elem_axis(self, d):

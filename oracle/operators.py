@@ -9,28 +9,52 @@ correction scalars alpha = c_L^T L M c_R = (-1)^p / 2 and beta = c_R^T L M c_L =
 import numpy as np
 
 
-def solution_points(n):
+def _gauss_legendre(n, dtype):
+    """Gauss-Legendre nodes and weights; for extended precision the float64 rule is
+    polished by Newton steps on the Legendre recurrence in that precision."""
+    x, w = np.polynomial.legendre.leggauss(n)
+    x = np.asarray(x, dtype=dtype)
+    if np.dtype(dtype) == np.float64:
+        return x, np.asarray(w, dtype=dtype)
+    one = dtype(1)
+    for _ in range(3):
+        p0, p1 = np.ones_like(x), x.copy()
+        for k in range(2, n + 1):
+            p0, p1 = p1, ((2 * k - 1) * x * p1 - (k - 1) * p0) / k
+        if n == 1:
+            p0, p1 = np.ones_like(x), x.copy()
+        dp = n * (x * p1 - p0) / (x * x - one)
+        x = x - p1 / dp
+    p0, p1 = np.ones_like(x), x.copy()
+    for k in range(2, n + 1):
+        p0, p1 = p1, ((2 * k - 1) * x * p1 - (k - 1) * p0) / k
+    if n == 1:
+        p0, p1 = np.ones_like(x), x.copy()
+    dp = n * (x * p1 - p0) / (x * x - one)
+    return x, 2 * one / ((one - x * x) * dp * dp)
+
+
+def solution_points(n, dtype=np.float64):
     """n Gauss-Legendre points on [-1, 1] and their quadrature weights
     (Sec. 2: solution points follow the n-point Gauss-Legendre rule)."""
-    x, w = np.polynomial.legendre.leggauss(n)
-    return np.asarray(x, dtype=np.float64), np.asarray(w, dtype=np.float64)
+    return _gauss_legendre(n, dtype)
 
 
-def flux_points(n):
+def flux_points(n, dtype=np.float64):
     """n+1 flux points: the Gauss-Legendre points of order n-1 plus the two end
     points -1 and +1 (Sec. 2). For n = 1 only the end points remain."""
     if n == 1:
-        inner = np.zeros(0)
+        inner = np.zeros(0, dtype=dtype)
     else:
-        inner, _ = np.polynomial.legendre.leggauss(n - 1)
-    return np.concatenate(([-1.0], np.asarray(inner, dtype=np.float64), [1.0]))
+        inner, _ = _gauss_legendre(n - 1, dtype)
+    return np.concatenate((np.array([-1], dtype=dtype), inner, np.array([1], dtype=dtype)))
 
 
 def lagrange_values(nodes, x):
     """A[i, j] = l_j(x_i), l_j the Lagrange basis polynomial on `nodes` (Eq. lagr:poly)."""
-    nodes = np.asarray(nodes, dtype=np.float64)
-    x = np.asarray(x, dtype=np.float64)
-    A = np.ones((len(x), len(nodes)))
+    nodes = np.asarray(nodes)
+    x = np.asarray(x)
+    A = np.ones((len(x), len(nodes)), dtype=nodes.dtype)
     for j in range(len(nodes)):
         for k in range(len(nodes)):
             if k != j:
@@ -43,15 +67,15 @@ def lagrange_derivatives(nodes, x):
     l_j'(x) = l_j(x) * sum_{k != j} 1/(x - x_k). Valid only where x is not a node,
     which holds for solution points against flux points (the zeros of consecutive
     Legendre polynomials interlace strictly)."""
-    nodes = np.asarray(nodes, dtype=np.float64)
-    x = np.asarray(x, dtype=np.float64)
+    nodes = np.asarray(nodes)
+    x = np.asarray(x)
     for xi in x:
         if np.min(np.abs(xi - nodes)) < 1e-14:
             raise ValueError("evaluation point coincides with a node")
     vals = lagrange_values(nodes, x)
     D = np.zeros_like(vals)
     for j in range(len(nodes)):
-        s = np.zeros(len(x))
+        s = np.zeros(len(x), dtype=nodes.dtype)
         for k in range(len(nodes)):
             if k != j:
                 s += 1.0 / (x - nodes[k])
@@ -68,19 +92,20 @@ class Operators:
     xs, ws: solution points and Gauss weights; xf: flux points.
     """
 
-    def __init__(self, n):
+    def __init__(self, n, dtype=np.float64):
         if n < 1:
             raise ValueError("n must be >= 1")
         self.n = n
         self.p = n - 1
-        self.xs, self.ws = solution_points(n)
-        self.xf = flux_points(n)
+        self.dtype = np.dtype(dtype)
+        self.xs, self.ws = solution_points(n, dtype)
+        self.xf = flux_points(n, dtype)
         self.L = lagrange_values(self.xs, self.xf)
         self.M = lagrange_derivatives(self.xf, self.xs)
-        self.cL = np.zeros(n + 1)
-        self.cL[0] = 1.0
-        self.cR = np.zeros(n + 1)
-        self.cR[n] = 1.0
+        self.cL = np.zeros(n + 1, dtype=dtype)
+        self.cL[0] = 1
+        self.cR = np.zeros(n + 1, dtype=dtype)
+        self.cR[n] = 1
 
     @property
     def alpha(self):
@@ -97,7 +122,10 @@ class Operators:
 _CACHE = {}
 
 
-def operators(n):
-    if n not in _CACHE:
-        _CACHE[n] = Operators(n)
-    return _CACHE[n]
+def operators(n, dtype=np.float64):
+    """Cached operators; dtype float64 (default) or np.longdouble (x86 80-bit extended
+    precision, used as a higher-precision evaluation of the same definition)."""
+    key = (n, np.dtype(dtype).name)
+    if key not in _CACHE:
+        _CACHE[key] = Operators(n, dtype)
+    return _CACHE[key]

@@ -46,7 +46,10 @@ def residual(U, grid: Grid, scheme, phys, return_parts=False):
     if scheme not in ("br1", "compact"):
         raise ValueError(scheme)
     U = np.asarray(U)
-    U = U.astype(np.complex128 if np.iscomplexobj(U) else np.float64)
+    if np.iscomplexobj(U):
+        U = U.astype(np.complex128)
+    else:
+        U = U.astype(grid.dtype)
     if U.shape != grid.shape(phys.nvar):
         raise ValueError("U has shape %s, expected %s" % (U.shape, grid.shape(phys.nvar)))
     ops = grid.ops

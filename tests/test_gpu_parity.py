@@ -2,10 +2,11 @@
 same seeded inputs.
 
 Tolerances:
-  * FP64 residual: max |R_gpu - R_oracle| <= 1e-12 * max |R_oracle|, per variable (the
-    FP64 target), on grids small enough that the conditioning of the discrete divergence
-    (2/h max_i sum_f |M_if| times the flux size over the residual size) keeps the
-    oracle's own round-off below that level.
+  * FP64 residual: max |R_gpu - R_ref| <= 1e-12 * max |R_ref|, per variable (the FP64
+    target). R_ref is the oracle evaluated in x86 80-bit extended precision: at Ma = 0.1
+    the momentum flux carries p0 ~ 71 while the residual is O(1), so the FP64 oracle's own
+    round-off reaches ~8e-12 on smooth Taylor-Green fields (measured against the extended
+    evaluation); the extended evaluation is the same definition with ~2000x less round-off.
   * FP32 residual: see test_fp32_* below; the bound is stated and derived in each test.
 """
 import numpy as np
@@ -41,6 +42,12 @@ def ns_phys(**kw):
                            suth_s=prm.suth_s, riemann=prm.riemann, harten=prm.harten)
 
 
+def ext_residual(U, dim, ne, lo, hi, p, scheme, phys_o):
+    """The oracle residual evaluated in extended precision (np.longdouble)."""
+    g = Grid(dim, ne, lo, hi, p, dtype=np.longdouble)
+    return oracle_residual(U, g, scheme, phys_o).astype(np.float64)
+
+
 def gpu_residual(U, dim, ne, lo, hi, p, scheme, phys, precision):
     ctx = sd.SD(dim, ne, lo, hi, p, scheme, phys, precision)
     dt = ctx.dtype
@@ -66,7 +73,7 @@ def test_scalar_fp64_parity(dim, ne, p, scheme, kind):
     U = inputs.random_scalar(dim, ne, p, seed=p + 10 * dim, lo=0.05, hi=1.0)
     phys_o = Heat(0.37) if kind == "heat" else PorousMedium(2.0)
     phys_g = sd.Physics(kind=kind, nu=0.37, m_pme=2.0)
-    Ro = oracle_residual(U, g, scheme, phys_o)
+    Ro = ext_residual(U, dim, ne, lo, hi, p, scheme, phys_o)
     Rg = gpu_residual(U, dim, ne, lo, hi, p, scheme, phys_g, "f64")
     assert rel_err(Rg, Ro).max() <= 1e-12
 
@@ -74,7 +81,7 @@ def test_scalar_fp64_parity(dim, ne, p, scheme, kind):
 def test_pme_exponent_five_fp64():
     g = Grid(1, (9,), (-1.0,), (1.0,), 4)
     U = inputs.random_scalar(1, (9,), 4, seed=3, lo=0.0, hi=1.0)
-    Ro = oracle_residual(U, g, "compact", PorousMedium(5.0))
+    Ro = ext_residual(U, 1, (9,), (-1.0,), (1.0,), 4, "compact", PorousMedium(5.0))
     Rg = gpu_residual(U, 1, (9,), (-1.0,), (1.0,), 4, "compact", sd.Physics(kind="pme", m_pme=5.0), "f64")
     assert rel_err(Rg, Ro).max() <= 1e-12
 
@@ -91,7 +98,7 @@ def test_ns_fp64_parity_random_state(ne, p, scheme):
     lo, hi = (0.0,) * 3, (TWO_PI, 0.8 * TWO_PI, 1.1 * TWO_PI)
     g = Grid(3, ne, lo, hi, p)
     U = inputs.random_state(ne, p, seed=p)
-    Ro = oracle_residual(U, g, scheme, NavierStokes(prm))
+    Ro = ext_residual(U, 3, ne, lo, hi, p, scheme, NavierStokes(prm))
     Rg = gpu_residual(U, 3, ne, lo, hi, p, scheme, phys, "f64")
     assert rel_err(Rg, Ro).max() <= 1e-12
 
@@ -105,7 +112,7 @@ def test_ns_fp64_parity_options(riemann, sutherland, scheme):
     lo, hi = (0.0,) * 3, (TWO_PI,) * 3
     g = Grid(3, ne, lo, hi, p)
     U = inputs.random_state(ne, p, seed=11, rel=0.3)
-    Ro = oracle_residual(U, g, scheme, NavierStokes(prm))
+    Ro = ext_residual(U, 3, ne, lo, hi, p, scheme, NavierStokes(prm))
     Rg = gpu_residual(U, 3, ne, lo, hi, p, scheme, phys, "f64")
     assert rel_err(Rg, Ro).max() <= 1e-12
 
@@ -117,7 +124,7 @@ def test_ns_fp64_parity_tgv(scheme):
     lo, hi = (0.0,) * 3, (TWO_PI,) * 3
     g = Grid(3, ne, lo, hi, p)
     U = inputs.tgv_3d(ne, p, perturb_seed=0)
-    Ro = oracle_residual(U, g, scheme, NavierStokes(prm))
+    Ro = ext_residual(U, 3, ne, lo, hi, p, scheme, NavierStokes(prm))
     Rg = gpu_residual(U, 3, ne, lo, hi, p, scheme, phys, "f64")
     assert rel_err(Rg, Ro).max() <= 1e-12
 

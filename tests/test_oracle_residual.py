@@ -287,3 +287,27 @@ def test_roe_flux_textbook_properties():
                                 B * np.array([1, -1, -1, -1, 1])[:, None], 0),
                        phys.convective_flux(B * np.array([1, -1, -1, -1, 1])[:, None], 0),
                        rtol=1e-12, atol=1e-12)
+
+
+# --------------------------------------------------------------- extended precision
+@pytest.mark.parametrize("scheme", SCHEMES)
+def test_extended_precision_evaluation_agrees(scheme):
+    # The same definition evaluated in np.longdouble (x86 80-bit) agrees with the float64
+    # evaluation to the float64 round-off, and its operators are exact to ~1e-18.
+    from oracle.operators import operators
+    o = operators(5, np.longdouble)
+    assert np.abs(o.M.sum(axis=1)).max() < 1e-17
+    assert np.abs(o.L.sum(axis=1) - 1).max() < 1e-18
+    ne, p = (3, 2, 3), 4
+    U = inputs.tgv_3d(ne, p, perturb_seed=5)
+    phys = NavierStokes(NSParams())
+    R64 = residual(U, Grid(3, ne, (0.0,) * 3, (2 * np.pi,) * 3, p), scheme, phys)
+    R80 = residual(U, Grid(3, ne, (0.0,) * 3, (2 * np.pi,) * 3, p, dtype=np.longdouble), scheme, phys)
+    assert R80.dtype == np.longdouble
+    for v in range(5):
+        assert np.abs(R64[v] - R80[v]).max() < 1e-10 * np.abs(R80[v]).max()
+    g = Grid(1, (8,), (-4.0,), (4.0,), 3, dtype=np.longdouble)
+    (x,) = g.coordinates()
+    u = x ** 3 - 0.5 * x
+    R = residual(u[None], g, scheme, Heat(1.0))[0]
+    assert np.abs(R[2:6] - 6 * x[2:6]).max() < 1e-15
