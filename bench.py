@@ -175,6 +175,24 @@ def run_reference(args, world):
     print(json.dumps(line), flush=True)
 
 
+def residual_only(sd, torch, args, ne, lo, hi, phys):
+    ctx = sd.SD(3, ne, lo, hi, P, args.scheme, phys, args.precision)
+    npts = int(np.prod(ne)) * (P + 1) ** 3
+    U = torch.from_numpy(inputs.tgv_3d(ne, P, perturb_seed=0)).to("cuda", ctx.dtype)
+    R = torch.empty_like(U)
+    ctx.residual(U, R)
+    torch.cuda.synchronize()
+    ctx.profile(True)
+    for _ in range(args.residual_only):
+        ctx.residual(U, R)
+    prof = ctx.profile_read()
+    ctx.close()
+    out = {k: {"ms_per_launch": ms / max(n, 1), "launches": n} for k, (ms, n) in prof.items() if n}
+    tot = sum(v["ms_per_launch"] for v in out.values())
+    print(json.dumps({"grid": ne, "p": P, "precision": args.precision, "scheme": args.scheme,
+                      "kernels": out, "residual_ms": tot, "dof_per_s": npts / (tot * 1e-3)}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -185,6 +203,10 @@ def main():
     ap.add_argument("--ne", type=int, default=NE[0])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=16, help="CPU baseline sample grid edge")
+    ap.add_argument("--residual-only", type=int, default=0, metavar="K",
+                    help="only evaluate K residuals (FP32 unless --precision f64) and print the "
+                         "per-kernel CUDA-event times; the small command used for ncu captures")
+    ap.add_argument("--precision", default="f32", choices=["f32", "f64"])
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if args.impl == "reference":
@@ -208,6 +230,9 @@ def main():
     ne = (args.ne,) * 3
     lo, hi = (0.0,) * 3, (2 * math.pi,) * 3
     phys = sd.Physics(kind="ns")
+    if args.residual_only:
+        residual_only(sd, torch, args, ne, lo, hi, phys)
+        return
     ctx = sd.SD(3, ne, lo, hi, P, args.scheme, phys, "f32")
     npts = int(np.prod(ne)) * (P + 1) ** 3
     U0 = inputs.tgv_3d(ne, P, perturb_seed=rank)

@@ -148,6 +148,35 @@ sd_status sd_profile_read(sd_ctx* ctx, double* ms, long long* launches);
 /* Total number of kernels the context has launched since sd_init. */
 long long sd_launch_count(const sd_ctx* ctx);
 
+/* ---- Per-element MLP closure network (64 -> 128 -> 128 -> 15, ReLU hidden layers) ----
+ * The paper has no learned component; this network is the sub-grid closure of the
+ * coarse Taylor-Green runs (features and targets are defined in the library's closure
+ * functions). BF16 operands on the tensor cores with FP32 accumulation; FP32 biases,
+ * FP32 master parameters and Adam moments. All buffers are device buffers owned by the
+ * caller; these calls allocate nothing and run asynchronously on `stream`.
+ * Parameter vector (FP32, sd_mlp_param_count() values, packed): W1[128][64], b1[128],
+ * W2[128][128], b2[128], W3[16][128] (row 15 zero), b3[16] (entry 15 zero). Wb: the BF16
+ * copy of the same vector (biases unused). X: BF16 [M][64]. Y, T, dY: FP32 [M][15].
+ * H: BF16 activation cache [2][M][128] written by the forward pass, read by backward. */
+int sd_mlp_param_count(void);
+/* Wb <- BF16(P). */
+sd_status sd_mlp_cast(const float* P, void* Wb, void* stream);
+/* Y = W3 relu(W2 relu(W1 x + b1) + b2) + b3 for the M rows of X; fills H. */
+sd_status sd_mlp_forward(const void* X, int M, const void* Wb, const float* P, float* Y,
+                         void* H, void* stream);
+/* Mean-squared error over the M x 15 outputs: *loss (device FP64) and dY = dL/dY.
+ * part: device FP64 scratch of 64 values (block partial sums). */
+sd_status sd_mlp_loss(const float* Y, const float* T, int M, float* dY, double* part,
+                      double* loss, void* stream);
+/* Parameter gradient grad (FP32, packed like P) of the loss whose output gradient is dY.
+ * part: device FP32 scratch of ceil(M/64) * sd_mlp_param_count() values (per-block partial
+ * gradients, summed in a fixed order). */
+sd_status sd_mlp_backward(const void* X, const void* H, const float* dY, int M, const void* Wb,
+                          float* part, float* grad, void* stream);
+/* One Adam step (step = 1, 2, ...) on the masters P with moments m1, m2; refreshes Wb. */
+sd_status sd_mlp_adam(float* P, float* m1, float* m2, const float* grad, void* Wb, int step,
+                      float lr, float b1, float b2, float eps, void* stream);
+
 const char* sd_status_str(sd_status s);
 /* Text of the last error raised on the calling thread ("" if none). */
 const char* sd_last_error(void);

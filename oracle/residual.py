@@ -36,12 +36,15 @@ def along(A, X, axis):
     return np.moveaxis(Y, 0, axis)
 
 
-def residual(U, grid: Grid, scheme, phys, return_parts=False):
+def residual(U, grid: Grid, scheme, phys, return_parts=False, tau=None):
     """du/dt at the solution points.
 
     U: array of shape grid.shape(phys.nvar), any float/complex dtype (promoted to
        float64 / complex128).
     scheme: "br1" (Sec. 2.1) or "compact" (Secs. 2.2, 2.3).
+    tau: optional per-element extra flux (nvar, E..., dim) of a learned closure (not part
+       of the paper's method; see oracle/closure.py): added to F at the element's interior
+       flux points, with the average of the two elements' values at each interface.
     """
     if scheme not in ("br1", "compact"):
         raise ValueError(scheme)
@@ -173,6 +176,13 @@ def residual(U, grid: Grid, scheme, phys, return_parts=False):
                                      uhatR[d], vr, m)
             Fm[_ix(nd, pa, 0)] = FL
             Fm[_ix(nd, pa, n)] = FR
+            if tau is not None:
+                t = tau[..., m]
+                Fm = Fm + t.reshape(t.shape + (1,) * dim)
+                tl = 0.5 * (np.roll(t, 1, axis=ea) + t) - t
+                tr = 0.5 * (t + np.roll(t, -1, axis=ea)) - t
+                Fm[_ix(nd, pa, 0)] += tl.reshape(tl.shape + (1,) * (dim - 1))
+                Fm[_ix(nd, pa, n)] += tr.reshape(tr.shape + (1,) * (dim - 1))
             Gd = Gd + S[d, m] * Fm
         G.append(Gd)
 

@@ -54,7 +54,9 @@ class _Diag(ctypes.Structure):
 
 EXPORTS = ("sd_init", "sd_destroy", "sd_set_stream", "sd_state_size", "sd_nvar", "sd_points",
            "sd_residual", "sd_residual_host", "sd_rk_step", "sd_diagnostics", "sd_status_str",
-           "sd_last_error", "sd_profile_enable", "sd_profile_read", "sd_launch_count")
+           "sd_last_error", "sd_profile_enable", "sd_profile_read", "sd_launch_count",
+           "sd_mlp_param_count", "sd_mlp_cast", "sd_mlp_forward", "sd_mlp_loss", "sd_mlp_backward",
+           "sd_mlp_adam")
 KERNEL_CLASSES = ("trace", "grad", "flux_div", "other")
 
 _lib_handle = None
@@ -101,6 +103,19 @@ def load_library(path=LIB_PATH):
     lib.sd_profile_read.restype = I
     lib.sd_launch_count.argtypes = [P]
     lib.sd_launch_count.restype = ctypes.c_longlong
+    lib.sd_mlp_param_count.argtypes = []
+    lib.sd_mlp_param_count.restype = I
+    lib.sd_mlp_cast.argtypes = [P, P, P]
+    lib.sd_mlp_cast.restype = I
+    lib.sd_mlp_forward.argtypes = [P, I, P, P, P, P, P]
+    lib.sd_mlp_forward.restype = I
+    lib.sd_mlp_loss.argtypes = [P, P, I, P, P, P, P]
+    lib.sd_mlp_loss.restype = I
+    lib.sd_mlp_backward.argtypes = [P, P, P, I, P, P, P, P]
+    lib.sd_mlp_backward.restype = I
+    lib.sd_mlp_adam.argtypes = [P, P, P, P, P, I, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                ctypes.c_float, P]
+    lib.sd_mlp_adam.restype = I
     _lib_handle = lib
     return lib
 
@@ -267,3 +282,118 @@ class SD:
             self.close()
         except Exception:
             pass
+
+
+# ---------------------------------------------------------------- MLP closure network
+MLP_IN, MLP_HID, MLP_OUT = 64, 128, 15
+
+
+def mlp_layout():
+    """Offsets of the packed parameter vector (W1, b1, W2, b2, W3 with a zero 16th row,
+    b3 with a zero 16th entry)."""
+    off = {}
+    o = 0
+    for name, size in (("W1", 128 * 64), ("b1", 128), ("W2", 128 * 128), ("b2", 128),
+                       ("W3", 16 * 128), ("b3", 16)):
+        off[name] = (o, size)
+        o += size
+    return off, o
+
+
+class MLP:
+    """Device state of the 64-128-128-15 closure network: FP32 master parameters, Adam
+    moments, the BF16 weight copy the kernels read, gradient buffers."""
+
+    def __init__(self, params=None, max_rows=4096, stream=None):
+        import torch
+        lib = load_library()
+        self.n = int(lib.sd_mlp_param_count())
+        off, total = mlp_layout()
+        assert total == self.n
+        self.off = off
+        self.P = torch.zeros(self.n, dtype=torch.float32, device="cuda")
+        if params is not None:
+            self.set_params(params)
+        self.m1 = torch.zeros_like(self.P)
+        self.m2 = torch.zeros_like(self.P)
+        self.grad = torch.zeros_like(self.P)
+        self.Wb = torch.zeros(self.n, dtype=torch.bfloat16, device="cuda")
+        self.max_rows = 0
+        self.step = 0
+        self.stream = stream
+        self._ensure(max_rows)
+        self.cast()
+
+    def _s(self):
+        return _stream_handle(self.stream)
+
+    def _ensure(self, M):
+        import torch
+        if M <= self.max_rows:
+            return
+        self.max_rows = M
+        nb = (M + 63) // 64
+        self.H = torch.empty(2 * M * 128, dtype=torch.bfloat16, device="cuda")
+        self.Y = torch.empty(M * MLP_OUT, dtype=torch.float32, device="cuda")
+        self.dY = torch.empty_like(self.Y)
+        self.part = torch.empty(nb * self.n, dtype=torch.float32, device="cuda")
+        self.lpart = torch.empty(64, dtype=torch.float64, device="cuda")
+        self.loss = torch.empty(1, dtype=torch.float64, device="cuda")
+
+    def set_params(self, params):
+        """params: list of (W, b) numpy arrays as in oracle.mlp (W of shape (out, in))."""
+        import numpy as np
+        import torch
+        flat = np.zeros(self.n, dtype=np.float32)
+        for (W, b), wn, bn in zip(params, ("W1", "W2", "W3"), ("b1", "b2", "b3")):
+            o, _ = self.off[wn]
+            flat[o:o + W.size] = np.asarray(W, dtype=np.float32).reshape(-1)
+            o, _ = self.off[bn]
+            flat[o:o + b.size] = np.asarray(b, dtype=np.float32)
+        self.P.copy_(torch.from_numpy(flat))
+
+    def get_params(self):
+        import numpy as np
+        flat = self.P.cpu().numpy()
+        out = []
+        for wn, bn, shp in (("W1", "b1", (128, 64)), ("W2", "b2", (128, 128)), ("W3", "b3", (15, 128))):
+            o, _ = self.off[wn]
+            W = flat[o:o + shp[0] * shp[1]].reshape(shp).copy()
+            o, _ = self.off[bn]
+            out.append((W, flat[o:o + shp[0]].copy()))
+        return out
+
+    def cast(self):
+        _check(load_library().sd_mlp_cast(_ptr(self.P), _ptr(self.Wb), self._s()), "sd_mlp_cast")
+
+    def forward(self, Xb):
+        """Xb: CUDA bfloat16 tensor (M, 64). Returns Y (M, 15) float32 (a view of the
+        internal buffer) and keeps the activation cache for backward()."""
+        M = int(Xb.shape[0])
+        self._ensure(M)
+        self.M = M
+        self.Xb = Xb.contiguous()
+        _check(load_library().sd_mlp_forward(_ptr(self.Xb), M, _ptr(self.Wb), _ptr(self.P),
+                                             _ptr(self.Y), _ptr(self.H), self._s()), "sd_mlp_forward")
+        return self.Y[:M * MLP_OUT].view(M, MLP_OUT)
+
+    def loss_backward(self, T):
+        """MSE loss against T (M, 15) float32 and the parameter gradient (self.grad)."""
+        M = self.M
+        T = T.contiguous()
+        lib = load_library()
+        _check(lib.sd_mlp_loss(_ptr(self.Y), _ptr(T), M, _ptr(self.dY), _ptr(self.lpart),
+                               _ptr(self.loss), self._s()), "sd_mlp_loss")
+        _check(lib.sd_mlp_backward(_ptr(self.Xb), _ptr(self.H), _ptr(self.dY), M, _ptr(self.Wb),
+                                   _ptr(self.part), _ptr(self.grad), self._s()), "sd_mlp_backward")
+        return self.loss
+
+    def adam(self, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
+        self.step += 1
+        _check(load_library().sd_mlp_adam(_ptr(self.P), _ptr(self.m1), _ptr(self.m2), _ptr(self.grad),
+                                          _ptr(self.Wb), self.step, lr, b1, b2, eps, self._s()),
+               "sd_mlp_adam")
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr())

@@ -59,7 +59,10 @@ def build(force=False, verbose=False, ptxas=False):
 
     def compile_one(src):
         obj = os.path.join(BUILD, os.path.basename(src) + ".o")
-        cmd = [nvcc] + ARCH + FLAGS + extra + ["-c", src, "-o", obj]
+        # the FP32 residual unit uses the fast single-precision division / square root
+        # (a few ulp); FP64 units keep IEEE arithmetic
+        fast = ["-use_fast_math"] if src.endswith("_f32.cu") else []
+        cmd = [nvcc] + ARCH + FLAGS + fast + extra + ["-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("nvcc failed on %s:\n%s\n%s" % (src, " ".join(cmd), r.stderr))

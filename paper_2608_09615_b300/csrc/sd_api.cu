@@ -216,11 +216,6 @@ static int ipow_h(int b, int e) {
     return r;
 }
 
-template <typename real, int N, int DIM, int NV>
-static bool smem_ok() {
-    return sdk::smem_ok_impl<real, N, DIM, NV>();
-}
-
 extern "C" sd_status sd_init(const sd_mesh* mesh, int p, sd_scheme scheme, const sd_physics* phys,
                              sd_precision prec, void* stream, sd_ctx** out) {
     g_err[0] = 0;
@@ -280,15 +275,17 @@ extern "C" sd_status sd_init(const sd_mesh* mesh, int p, sd_scheme scheme, const
     c->ntg = (size_t)c->nelem * 2 * c->dim * c->ngrad * nq;
     c->esize = prec == SD_F32 ? sizeof(float) : sizeof(double);
 
-    // shared memory feasibility of the element-staged kernels
+    // shared memory feasibility of the element-staged kernels (line layout of sd_line.cuh:
+    // per element u, two trace sets, v^S and the neighbour interface gradients)
     {
-        using namespace sdk;
-        const int n = c->n;
-        const size_t per = c->esize;
-        const int NV = c->nvar, DIM = c->dim;
-        const size_t flux = (size_t)(NV * np + 2 * 2 * DIM * NV * nq + NV * DIM * np + NV * (n + 1) * nq);
-        if (flux * per > 227 * 1024 || ((np + 31) / 32) * 32 > 1024) {
-            sdi_set_error("n = %d needs %zu bytes of shared memory per element", n, flux * per);
+        const int n = c->n, NV = c->nvar, DIM = c->dim;
+        const size_t per = (size_t)(NV * np + 2 * 2 * DIM * NV * nq + NV * DIM * np + 2 * DIM * c->ngrad * nq);
+        const int nqv = nq, epw = nqv <= 32 ? 32 / nqv : 1, wpd = nqv <= 32 ? 1 : (nqv + 31) / 32;
+        const int unit = DIM * wpd * 32, upb = unit >= 192 ? 1 : 192 / unit;
+        const size_t blk = per * (size_t)(upb * epw) * c->esize;
+        const size_t diag = (size_t)(NV * np + 2 * 2 * DIM * NV * nq + NV * DIM * np) * sizeof(double);
+        if (blk > 227 * 1024 || diag > 227 * 1024) {
+            sdi_set_error("n = %d needs %zu bytes of shared memory per block", n, blk);
             free(c);
             return SD_EUNSUPPORTED;
         }
@@ -327,6 +324,11 @@ extern "C" sd_status sd_init(const sd_mesh* mesh, int p, sd_scheme scheme, const
         free_all(c);
         free(c);
         return SD_ENOMEM;
+    }
+    if (sdi_upload_f32(c) != SD_OK || sdi_upload_f64(c) != SD_OK) {
+        free_all(c);
+        free(c);
+        return SD_ECUDA;
     }
     if (cudaMemcpy(c->dW, c->ws, c->n * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess) {
         sdi_set_error("cudaMemcpy of the Gauss weights failed");
@@ -370,9 +372,9 @@ static bool overlap(const void* a, const void* b, size_t bytes) {
     return x < y + bytes && y < x + bytes;
 }
 
-static sd_status residual_any(sd_ctx* c, const void* U, void* R) {
-    if (c->prec == SD_F32) return sdi_residual_f32(c, (const float*)U, (float*)R);
-    return sdi_residual_f64(c, (const double*)U, (double*)R);
+static sd_status residual_any(sd_ctx* c, const void* U, void* R, int offset_in = 0) {
+    if (c->prec == SD_F32) return sdi_residual_f32(c, (const float*)U, (float*)R, offset_in);
+    return sdi_residual_f64(c, (const double*)U, (double*)R, offset_in);
 }
 
 extern "C" sd_status sd_residual(sd_ctx* c, const void* U, void* R) {
@@ -405,21 +407,22 @@ static sd_status rk_step_t(sd_ctx* c, double* U, double dt, sd_rk rk) {
     real* K = (real*)c->K;
     const int gb = grid_for(n);
     cudaStream_t st = c->stream;
-    // residual of the stage input; stage 1 reads U itself (an FP32 copy when needed)
-    auto res = [&](const void* in) -> sd_status { return residual_any(c, in, K); };
-    const void* first = U;
-    if (sizeof(real) == 4) {
-        sdi_prof_begin(c, SD_K_OTHER);
-        sdk::k_to_real<real><<<gb, 256, 0, st>>>(U, S, n);
-        sdi_prof_end(c, SD_K_OTHER);
-        first = S;
-    }
+    // every stage input, the first included, is a copy in the residual precision with the
+    // reference offsets removed in FP64 before rounding
+    sdk::StageOff so;
+    so.npts = c->npts;
+    sdk::stage_offsets(c, so.off0, so.off4);
+    auto res = [&](const void* in) -> sd_status { return residual_any(c, in, K, 1); };
+    const void* first = S;
+    sdi_prof_begin(c, SD_K_OTHER);
+    sdk::k_to_real<real><<<gb, 256, 0, st>>>(U, S, n, so);
+    sdi_prof_end(c, SD_K_OTHER);
     sd_status s;
     if (rk == SD_RK4) {
         for (int k = 0; k < 4; ++k) {
             if ((s = res(k == 0 ? first : (const void*)S)) != SD_OK) return s;
             sdi_prof_begin(c, SD_K_OTHER);
-            sdk::k_rk4<real><<<gb, 256, 0, st>>>(k, U, c->rA, K, S, dt, n);
+            sdk::k_rk4<real><<<gb, 256, 0, st>>>(k, U, c->rA, K, S, dt, n, so);
             sdi_prof_end(c, SD_K_OTHER);
         }
     } else if (rk == SD_SSPRK54) {
@@ -431,7 +434,7 @@ static sd_status rk_step_t(sd_ctx* c, double* U, double dt, sd_rk rk) {
         for (int k = 0; k < 5; ++k) {
             if ((s = res(k == 0 ? first : (const void*)S)) != SD_OK) return s;
             sdi_prof_begin(c, SD_K_OTHER);
-            sdk::k_ssp<real><<<gb, 256, 0, st>>>(k, U, c->rA, c->rB, c->rC, K, S, dt, cf, n);
+            sdk::k_ssp<real><<<gb, 256, 0, st>>>(k, U, c->rA, c->rB, c->rC, K, S, dt, cf, n, so);
             sdi_prof_end(c, SD_K_OTHER);
         }
     } else if (rk == SD_LSRK54) {
@@ -447,7 +450,7 @@ static sd_status rk_step_t(sd_ctx* c, double* U, double dt, sd_rk rk) {
         for (int k = 0; k < 5; ++k) {
             if ((s = res(k == 0 ? first : (const void*)S)) != SD_OK) return s;
             sdi_prof_begin(c, SD_K_OTHER);
-            sdk::k_lsrk<real><<<gb, 256, 0, st>>>(U, c->rA, K, S, A[k], B[k], dt, n);
+            sdk::k_lsrk<real><<<gb, 256, 0, st>>>(U, c->rA, K, S, A[k], B[k], dt, n, so);
             sdi_prof_end(c, SD_K_OTHER);
         }
     } else {

@@ -1,6 +1,9 @@
-// FP32 residual instantiations (every n in 2..9, 1D/3D scalar and 3D Navier-Stokes).
+// FP32 residual instantiations (every n in 2..9, 1D/3D scalar and 3D Navier-Stokes) and
+// the upload of this translation unit's constant operator tables.
 #include "sd_launch.cuh"
 
-sd_status sdi_residual_f32(sd_ctx* c, const float* U, float* R) {
-    return sdk::residual_dispatch<float>(c, U, R);
+sd_status sdi_residual_f32(sd_ctx* c, const float* U, float* R, int offset_in) {
+    return sdk::residual_dispatch<float>(c, U, R, offset_in);
 }
+
+sd_status sdi_upload_f32(const sd_ctx* c) { return sdk::upload_dispatch<float>(c); }

@@ -1,6 +1,9 @@
-// FP64 residual instantiations (every n in 2..9, 1D/3D scalar and 3D Navier-Stokes).
+// FP64 residual instantiations (every n in 2..9, 1D/3D scalar and 3D Navier-Stokes) and
+// the upload of this translation unit's constant operator tables.
 #include "sd_launch.cuh"
 
-sd_status sdi_residual_f64(sd_ctx* c, const double* U, double* R) {
-    return sdk::residual_dispatch<double>(c, U, R);
+sd_status sdi_residual_f64(sd_ctx* c, const double* U, double* R, int offset_in) {
+    return sdk::residual_dispatch<double>(c, U, R, offset_in);
 }
+
+sd_status sdi_upload_f64(const sd_ctx* c) { return sdk::upload_dispatch<double>(c); }

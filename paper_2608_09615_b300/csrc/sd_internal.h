@@ -63,8 +63,11 @@ void sdi_prof_begin(sd_ctx* c, int k);
 void sdi_prof_end(sd_ctx* c, int k);
 
 // dispatch entry points (one translation unit per residual precision)
-sd_status sdi_residual_f32(sd_ctx* c, const float* U, float* R);
-sd_status sdi_residual_f64(sd_ctx* c, const double* U, double* R);
+// offset_in != 0: U already has the reference offsets removed (Runge-Kutta stage copies)
+sd_status sdi_residual_f32(sd_ctx* c, const float* U, float* R, int offset_in);
+sd_status sdi_residual_f64(sd_ctx* c, const double* U, double* R, int offset_in);
+sd_status sdi_upload_f32(const sd_ctx* c);
+sd_status sdi_upload_f64(const sd_ctx* c);
 sd_status sdi_diag(sd_ctx* c, const double* U64, double* host_out);
 sd_status sdi_check_smem(sd_ctx* c);
 void sdi_set_error(const char* fmt, ...);

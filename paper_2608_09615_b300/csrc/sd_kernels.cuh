@@ -1,15 +1,9 @@
 // Device code of the SD residual (Lodato & Tonicello, Secs. 2.1-2.3, 4.3, 4.4).
 //
-// Three element-local kernels evaluate one residual:
-//   k_trace    u at the 2*DIM faces of every element (Sec. 2.3 step 1, interface rows only)
-//   k_grad     common solution corrections, gradient v^S at the solution points (Eq. w:e)
-//              and the element's own interface gradient values (BR1: Eq. v:e; compact:
-//              Eqs. aux:cmp:lr:2d, aux:cmp:bt:2d in closed form, see face_grad below)
-//   k_flux_div gradient at interior flux points, interface averages (Eq. c:aux:v:2d),
-//              physical / Riemann fluxes at all flux points and the divergence (step 5)
-// Every element is staged in shared memory; 1D operators act along one direction at a
-// time (tensor-product sweeps). Values exchanged between elements go through two
-// face-trace buffers: Tu[e][face][var][q] and Tg[e][face][comp][q].
+// This header holds the physics device functions, the element staging used by the FP64
+// diagnostics, and the Runge-Kutta stage kernels. The residual kernels themselves are
+// in sd_line.cuh. Values exchanged between elements go through two face-trace buffers:
+// Tu[e][face][var][q] (traces of u) and Tg[e][face][comp][q] (own interface gradients).
 //
 // Bitwise consistency: a value computed by both elements sharing an interface (the
 // trace, the correction delta, the own-side interface gradient) is produced by the same
@@ -50,6 +44,7 @@ struct Phys {
     int riemann;             // 0 Roe, 1 Rusanov
     real nu, m_pme;
     real gamma, gm1, gamma_Pr, mu0, p0, rhoE0, inv_e0, suth_s, suth_1ps, harten;
+    real rho0, H0;           // reference offsets: rho0, rhoE0 + p0
 };
 
 struct Mesh {
@@ -120,23 +115,29 @@ __device__ __forceinline__ real sutherland_mu(const Phys<real>& P, real e) {
     return P.mu0 * th * sqrt(th) * P.suth_1ps / (th + P.suth_s);
 }
 
-// Sec. 4.4 inviscid flux along d; the momentum rows carry p - p0 (the constant p0 has
-// zero discrete divergence, so this is the same scheme with less FP32 cancellation).
+// Navier-Stokes fluxes on reference-offset states. The residual kernels stage
+// U' = (rho - rho0, rho u, rho v, rho w, rho E - rhoE0) with rhoE0 = p0/(gamma - 1): the
+// 1D operators commute with constant offsets (rows of L sum to 1, rows of D and M to 0),
+// so this is the same scheme, but the sweeps no longer carry the O(p0/(gamma-1)) constant
+// part of rho E (at Ma = 0.1 it is ~180 against O(1) variations, and its round-off in the
+// extrapolated traces was the dominant residual error). p' = p - p0 = (gamma-1)(U'_4 - rho
+// |u|^2/2) and the momentum rows carry p' (the constant p0 has zero discrete divergence).
+
+// Sec. 4.4 inviscid flux along d (F_c), offset state
 template <typename real>
 __device__ __forceinline__ void ns_convective(const real* U, int d, const Phys<real>& P,
                                               real* F) {
-    const real ir = real(1) / U[0];
+    const real ir = real(1) / (U[0] + P.rho0);
     const real v0 = U[1] * ir, v1 = U[2] * ir, v2 = U[3] * ir;
     const real ke2 = U[1] * v0 + U[2] * v1 + U[3] * v2;        // rho |u|^2
-    const real pp = P.gm1 * ((U[4] - P.rhoE0) - real(0.5) * ke2);   // p - p0
-    const real p = pp + P.p0;
+    const real pp = P.gm1 * (U[4] - real(0.5) * ke2);          // p - p0
     const real ud = (d == 0) ? v0 : (d == 1 ? v1 : v2);
     F[0] = U[1 + d];
     F[1] = U[1] * ud;
     F[2] = U[2] * ud;
     F[3] = U[3] * ud;
     F[1 + d] += pp;
-    F[4] = (U[4] + p) * ud;
+    F[4] = ((U[4] + pp) + P.H0) * ud;                          // (rho E + p) u_d
 }
 
 // Sec. 4.4 viscous flux along d from the 9 exchanged conservative-gradient components g
@@ -145,9 +146,9 @@ __device__ __forceinline__ void ns_convective(const real* U, int d, const Phys<r
 template <typename real>
 __device__ __forceinline__ void ns_viscous(const real* U, const real* g, int d,
                                            const Phys<real>& P, real* Fv) {
-    const real ir = real(1) / U[0];
+    const real ir = real(1) / (U[0] + P.rho0);
     const real vel[3] = {U[1] * ir, U[2] * ir, U[3] * ir};
-    const real E = U[4] * ir;
+    const real E = (U[4] + P.rhoE0) * ir;
     const real e = E - real(0.5) * (vel[0] * vel[0] + vel[1] * vel[1] + vel[2] * vel[2]);
     const real mu = sutherland_mu(P, e);
     real dud[3];
@@ -170,36 +171,39 @@ __device__ __forceinline__ void ns_viscous(const real* U, const real* g, int d,
     Fv[4] = vel[0] * tau[0] + vel[1] * tau[1] + vel[2] * tau[2] + mu * P.gamma_Pr * de;
 }
 
-// Roe flux with Harten's fix on the acoustic eigenvalues (Sec. 4.4), or Rusanov.
+// Roe flux with Harten's fix on the acoustic eigenvalues (Sec. 4.4), or Rusanov; offset
+// states (jumps and p' differences are offset-free)
 template <typename real>
 __device__ __forceinline__ void ns_riemann(const real* UL, const real* UR, int d,
                                            const Phys<real>& P, real* F) {
-    real FL[5], FR[5];
-    ns_convective(UL, d, P, FL);
-    ns_convective(UR, d, P, FR);
-    const real irl = real(1) / UL[0], irr = real(1) / UR[0];
+    // central part first: F = (F_c(U_L) + F_c(U_R)) / 2
+    ns_convective(UL, d, P, F);
+    {
+        real FR[5];
+        ns_convective(UR, d, P, FR);
+#pragma unroll
+        for (int k = 0; k < 5; ++k) F[k] = real(0.5) * (F[k] + FR[k]);
+    }
+    const real rl = UL[0] + P.rho0, rr = UR[0] + P.rho0;
+    const real irl = real(1) / rl, irr = real(1) / rr;
     const real vl[3] = {UL[1] * irl, UL[2] * irl, UL[3] * irl};
     const real vr[3] = {UR[1] * irr, UR[2] * irr, UR[3] * irr};
-    const real ppl = P.gm1 * ((UL[4] - P.rhoE0) -
-                              real(0.5) * (UL[1] * vl[0] + UL[2] * vl[1] + UL[3] * vl[2]));
-    const real ppr = P.gm1 * ((UR[4] - P.rhoE0) -
-                              real(0.5) * (UR[1] * vr[0] + UR[2] * vr[1] + UR[3] * vr[2]));
-    const real pl = ppl + P.p0, pr = ppr + P.p0;
+    const real ppl = P.gm1 * (UL[4] - real(0.5) * (UL[1] * vl[0] + UL[2] * vl[1] + UL[3] * vl[2]));
+    const real ppr = P.gm1 * (UR[4] - real(0.5) * (UR[1] * vr[0] + UR[2] * vr[1] + UR[3] * vr[2]));
     if (P.riemann == 1) {
-        const real cl = sqrt(P.gamma * pl * irl), cr = sqrt(P.gamma * pr * irr);
+        const real cl = sqrt(P.gamma * (ppl + P.p0) * irl), cr = sqrt(P.gamma * (ppr + P.p0) * irr);
         const real sl = fabs(vl[d]) + cl, sr = fabs(vr[d]) + cr;
         const real smax = sl > sr ? sl : sr;
 #pragma unroll
-        for (int k = 0; k < 5; ++k) F[k] = real(0.5) * (FL[k] + FR[k]) - real(0.5) * smax * (UR[k] - UL[k]);
+        for (int k = 0; k < 5; ++k) F[k] -= real(0.5) * smax * (UR[k] - UL[k]);
         return;
     }
-    const real Hl = (UL[4] + pl) * irl, Hr = (UR[4] + pr) * irr;
-    const real sl = sqrt(UL[0]), sr = sqrt(UR[0]);
+    const real sl = sqrt(rl), sr = sqrt(rr);
     const real iw = real(1) / (sl + sr);
+    const real Ht = (sl * (((UL[4] + ppl) + P.H0) * irl) + sr * (((UR[4] + ppr) + P.H0) * irr)) * iw;
     real ut[3];
 #pragma unroll
     for (int i = 0; i < 3; ++i) ut[i] = (sl * vl[i] + sr * vr[i]) * iw;
-    const real Ht = (sl * Hl + sr * Hr) * iw;
     const real rt = sl * sr;
     const real q2 = ut[0] * ut[0] + ut[1] * ut[1] + ut[2] * ut[2];
     const real c2 = P.gm1 * (Ht - real(0.5) * q2);
@@ -221,21 +225,19 @@ __device__ __forceinline__ void ns_riemann(const real* UL, const real* UR, int d
     const real a1 = (dp - rt * c * dvn) * real(0.5) * ic2;
     const real a2 = drho - dp * ic2;
     const real a5 = (dp + rt * c * dvn) * real(0.5) * ic2;
-    const real w1 = l1 * a1, w2 = l2 * a2, w5 = l5 * a5, ws = l2 * rt;
-    real dvt[3];
-#pragma unroll
-    for (int i = 0; i < 3; ++i) dvt[i] = dv[i] - (i == d ? dvn : real(0));
-    real diss[5];
-    diss[0] = w1 + w2 + w5;
+    // half of the dissipation sum_k |lambda_k| alpha_k r_k, subtracted component by component
+    const real w1 = real(0.5) * l1 * a1, w2 = real(0.5) * l2 * a2, w5 = real(0.5) * l5 * a5;
+    const real ws = real(0.5) * l2 * rt;
+    F[0] -= w1 + w2 + w5;
+    real utdvt = real(0);
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
+        const real dvt = dv[i] - (i == d ? dvn : real(0));
         const real en = (i == d) ? c : real(0);
-        diss[1 + i] = w1 * (ut[i] - en) + w2 * ut[i] + w5 * (ut[i] + en) + ws * dvt[i];
+        F[1 + i] -= w1 * (ut[i] - en) + w2 * ut[i] + w5 * (ut[i] + en) + ws * dvt;
+        utdvt += ut[i] * dvt;
     }
-    diss[4] = w1 * (Ht - qn * c) + w2 * real(0.5) * q2 + w5 * (Ht + qn * c) +
-              ws * (ut[0] * dvt[0] + ut[1] * dvt[1] + ut[2] * dvt[2]);
-#pragma unroll
-    for (int k = 0; k < 5; ++k) F[k] = real(0.5) * (FL[k] + FR[k]) - real(0.5) * diss[k];
+    F[4] -= w1 * (Ht - qn * c) + w2 * real(0.5) * q2 + w5 * (Ht + qn * c) + ws * utdvt;
 }
 
 // scalar diffusion flux (heat: -nu v_d; PME: -m |u|^(m-1) v_d, Eq. pme)
@@ -362,156 +364,6 @@ __global__ void k_trace(const real* __restrict__ U, real* __restrict__ Tu, Ops<r
     }
 }
 
-template <typename real, int N, int DIM, int NV>
-__global__ void __launch_bounds__(Footprint<N, DIM, NV>::MAXT) k_grad(const real* __restrict__ U, const real* __restrict__ Tu,
-                       real* __restrict__ Tg, Ops<real, N> ops, Mesh g, int compact) {
-    using FP = Footprint<N, DIM, NV>;
-    constexpr int NQ = FP::NQ, NF = FP::NF, TPE = FP::TPE;
-    constexpr int NG = NumGrad<NV>::value;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    real* sm = reinterpret_cast<real*>(smem_raw);
-    const int le = threadIdx.x / TPE, tid = threadIdx.x - le * TPE;
-    const int epb = blockDim.x / TPE;
-    const int e = blockIdx.x * epb + le;
-    const bool valid = e < g.nelem;
-    real* base = sm + le * FP::grad;
-    real* su = base;
-    real* tro = su + FP::U;
-    real* trn = tro + FP::TR;
-    real* vS = trn + FP::TR;
-    stage_element<real, N, DIM, NV>(U, Tu, ops, g, e, valid, tid, su, tro, trn, vS);
-    if (!valid) return;
-    for (int k = tid; k < NF * NG * NQ; k += TPE) {
-        const int f = k / (NG * NQ);
-        const int rem = k - f * NG * NQ;
-        const int c = rem / NQ, q = rem - c * NQ;
-        Tg[(size_t)e * NF * NG * NQ + k] =
-            face_grad<real, N, DIM, NV>(ops, compact, f, c, q, vS, tro, trn);
-    }
-}
-
-template <typename real, int N, int DIM, int NV>
-__global__ void __launch_bounds__(Footprint<N, DIM, NV>::MAXT) k_flux_div(const real* __restrict__ U, const real* __restrict__ Tu,
-                           const real* __restrict__ Tg, real* __restrict__ R, Ops<real, N> ops,
-                           Mesh g, Phys<real> P, int compact) {
-    using FP = Footprint<N, DIM, NV>;
-    constexpr int NP = FP::NP, NQ = FP::NQ, NF = FP::NF, TPE = FP::TPE;
-    constexpr int NG = NumGrad<NV>::value;
-    constexpr int NIT = (NV * NP + TPE - 1) / TPE;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    real* sm = reinterpret_cast<real*>(smem_raw);
-    const int le = threadIdx.x / TPE, tid = threadIdx.x - le * TPE;
-    const int epb = blockDim.x / TPE;
-    const int e = blockIdx.x * epb + le;
-    const bool valid = e < g.nelem;
-    real* base = sm + le * FP::flux;
-    real* su = base;
-    real* tro = su + FP::U;
-    real* trn = tro + FP::TR;
-    real* vS = trn + FP::TR;
-    real* G = vS + FP::VS;
-    stage_element<real, N, DIM, NV>(U, Tu, ops, g, e, valid, tid, su, tro, trn, vS);
-
-    real racc[NIT];
-#pragma unroll
-    for (int k = 0; k < NIT; ++k) racc[k] = real(0);
-
-#pragma unroll 1
-    for (int d = 0; d < DIM; ++d) {
-        const int stride = npow<N>(d);
-        if (valid) {
-            for (int k = tid; k < (N + 1) * NQ; k += TPE) {
-                const int f = k / NQ, q = k - f * NQ;
-                real F[NV];
-                if (f > 0 && f < N) {
-                    // interior flux point: extrapolated solution and gradient (Eq. aux:v:std:2d)
-                    const real* Lr = ops.L + f * N;
-                    real uf[NV], gr[NG];
-#pragma unroll
-                    for (int v = 0; v < NV; ++v)
-                        uf[v] = line_dot<real, N>(Lr, su + v * NP + pt_of<N>(d, 0, q), stride);
-#pragma unroll
-                    for (int c = 0; c < NG; ++c) {
-                        int v, m;
-                        comp_map<NV>(d, c, v, m);
-                        gr[c] = line_dot<real, N>(Lr, vS + (v * DIM + m) * NP + pt_of<N>(d, 0, q), stride);
-                    }
-                    if constexpr (NV == 5) {
-                        real Fv[5];
-                        ns_convective(uf, d, P, F);
-                        ns_viscous(uf, gr, d, P, Fv);
-#pragma unroll
-                        for (int v = 0; v < NV; ++v) F[v] -= Fv[v];
-                    } else {
-                        F[0] = scalar_flux(P, uf[0], gr[0]);
-                    }
-                } else {
-                    // interface flux point: common solution, averaged gradient, Riemann flux
-                    const int s = (f == N) ? 1 : 0;
-                    const int face = 2 * d + s;
-                    const int en = neighbour(g, e, d, s);
-                    real UL[NV], UR[NV], Uh[NV], vh[NG];
-#pragma unroll
-                    for (int v = 0; v < NV; ++v) {
-                        const real own = tro[(face * NV + v) * NQ + q];
-                        const real nb = trn[(face * NV + v) * NQ + q];
-                        UL[v] = s ? own : nb;
-                        UR[v] = s ? nb : own;
-                        Uh[v] = real(0.5) * (UL[v] + UR[v]);
-                    }
-#pragma unroll
-                    for (int c = 0; c < NG; ++c) {
-                        const real go = face_grad<real, N, DIM, NV>(ops, compact, face, c, q, vS, tro, trn);
-                        const real gn = Tg[(((size_t)en * NF + (face ^ 1)) * NG + c) * NQ + q];
-                        vh[c] = s ? real(0.5) * (go + gn) : real(0.5) * (gn + go);
-                    }
-                    if constexpr (NV == 5) {
-                        real Fv[5];
-                        ns_riemann(UL, UR, d, P, F);
-                        ns_viscous(Uh, vh, d, P, Fv);
-#pragma unroll
-                        for (int v = 0; v < NV; ++v) F[v] -= Fv[v];
-                    } else {
-                        F[0] = scalar_flux(P, Uh[0], vh[0]);
-                    }
-                }
-#pragma unroll
-                for (int v = 0; v < NV; ++v) G[(v * (N + 1) + f) * NQ + q] = F[v];
-            }
-        }
-        __syncthreads();
-        if (valid) {
-            // step 5: dq/dt = -sum_d M_d G^{Fd}, with J^-1 S_dd = 2/h_d
-#pragma unroll
-            for (int it = 0; it < NIT; ++it) {
-                const int k = tid + it * TPE;
-                if (k < NV * NP) {
-                    const int v = k / NP, pt = k - v * NP;
-                    const int i = (pt / stride) % N;
-                    const int q = (pt % stride) + stride * (pt / (stride * N));
-                    const real* Gl = G + v * (N + 1) * NQ + q;
-                    const real* Mr = ops.M + i * (N + 1);
-                    real s = Mr[0] * Gl[0];
-#pragma unroll
-                    for (int f = 1; f <= N; ++f) s = fma(Mr[f], Gl[f * NQ], s);
-                    racc[it] = fma(-ops.two_h[d], s, racc[it]);
-                }
-            }
-        }
-        __syncthreads();
-    }
-    if (valid) {
-#pragma unroll
-        for (int it = 0; it < NIT; ++it) {
-            const int k = tid + it * TPE;
-            if (k < NV * NP) {
-                const int v = k / NP, pt = k - v * NP;
-                R[(size_t)v * g.nelem * NP + (size_t)e * NP + pt] = racc[it];
-            }
-        }
-    }
-}
-
 // ------------------------------------------------------------------ diagnostics (FP64)
 // Sums, per block, of the Gauss-weighted integrands of Sec. 4.4 plus conserved totals;
 // k_diag_final adds the block partials in a fixed order (deterministic).
@@ -596,32 +448,45 @@ __global__ void k_diag_final(const double* __restrict__ partial, int nblocks,
                              double* __restrict__ out);
 
 // ------------------------------------------------------------------ Runge-Kutta (FP64)
-// out_real = shadow of a FP64 array in the residual precision
+// Stage inputs of the residual are written in the residual precision and with the
+// reference offsets of the first and last variable removed (rho - rho0, rho E - rhoE0 for
+// Navier-Stokes; zero offsets otherwise), in FP64 before rounding.
+struct StageOff {
+    size_t npts;      // values per variable
+    double off0, off4;
+};
+
+__device__ __forceinline__ double stage_offset(const StageOff& o, size_t i) {
+    return i < o.npts ? o.off0 : (i >= 4 * o.npts ? o.off4 : 0.0);
+}
+
 template <typename real>
-__global__ void k_to_real(const double* __restrict__ x, real* __restrict__ y, size_t n) {
+__global__ void k_to_real(const double* __restrict__ x, real* __restrict__ y, size_t n, StageOff o) {
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (size_t)gridDim.x * blockDim.x)
-        y[i] = (real)x[i];
+        y[i] = (real)(x[i] - stage_offset(o, i));
 }
 
 // RK4 stage k (0..3): K holds R(stage input). Uacc accumulates the weighted stages; S is
 // the next stage input (residual precision); the last stage writes U.
 template <typename real>
 __global__ void k_rk4(int k, double* __restrict__ U, double* __restrict__ Uacc,
-                      const real* __restrict__ K, real* __restrict__ S, double dt, size_t n) {
+                      const real* __restrict__ K, real* __restrict__ S, double dt, size_t n,
+                      StageOff o) {
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (size_t)gridDim.x * blockDim.x) {
         const double u = U[i];
         const double kk = (double)K[i];
+        const double off = stage_offset(o, i);
         if (k == 0) {
             Uacc[i] = u + dt / 6.0 * kk;
-            S[i] = (real)(u + 0.5 * dt * kk);
+            S[i] = (real)(u + 0.5 * dt * kk - off);
         } else if (k == 1) {
             Uacc[i] += dt / 3.0 * kk;
-            S[i] = (real)(u + 0.5 * dt * kk);
+            S[i] = (real)(u + 0.5 * dt * kk - off);
         } else if (k == 2) {
             Uacc[i] += dt / 3.0 * kk;
-            S[i] = (real)(u + dt * kk);
+            S[i] = (real)(u + dt * kk - off);
         } else {
             U[i] = Uacc[i] + dt / 6.0 * kk;
         }
@@ -637,28 +502,29 @@ struct SSPCoef {
 template <typename real>
 __global__ void k_ssp(int k, double* __restrict__ U, double* __restrict__ A,
                       double* __restrict__ B, double* __restrict__ C, const real* __restrict__ K,
-                      real* __restrict__ S, double dt, SSPCoef c, size_t n) {
+                      real* __restrict__ S, double dt, SSPCoef c, size_t n, StageOff o) {
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (size_t)gridDim.x * blockDim.x) {
         const double kk = dt * (double)K[i];
+        const double off = stage_offset(o, i);
         if (k == 0) {
             const double u1 = U[i] + c.a10 * kk;
             A[i] = u1;
-            S[i] = (real)u1;
+            S[i] = (real)(u1 - off);
         } else if (k == 1) {
             const double u2 = c.a20 * U[i] + c.a21 * A[i] + c.b21 * kk;
             B[i] = u2;
-            S[i] = (real)u2;
+            S[i] = (real)(u2 - off);
         } else if (k == 2) {
             const double u3 = c.a30 * U[i] + c.a32 * B[i] + c.b32 * kk;
             A[i] = u3;
-            S[i] = (real)u3;
+            S[i] = (real)(u3 - off);
         } else if (k == 3) {
             const double u3 = A[i];
             C[i] = c.a52 * B[i] + c.a53 * u3 + c.b53 * kk;
             const double u4 = c.a40 * U[i] + c.a43 * u3 + c.b43 * kk;
             A[i] = u4;
-            S[i] = (real)u4;
+            S[i] = (real)(u4 - off);
         } else {
             U[i] = C[i] + c.a54 * A[i] + c.b54 * kk;
         }
@@ -668,14 +534,14 @@ __global__ void k_ssp(int k, double* __restrict__ U, double* __restrict__ A,
 // LSRK(5,4) of Carpenter & Kennedy: dU <- a dU + dt K; U <- U + b dU.
 template <typename real>
 __global__ void k_lsrk(double* __restrict__ U, double* __restrict__ dU, const real* __restrict__ K,
-                       real* __restrict__ S, double a, double b, double dt, size_t n) {
+                       real* __restrict__ S, double a, double b, double dt, size_t n, StageOff o) {
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (size_t)gridDim.x * blockDim.x) {
         const double du = a * dU[i] + dt * (double)K[i];
         dU[i] = du;
         const double u = U[i] + b * du;
         U[i] = u;
-        S[i] = (real)u;
+        S[i] = (real)(u - stage_offset(o, i));
     }
 }
 

@@ -2,9 +2,11 @@
 #pragma once
 
 #include <algorithm>
+#include <mutex>
 
 #include "sd_internal.h"
 #include "sd_kernels.cuh"
+#include "sd_line.cuh"
 
 namespace sdk {
 
@@ -46,7 +48,71 @@ static Phys<real> make_phys(const sd_ctx* c) {
     P.suth_s = (real)s.suth_s;
     P.suth_1ps = (real)(1.0 + s.suth_s);
     P.harten = (real)s.harten;
+    P.rho0 = (real)(s.kind == SD_NS ? s.rho0 : 0.0);
+    P.H0 = (real)(p0 / (gamma - 1.0) + p0);
     return P;
+}
+
+// reference offsets removed from variables 0 and 4 when the residual kernels stage a
+// Navier-Stokes state (zero for scalar physics)
+inline void stage_offsets(const sd_ctx* c, double& off0, double& off4) {
+    off0 = off4 = 0.0;
+    if (c->phys.kind == SD_NS) {
+        const double p0 = c->phys.rho0 * (c->phys.u0 / c->phys.Ma) * (c->phys.u0 / c->phys.Ma) / c->phys.gamma;
+        off0 = c->phys.rho0;
+        off4 = p0 / (c->phys.gamma - 1.0);
+    }
+}
+
+template <typename real>
+static LineGeo<real> make_geo(const sd_ctx* c, int offset_in) {
+    LineGeo<real> o;
+    for (int d = 0; d < 3; ++d) {
+        const double th = d < c->dim ? 2.0 / c->h[d] : 0.0;
+        o.two_h[d] = (real)th;
+        o.corrL[d] = (real)(th * c->alpha);
+        o.corrR[d] = (real)(th * c->beta);
+    }
+    double off0, off4;
+    stage_offsets(c, off0, off4);
+    o.off0 = offset_in ? real(0) : (real)off0;
+    o.off4 = offset_in ? real(0) : (real)off4;
+    return o;
+}
+
+// upload the 1D operators of n = N to this translation unit's constant table on the
+// current device (once per device and n)
+template <typename real, int N>
+static sd_status upload_ops(const sd_ctx* c) {
+    static std::mutex mu;
+    static bool done[64] = {false};
+    std::lock_guard<std::mutex> lock(mu);
+    if (c->device >= 0 && c->device < 64 && done[c->device]) return SD_OK;
+    OpTab<real, N> t;
+    for (int k = 0; k < (N + 1) * N; ++k) t.L[k] = (real)c->L[k];
+    for (int k = 0; k < N * (N + 1); ++k) t.M[k] = (real)c->M[k];
+    for (int k = 0; k < N * N; ++k) t.D[k] = (real)c->D[k];
+    if (cudaMemcpyToSymbol(c_op<real, N>, &t, sizeof(t)) != cudaSuccess) {
+        sdi_set_error("upload of the operator table failed");
+        return SD_ECUDA;
+    }
+    if (c->device >= 0 && c->device < 64) done[c->device] = true;
+    return SD_OK;
+}
+
+template <typename real>
+static sd_status upload_dispatch(const sd_ctx* c) {
+    switch (c->n) {
+        case 2: return upload_ops<real, 2>(c);
+        case 3: return upload_ops<real, 3>(c);
+        case 4: return upload_ops<real, 4>(c);
+        case 5: return upload_ops<real, 5>(c);
+        case 6: return upload_ops<real, 6>(c);
+        case 7: return upload_ops<real, 7>(c);
+        case 8: return upload_ops<real, 8>(c);
+        case 9: return upload_ops<real, 9>(c);
+        default: return SD_EUNSUPPORTED;
+    }
 }
 
 inline Mesh make_mesh(const sd_ctx* c) {
@@ -77,33 +143,29 @@ inline int trace_blocks(long long total) {
 }
 
 template <typename real, int N, int DIM, int NV>
-static sd_status residual_impl(sd_ctx* c, const real* U, real* R) {
-    using FP = Footprint<N, DIM, NV>;
-    const Ops<real, N> ops = make_ops<real, N>(c);
+static sd_status residual_impl(sd_ctx* c, const real* U, real* R, int offset_in) {
+    using LL = LineLayout<N, DIM, NV>;
+    const LineGeo<real> geo = make_geo<real>(c, offset_in);
     const Mesh g = make_mesh(c);
     const Phys<real> P = make_phys<real>(c);
     const int compact = c->scheme == SD_COMPACT ? 1 : 0;
     real* Tu = static_cast<real*>(c->Tu);
     real* Tg = static_cast<real*>(c->Tg);
-    const long long ntr = (long long)g.nelem * FP::NF * NV * FP::NQ;
+    const int blocks = (g.nelem + LL::EB - 1) / LL::EB;
+    const size_t st = (size_t)LL::EB * LL::PER_TRACE * sizeof(real);
+    const size_t sg = LL::NBR_BYTES + (size_t)LL::EB * LL::PER_GRAD * sizeof(real);
+    const size_t sf = LL::NBR_BYTES + (size_t)LL::EB * LL::PER_FLUX * sizeof(real);
+    if (!set_smem(k_line_trace<real, N, DIM, NV>, st) || !set_smem(k_line_grad<real, N, DIM, NV>, sg) ||
+        !set_smem(k_line_flux<real, N, DIM, NV>, sf))
+        return SD_EUNSUPPORTED;
     sdi_prof_begin(c, SD_K_TRACE);
-    k_trace<real, N, DIM, NV><<<trace_blocks(ntr), 256, 0, c->stream>>>(U, Tu, ops, g);
+    k_line_trace<real, N, DIM, NV><<<blocks, LL::THREADS, st, c->stream>>>(U, Tu, geo, g);
     sdi_prof_end(c, SD_K_TRACE);
-
-    const size_t bg = FP::grad * sizeof(real);
-    const int eg = pick_epb(FP::TPE, bg);
-    if (!set_smem(k_grad<real, N, DIM, NV>, eg * bg)) return SD_EUNSUPPORTED;
     sdi_prof_begin(c, SD_K_GRAD);
-    k_grad<real, N, DIM, NV><<<(g.nelem + eg - 1) / eg, eg * FP::TPE, eg * bg, c->stream>>>(
-        U, Tu, Tg, ops, g, compact);
+    k_line_grad<real, N, DIM, NV><<<blocks, LL::THREADS, sg, c->stream>>>(U, Tu, Tg, geo, g, compact);
     sdi_prof_end(c, SD_K_GRAD);
-
-    const size_t bf = FP::flux * sizeof(real);
-    const int ef = pick_epb(FP::TPE, bf);
-    if (!set_smem(k_flux_div<real, N, DIM, NV>, ef * bf)) return SD_EUNSUPPORTED;
     sdi_prof_begin(c, SD_K_FLUX);
-    k_flux_div<real, N, DIM, NV><<<(g.nelem + ef - 1) / ef, ef * FP::TPE, ef * bf, c->stream>>>(
-        U, Tu, Tg, R, ops, g, P, compact);
+    k_line_flux<real, N, DIM, NV><<<blocks, LL::THREADS, sf, c->stream>>>(U, Tu, Tg, R, geo, g, P, compact);
     sdi_prof_end(c, SD_K_FLUX);
     const cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) {
@@ -114,32 +176,25 @@ static sd_status residual_impl(sd_ctx* c, const real* U, real* R) {
 }
 
 template <typename real, int N>
-static sd_status residual_n(sd_ctx* c, const real* U, real* R) {
-    if (c->nvar == 5) return residual_impl<real, N, 3, 5>(c, U, R);
-    if (c->dim == 1) return residual_impl<real, N, 1, 1>(c, U, R);
-    return residual_impl<real, N, 3, 1>(c, U, R);
+static sd_status residual_n(sd_ctx* c, const real* U, real* R, int offset_in) {
+    if (c->nvar == 5) return residual_impl<real, N, 3, 5>(c, U, R, offset_in);
+    if (c->dim == 1) return residual_impl<real, N, 1, 1>(c, U, R, offset_in);
+    return residual_impl<real, N, 3, 1>(c, U, R, offset_in);
 }
 
 template <typename real>
-static sd_status residual_dispatch(sd_ctx* c, const real* U, real* R) {
+static sd_status residual_dispatch(sd_ctx* c, const real* U, real* R, int offset_in) {
     switch (c->n) {
-        case 2: return residual_n<real, 2>(c, U, R);
-        case 3: return residual_n<real, 3>(c, U, R);
-        case 4: return residual_n<real, 4>(c, U, R);
-        case 5: return residual_n<real, 5>(c, U, R);
-        case 6: return residual_n<real, 6>(c, U, R);
-        case 7: return residual_n<real, 7>(c, U, R);
-        case 8: return residual_n<real, 8>(c, U, R);
-        case 9: return residual_n<real, 9>(c, U, R);
+        case 2: return residual_n<real, 2>(c, U, R, offset_in);
+        case 3: return residual_n<real, 3>(c, U, R, offset_in);
+        case 4: return residual_n<real, 4>(c, U, R, offset_in);
+        case 5: return residual_n<real, 5>(c, U, R, offset_in);
+        case 6: return residual_n<real, 6>(c, U, R, offset_in);
+        case 7: return residual_n<real, 7>(c, U, R, offset_in);
+        case 8: return residual_n<real, 8>(c, U, R, offset_in);
+        case 9: return residual_n<real, 9>(c, U, R, offset_in);
         default: return SD_EUNSUPPORTED;
     }
-}
-
-// shared-memory feasibility of every kernel of this configuration (checked at init)
-template <typename real, int N, int DIM, int NV>
-static bool smem_ok_impl() {
-    using FP = Footprint<N, DIM, NV>;
-    return FP::flux * sizeof(real) <= 227 * 1024 && FP::TPE <= 1024;
 }
 
 }  // namespace sdk

@@ -1,0 +1,499 @@
+// Line-blocked residual kernels (the production path of sd_residual).
+//
+// Work decomposition. A block holds EB elements in shared memory. Direction-structured
+// phases assign one warp (WPD warps when a face has more than 32 points) per direction
+// per element group; inside it each lane owns one line of n points along that direction
+// (lanes index the face point q, and for small n several elements share a warp). The
+// direction is a template parameter, so every index into the per-thread arrays below is a
+// compile-time constant and the arrays live in registers. A lane loads its line once and
+// produces all n+1 flux-point values, the fluxes there and the divergence contribution
+// to the n points of the line. The flux-point loop is not unrolled (its operator rows
+// come from constant memory), which keeps one copy of the flux code per direction.
+//
+// Kernels per residual (Sec. 2.3 steps 1-5):
+//   k_line_trace  u at the 2*DIM faces (step 1, interface rows)            -> Tu
+//   k_line_grad   common-solution corrections, v^S (Eq. w:e), own interface
+//                 gradients (BR1 Eq. v:e / compact closed form)            -> Tg
+//   k_line_flux   interior gradients (Eq. aux:v:std:2d), interface averages
+//                 (Eq. c:aux:v:2d), fluxes (Sec. 4.4 / Eq. pme), divergence -> R
+// The three directions of k_line_flux add into R in the fixed order x, y, z, so results
+// are deterministic. Values that both elements of an interface compute (traces, delta,
+// own interface gradients) come from the same device functions with explicit fma
+// sequences, so the interface flux is single-valued and conservation holds to round-off.
+//
+// Navier-Stokes states are staged with the reference offsets removed from rho and rho E
+// (see ns_convective); Tu holds traces of the offset state.
+#pragma once
+
+#include "sd_kernels.cuh"
+
+// Minimum resident blocks per SM requested for k_line_flux (caps its registers; 3 blocks of
+// 192 threads measured fastest for the FP32 Navier-Stokes n = 5 case on B300).
+#ifndef SD_FLUX_MINB
+#define SD_FLUX_MINB 3
+#endif
+
+namespace sdk {
+
+// 1D operators of one n, in constant memory (uploaded once per device by the
+// translation unit that launches the kernels).
+template <typename real, int N>
+struct OpTab {
+    real L[(N + 1) * N];     // L[f*N + i]     = l_i(xi_{f-1/2})          (Eq. Lmat)
+    real M[N * (N + 1)];     // M[i*(N+1) + f] = l'_{f-1/2}(xi_i)         (Eq. Mmat)
+    real D[N * N];           // D = M L
+};
+
+template <typename real, int N>
+__constant__ OpTab<real, N> c_op;
+
+// per-grid scalars of the line kernels
+template <typename real>
+struct LineGeo {
+    real two_h[3];           // 2/h_d
+    real corrL[3];           // (2/h_d) alpha
+    real corrR[3];           // (2/h_d) beta
+    real off0, off4;         // offsets removed from variables 0 and 4 when staging
+};
+
+template <int N, int DIM, int NV>
+struct LineLayout {
+    static constexpr int NP = ipow(N, DIM);
+    static constexpr int NQ = ipow(N, DIM - 1);
+    static constexpr int NF = 2 * DIM;
+    static constexpr int NG = NumGrad<NV>::value;
+    static constexpr int EPW = NQ <= 32 ? 32 / NQ : 1;            // elements per warp
+    static constexpr int WPD = NQ <= 32 ? 1 : (NQ + 31) / 32;     // warps per direction
+    static constexpr int UNIT = DIM * WPD * 32;                   // threads per element group
+    static constexpr int UPB = UNIT >= 192 ? 1 : 192 / UNIT;      // groups per block
+    static constexpr int THREADS = UPB * UNIT;
+    static constexpr int EB = UPB * EPW;                          // elements per block
+    static constexpr int S_U = NV * NP;
+    static constexpr int S_TR = NF * NV * NQ;
+    static constexpr int S_VS = NV * DIM * NP;
+    static constexpr int S_TG = NF * NG * NQ;
+    static constexpr int PER_TRACE = S_U;
+    static constexpr int PER_GRAD = S_U + 2 * S_TR + S_VS;
+    static constexpr int PER_FLUX = S_U + 2 * S_TR + S_VS + S_TG;
+    static constexpr int NBR_BYTES = ((EB * NF * 4 + 15) / 16) * 16;   // neighbour table
+};
+
+struct LineId {
+    int d;      // direction of this warp
+    int eb;     // element slot in the block
+    int q;      // face point index of the lane's line
+    bool ok;    // lane carries a line
+};
+
+template <class LL>
+__device__ __forceinline__ LineId line_id(int tid) {
+    const int unit = tid / LL::UNIT;
+    const int t = tid - unit * LL::UNIT;
+    LineId r;
+    r.d = t / (LL::WPD * 32);
+    const int w = (t >> 5) % LL::WPD;
+    const int lane = t & 31;
+    if (LL::EPW > 1) {
+        const int eu = lane / LL::NQ;
+        r.q = lane - eu * LL::NQ;
+        r.eb = unit * LL::EPW + eu;
+        r.ok = eu < LL::EPW;
+    } else {
+        r.q = lane + 32 * w;
+        r.eb = unit;
+        r.ok = r.q < LL::NQ;
+    }
+    return r;
+}
+
+// point index of position i along compile-time direction D on line q
+template <int N, int D>
+__device__ __forceinline__ int lpt(int i, int q) {
+    constexpr int lo = ipow(N, D);
+    return (q % lo) + lo * i + lo * N * (q / lo);
+}
+
+// sum_i row[i] * x[i], one fixed fma sequence (row from constant memory)
+template <typename real, int N>
+__device__ __forceinline__ real dotc(const real* row, const real* x) {
+    real s = row[0] * x[0];
+#pragma unroll
+    for (int i = 1; i < N; ++i) s = fma(row[i], x[i], s);
+    return s;
+}
+
+// ---------------------------------------------------------------- staging helpers
+// flat load of the block's elements (u, offsets removed unless the input already carries
+// them) and, optionally, the neighbour traces and neighbour interface gradients
+template <typename real, class LL, int NV, bool NB_TR, bool NB_TG>
+__device__ __forceinline__ void stage_load(const real* __restrict__ U, const real* __restrict__ Tu,
+                                           const real* __restrict__ Tg, const Mesh& g, int e0,
+                                           real* sm, int per, real off0, real off4, int* nbr) {
+    constexpr int NP = LL::NP, NQ = LL::NQ, NF = LL::NF, NG = LL::NG;
+    const int nloc = min(LL::EB, g.nelem - e0);
+    if (NB_TR || NB_TG) {
+        // neighbour element of every (element, face), computed once
+        for (int k = threadIdx.x; k < nloc * NF; k += blockDim.x) {
+            const int eb = k / NF, f = k - eb * NF;
+            nbr[k] = neighbour(g, e0 + eb, f >> 1, f & 1);
+        }
+        __syncthreads();
+    }
+    for (int k = threadIdx.x; k < nloc * NV * NP; k += blockDim.x) {
+        const int eb = k / (NV * NP);
+        const int r = k - eb * NV * NP;
+        const int v = r / NP, pt = r - v * NP;
+        real x = U[(size_t)v * g.nelem * NP + (size_t)(e0 + eb) * NP + pt];
+        if (v == 0) x -= off0;
+        if (v == 4) x -= off4;
+        sm[eb * per + r] = x;
+    }
+    if (NB_TR) {
+        for (int k = threadIdx.x; k < nloc * NF * NV * NQ; k += blockDim.x) {
+            const int eb = k / (NF * NV * NQ);
+            const int r = k - eb * NF * NV * NQ;
+            const int f = r / (NV * NQ), rem = r - f * NV * NQ;
+            const int en = nbr[eb * NF + f];
+            sm[eb * per + LL::S_U + LL::S_TR + r] = Tu[((size_t)en * NF + (f ^ 1)) * NV * NQ + rem];
+        }
+    }
+    if (NB_TG) {
+        for (int k = threadIdx.x; k < nloc * NF * NG * NQ; k += blockDim.x) {
+            const int eb = k / (NF * NG * NQ);
+            const int r = k - eb * NF * NG * NQ;
+            const int f = r / (NG * NQ), rem = r - f * NG * NQ;
+            const int en = nbr[eb * NF + f];
+            sm[eb * per + LL::S_U + 2 * LL::S_TR + LL::S_VS + r] =
+                Tg[((size_t)en * NF + (f ^ 1)) * NG * NQ + rem];
+        }
+    }
+}
+
+// own traces at the two faces of direction D for every variable of line q
+template <typename real, int N, int NP, int NQ, int NV, int D>
+__device__ __forceinline__ void line_traces(const real* su, int q, real* outL, real* outR,
+                                            int ostride) {
+    const OpTab<real, N>& op = c_op<real, N>;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+        real u[N];
+#pragma unroll
+        for (int i = 0; i < N; ++i) u[i] = su[v * NP + lpt<N, D>(i, q)];
+        outL[v * ostride] = dotc<real, N>(op.L, u);
+        outR[v * ostride] = dotc<real, N>(op.L + N * N, u);
+    }
+}
+
+// v^S along D for every variable of line q (Eq. w:e in Cartesian form):
+// v_D = (2/h_D) (D u + M[:,0] delta_L + M[:,N] delta_R)
+template <typename real, int N, int DIM, int NV, int D>
+__device__ __forceinline__ void line_vs(const LineGeo<real>& geo, const real* su, const real* tro,
+                                        const real* trn, real* vS, int q) {
+    constexpr int NP = ipow(N, DIM), NQ = ipow(N, DIM - 1);
+    const OpTab<real, N>& op = c_op<real, N>;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+        real u[N];
+#pragma unroll
+        for (int i = 0; i < N; ++i) u[i] = su[v * NP + lpt<N, D>(i, q)];
+        const int il = ((2 * D) * NV + v) * NQ + q, ir = ((2 * D + 1) * NV + v) * NQ + q;
+        const real dl = real(0.5) * (trn[il] - tro[il]);
+        const real dr = real(0.5) * (trn[ir] - tro[ir]);
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            real acc = dotc<real, N>(op.D + i * N, u);
+            acc = fma(op.M[i * (N + 1)], dl, acc);
+            acc = fma(op.M[i * (N + 1) + N], dr, acc);
+            vS[(v * DIM + D) * NP + lpt<N, D>(i, q)] = geo.two_h[D] * acc;
+        }
+    }
+}
+
+// own interface gradient of component c on side s (0: face 2D, 1: face 2D+1) from the
+// loaded line g[] (BR1: Eq. v:e at the interface row; compact: minus (2/h) alpha (beta)
+// times the opposite-face correction on the d-component)
+template <typename real, int N, int NQ, int NV, int D>
+__device__ __forceinline__ real face_value(const LineGeo<real>& geo, int compact, int c, int s,
+                                           const real* g, const real* tro, const real* trn, int q) {
+    const OpTab<real, N>& op = c_op<real, N>;
+    real a = dotc<real, N>(op.L + (s ? N * N : 0), g);
+    int v, m;
+    comp_map<NV>(D, c, v, m);
+    if (compact && m == D) {
+        const int fo = 2 * D + (1 - s);
+        const int io = (fo * NV + v) * NQ + q;
+        const real dop = real(0.5) * (trn[io] - tro[io]);
+        a = fma(-(s ? geo.corrR[D] : geo.corrL[D]), dop, a);
+    }
+    return a;
+}
+
+// ---------------------------------------------------------------- kernels
+template <typename real, int N, int DIM, int NV>
+__global__ void __launch_bounds__(LineLayout<N, DIM, NV>::THREADS)
+k_line_trace(const real* __restrict__ U, real* __restrict__ Tu, LineGeo<real> geo, Mesh g) {
+    using LL = LineLayout<N, DIM, NV>;
+    constexpr int NP = LL::NP, NQ = LL::NQ, NF = LL::NF;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    real* sm = reinterpret_cast<real*>(smem_raw);
+    const int e0 = blockIdx.x * LL::EB;
+    stage_load<real, LL, NV, false, false>(U, nullptr, nullptr, g, e0, sm, LL::PER_TRACE, geo.off0, geo.off4,
+                                           nullptr);
+    __syncthreads();
+    const LineId id = line_id<LL>(threadIdx.x);
+    const int e = e0 + id.eb;
+    if (!id.ok || e >= g.nelem) return;
+    const real* su = sm + id.eb * LL::PER_TRACE;
+    real* out = Tu + (size_t)e * NF * NV * NQ + id.q;
+    if (id.d == 0) line_traces<real, N, NP, NQ, NV, 0>(su, id.q, out, out + NV * NQ, NQ);
+    if constexpr (DIM == 3) {
+        if (id.d == 1) line_traces<real, N, NP, NQ, NV, 1>(su, id.q, out + 2 * NV * NQ, out + 3 * NV * NQ, NQ);
+        if (id.d == 2) line_traces<real, N, NP, NQ, NV, 2>(su, id.q, out + 4 * NV * NQ, out + 5 * NV * NQ, NQ);
+    }
+}
+
+// shared prologue of the gradient and flux kernels: own traces, then v^S
+template <typename real, int N, int DIM, int NV>
+__device__ __forceinline__ void prologue(const LineGeo<real>& geo, const LineId& id, bool live,
+                                         real* su, real* tro, real* trn, real* vS) {
+    using LL = LineLayout<N, DIM, NV>;
+    constexpr int NP = LL::NP, NQ = LL::NQ;
+    if (live) {
+        real* o = tro + id.q;
+        if (id.d == 0) line_traces<real, N, NP, NQ, NV, 0>(su, id.q, o, o + NV * NQ, NQ);
+        if constexpr (DIM == 3) {
+            if (id.d == 1) line_traces<real, N, NP, NQ, NV, 1>(su, id.q, o + 2 * NV * NQ, o + 3 * NV * NQ, NQ);
+            if (id.d == 2) line_traces<real, N, NP, NQ, NV, 2>(su, id.q, o + 4 * NV * NQ, o + 5 * NV * NQ, NQ);
+        }
+    }
+    __syncthreads();
+    if (live) {
+        if (id.d == 0) line_vs<real, N, DIM, NV, 0>(geo, su, tro, trn, vS, id.q);
+        if constexpr (DIM == 3) {
+            if (id.d == 1) line_vs<real, N, DIM, NV, 1>(geo, su, tro, trn, vS, id.q);
+            if (id.d == 2) line_vs<real, N, DIM, NV, 2>(geo, su, tro, trn, vS, id.q);
+        }
+    }
+    __syncthreads();
+}
+
+template <typename real, int N, int DIM, int NV, int D>
+__device__ __forceinline__ void grad_faces(const LineGeo<real>& geo, int compact, const real* vS,
+                                           const real* tro, const real* trn, real* out, int q) {
+    using LL = LineLayout<N, DIM, NV>;
+    constexpr int NP = LL::NP, NQ = LL::NQ, NG = LL::NG;
+#pragma unroll
+    for (int c = 0; c < NG; ++c) {
+        int v, m;
+        comp_map<NV>(D, c, v, m);
+        real gl[N];
+#pragma unroll
+        for (int i = 0; i < N; ++i) gl[i] = vS[(v * DIM + m) * NP + lpt<N, D>(i, q)];
+        out[((2 * D) * NG + c) * NQ + q] = face_value<real, N, NQ, NV, D>(geo, compact, c, 0, gl, tro, trn, q);
+        out[((2 * D + 1) * NG + c) * NQ + q] = face_value<real, N, NQ, NV, D>(geo, compact, c, 1, gl, tro, trn, q);
+    }
+}
+
+template <typename real, int N, int DIM, int NV>
+__global__ void __launch_bounds__(LineLayout<N, DIM, NV>::THREADS)
+k_line_grad(const real* __restrict__ U, const real* __restrict__ Tu, real* __restrict__ Tg,
+            LineGeo<real> geo, Mesh g, int compact) {
+    using LL = LineLayout<N, DIM, NV>;
+    constexpr int NQ = LL::NQ, NF = LL::NF, NG = LL::NG;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    int* nbr = reinterpret_cast<int*>(smem_raw);
+    real* sm = reinterpret_cast<real*>(smem_raw + LL::NBR_BYTES);
+    const int e0 = blockIdx.x * LL::EB;
+    stage_load<real, LL, NV, true, false>(U, Tu, nullptr, g, e0, sm, LL::PER_GRAD, geo.off0, geo.off4, nbr);
+    __syncthreads();
+    const LineId id = line_id<LL>(threadIdx.x);
+    const int e = e0 + id.eb;
+    const bool live = id.ok && e < g.nelem;
+    real* su = sm + id.eb * LL::PER_GRAD;
+    real* tro = su + LL::S_U;
+    real* trn = tro + LL::S_TR;
+    real* vS = trn + LL::S_TR;
+    prologue<real, N, DIM, NV>(geo, id, live, su, tro, trn, vS);
+    if (!live) return;
+    real* out = Tg + (size_t)e * NF * NG * NQ;
+    if (id.d == 0) grad_faces<real, N, DIM, NV, 0>(geo, compact, vS, tro, trn, out, id.q);
+    if constexpr (DIM == 3) {
+        if (id.d == 1) grad_faces<real, N, DIM, NV, 1>(geo, compact, vS, tro, trn, out, id.q);
+        if (id.d == 2) grad_faces<real, N, DIM, NV, 2>(geo, compact, vS, tro, trn, out, id.q);
+    }
+}
+
+// fluxes along D at the n+1 flux points of line q and their divergence on the line
+template <typename real, int N, int DIM, int NV, int D>
+__device__ __forceinline__ void line_flux(const LineGeo<real>& geo, const Phys<real>& P, int compact,
+                                          const real* su, const real* vS, const real* tro,
+                                          const real* trn, const real* tgn, int q, real (&r)[NV][N]) {
+    using LL = LineLayout<N, DIM, NV>;
+    constexpr int NP = LL::NP, NQ = LL::NQ, NG = LL::NG;
+    const OpTab<real, N>& op = c_op<real, N>;
+    // gradient line of component c, read from shared memory where it is needed
+    auto gline = [&](int c, real* gl) {
+        int v, m;
+        comp_map<NV>(D, c, v, m);
+#pragma unroll
+        for (int i = 0; i < N; ++i) gl[i] = vS[(v * DIM + m) * NP + lpt<N, D>(i, q)];
+    };
+#pragma unroll
+    for (int v = 0; v < NV; ++v)
+#pragma unroll
+        for (int i = 0; i < N; ++i) r[v][i] = real(0);
+
+    // interface flux points (f = 0 and f = N): Riemann flux of the two traces minus the
+    // viscous flux of the averaged state and the averaged gradient; the viscous part is
+    // applied first so that its temporaries are dead before the Riemann solver runs
+#pragma unroll 1
+    for (int s = 0; s < 2; ++s) {
+        const int face = 2 * D + s;
+        const int f = s ? N : 0;
+        real F[NV];
+        {
+            real Uh[NV], vh[NG];
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                const real own = tro[(face * NV + v) * NQ + q];
+                const real nb = trn[(face * NV + v) * NQ + q];
+                Uh[v] = s ? real(0.5) * (own + nb) : real(0.5) * (nb + own);
+            }
+#pragma unroll
+            for (int c = 0; c < NG; ++c) {
+                real gl[N];
+                gline(c, gl);
+                const real go = face_value<real, N, NQ, NV, D>(geo, compact, c, s, gl, tro, trn, q);
+                const real gn = tgn[(face * NG + c) * NQ + q];
+                vh[c] = s ? real(0.5) * (go + gn) : real(0.5) * (gn + go);
+            }
+            if constexpr (NV == 5) {
+                ns_viscous(Uh, vh, D, P, F);
+#pragma unroll
+                for (int v = 0; v < NV; ++v) F[v] = -F[v];
+            } else {
+                F[0] = scalar_flux(P, Uh[0], vh[0]);
+            }
+#pragma unroll
+            for (int v = 0; v < NV; ++v)
+#pragma unroll
+                for (int i = 0; i < N; ++i) r[v][i] = fma(op.M[i * (N + 1) + f], F[v], r[v][i]);
+        }
+        if constexpr (NV == 5) {
+            real UL[NV], UR[NV];
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                const real own = tro[(face * NV + v) * NQ + q];
+                const real nb = trn[(face * NV + v) * NQ + q];
+                UL[v] = s ? own : nb;
+                UR[v] = s ? nb : own;
+            }
+            ns_riemann(UL, UR, D, P, F);
+#pragma unroll
+            for (int v = 0; v < NV; ++v)
+#pragma unroll
+                for (int i = 0; i < N; ++i) r[v][i] = fma(op.M[i * (N + 1) + f], F[v], r[v][i]);
+        }
+    }
+    // interior flux points: extrapolated solution and gradient (Eq. aux:v:std:2d)
+    real u[NV][N];
+#pragma unroll
+    for (int v = 0; v < NV; ++v)
+#pragma unroll
+        for (int i = 0; i < N; ++i) u[v][i] = su[v * NP + lpt<N, D>(i, q)];
+#pragma unroll 1
+    for (int f = 1; f < N; ++f) {
+        const real* Lr = op.L + f * N;
+        real uf[NV], F[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) uf[v] = dotc<real, N>(Lr, u[v]);
+        if constexpr (NV == 5) {
+            real gf[NG];
+#pragma unroll
+            for (int c = 0; c < NG; ++c) {
+                real gl[N];
+                gline(c, gl);
+                gf[c] = dotc<real, N>(Lr, gl);
+            }
+            ns_viscous(uf, gf, D, P, F);
+#pragma unroll
+            for (int v = 0; v < NV; ++v)
+#pragma unroll
+                for (int i = 0; i < N; ++i) r[v][i] = fma(op.M[i * (N + 1) + f], -F[v], r[v][i]);
+            ns_convective(uf, D, P, F);
+        } else {
+            real gl[N];
+            gline(0, gl);
+            F[0] = scalar_flux(P, uf[0], dotc<real, N>(Lr, gl));
+        }
+#pragma unroll
+        for (int v = 0; v < NV; ++v)
+#pragma unroll
+            for (int i = 0; i < N; ++i) r[v][i] = fma(op.M[i * (N + 1) + f], F[v], r[v][i]);
+    }
+#pragma unroll
+    for (int v = 0; v < NV; ++v)
+#pragma unroll
+        for (int i = 0; i < N; ++i) r[v][i] = -geo.two_h[D] * r[v][i];
+}
+
+template <typename real, int N, int DIM, int NV>
+__global__ void __launch_bounds__(LineLayout<N, DIM, NV>::THREADS, SD_FLUX_MINB)
+k_line_flux(const real* __restrict__ U, const real* __restrict__ Tu, const real* __restrict__ Tg,
+            real* __restrict__ R, LineGeo<real> geo, Mesh g, Phys<real> P, int compact) {
+    using LL = LineLayout<N, DIM, NV>;
+    constexpr int NP = LL::NP;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    int* nbr = reinterpret_cast<int*>(smem_raw);
+    real* sm = reinterpret_cast<real*>(smem_raw + LL::NBR_BYTES);
+    const int e0 = blockIdx.x * LL::EB;
+    stage_load<real, LL, NV, true, true>(U, Tu, Tg, g, e0, sm, LL::PER_FLUX, geo.off0, geo.off4, nbr);
+    __syncthreads();
+    const LineId id = line_id<LL>(threadIdx.x);
+    const int e = e0 + id.eb;
+    const bool live = id.ok && e < g.nelem;
+    real* su = sm + id.eb * LL::PER_FLUX;
+    real* tro = su + LL::S_U;
+    real* trn = tro + LL::S_TR;
+    real* vS = trn + LL::S_TR;
+    real* tgn = vS + LL::S_VS;
+    prologue<real, N, DIM, NV>(geo, id, live, su, tro, trn, vS);
+
+    real r[NV][N];
+    if (live) {
+        if (id.d == 0) line_flux<real, N, DIM, NV, 0>(geo, P, compact, su, vS, tro, trn, tgn, id.q, r);
+        if constexpr (DIM == 3) {
+            if (id.d == 1) line_flux<real, N, DIM, NV, 1>(geo, P, compact, su, vS, tro, trn, tgn, id.q, r);
+            if (id.d == 2) line_flux<real, N, DIM, NV, 2>(geo, P, compact, su, vS, tro, trn, tgn, id.q, r);
+        }
+    }
+    // every line has read u and v^S: the u slot now accumulates R, direction by direction
+    // in the fixed order x, y, z (deterministic sums)
+    __syncthreads();
+#pragma unroll 1
+    for (int dd = 0; dd < DIM; ++dd) {
+        if (live && id.d == dd) {
+#pragma unroll
+            for (int v = 0; v < NV; ++v)
+#pragma unroll
+                for (int i = 0; i < N; ++i) {
+                    int pt;
+                    if (dd == 0) pt = lpt<N, 0>(i, id.q);
+                    else if (dd == 1) pt = lpt<N, (DIM == 3 ? 1 : 0)>(i, id.q);
+                    else pt = lpt<N, (DIM == 3 ? 2 : 0)>(i, id.q);
+                    real* dst = su + v * NP + pt;
+                    *dst = (dd == 0) ? r[v][i] : *dst + r[v][i];
+                }
+        }
+        __syncthreads();
+    }
+    const int nloc = min(LL::EB, g.nelem - e0);
+    for (int k = threadIdx.x; k < nloc * NV * NP; k += blockDim.x) {
+        const int eb = k / (NV * NP);
+        const int rr = k - eb * NV * NP;
+        const int v = rr / NP, pt = rr - v * NP;
+        R[(size_t)v * g.nelem * NP + (size_t)(e0 + eb) * NP + pt] = sm[eb * LL::PER_FLUX + rr];
+    }
+}
+
+}  // namespace sdk

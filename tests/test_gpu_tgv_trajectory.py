@@ -1,0 +1,89 @@
+"""Taylor-Green vortex trajectories on the GPU (Sec. 4.4 setup, Re = 1600, Ma = 0.1):
+the FP32 residual with FP64 SSPRK(5,4) accumulation against the all-FP64 run.
+
+Criterion: the kinetic-energy dissipation rate eps = -dE_k/dt (centred differences of the
+samples taken every 0.1) of the FP32 run stays within 1e-3 relative (to max |eps| of the
+FP64 run) over t in [0, 10]. The grid is 16^3 elements at p = 4 (80^3 DOF) so that the
+all-FP64 run takes about a minute.
+
+Also checked: E_k(0)/|Omega| = 1/8, mass and energy conservation to round-off, and the
+initial decay rate eps(0) against nu int omega^2 (within 2%, the discretisation and
+compressibility effects at this resolution)."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2608_09615_b300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+import paper_2608_09615_b300 as sd  # noqa: E402
+
+NE, P = (16, 16, 16), 4
+DT = 1.25e-3
+T_END = 10.0
+EVERY = 0.1
+
+
+def run(precision, scheme="compact"):
+    ctx = sd.SD(3, NE, (0.0,) * 3, (2 * math.pi,) * 3, P, scheme, sd.Physics(kind="ns"), precision)
+    U = torch.from_numpy(inputs.tgv_3d(NE, P)).cuda()
+    steps_per = int(round(EVERY / DT))
+    nsamp = int(round(T_END / EVERY))
+    t = 0.0
+    rec = [ctx.diagnostics(U, t)]
+    for _ in range(nsamp):
+        for _ in range(steps_per):
+            ctx.rk_step(U, t, DT, "ssprk54")
+            t += DT
+        rec.append(ctx.diagnostics(U, t))
+    ctx.close()
+    return rec
+
+
+@pytest.fixture(scope="module")
+def trajectories():
+    return {prec: run(prec) for prec in ("f64", "f32")}
+
+
+def dissipation(rec):
+    ke = np.array([r["ke"] / r["volume"] for r in rec])
+    eps = -(ke[2:] - ke[:-2]) / (2 * EVERY)
+    return ke, eps
+
+
+def test_fp32_dissipation_matches_fp64(trajectories, capsys):
+    ke64, eps64 = dissipation(trajectories["f64"])
+    ke32, eps32 = dissipation(trajectories["f32"])
+    err = np.abs(eps32 - eps64).max() / np.abs(eps64).max()
+    with capsys.disabled():
+        print("\nTGV 16^3 p4 Re1600 to t=10: max|eps32-eps64|/max|eps64| = %.3e, "
+              "eps_max = %.4e at t = %.1f, E_k(10)/E_k(0) = %.4f"
+              % (err, eps64.max(), EVERY * (1 + np.argmax(eps64)), ke64[-1] / ke64[0]))
+    assert err <= 1e-3
+
+
+def test_initial_state_and_conservation(trajectories):
+    # FP32 residuals conserve to FP32 round-off per step, FP64 ones to FP64 round-off;
+    # the state update adds that round-off every step (8000 steps)
+    tol = {"f64": (1e-11, 1e-10), "f32": (1e-9, 1e-7)}
+    for prec, rec in trajectories.items():
+        r0 = rec[0]
+        rel, mom = tol[prec]
+        assert r0["ke"] / r0["volume"] == pytest.approx(1.0 / 8.0, abs=1e-12)
+        for r in rec:
+            assert r["nonfinite"] == 0
+            assert r["mass"] == pytest.approx(r0["mass"], rel=rel)
+            assert r["energy"] == pytest.approx(r0["energy"], rel=rel)
+            for i in range(3):
+                assert abs(r["mom"][i]) < mom * r0["mass"]
+
+
+def test_initial_decay_rate(trajectories):
+    rec = trajectories["f64"]
+    ke = np.array([r["ke"] / r["volume"] for r in rec])
+    eps0 = -(-3 * ke[0] + 4 * ke[1] - ke[2]) / (2 * EVERY)     # one-sided, second order
+    nu = 1.0 / 1600.0
+    assert eps0 == pytest.approx(nu * rec[0]["enstrophy"] / rec[0]["volume"], rel=2e-2)
