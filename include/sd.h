@@ -177,6 +177,23 @@ sd_status sd_mlp_backward(const void* X, const void* H, const float* dY, int M, 
 sd_status sd_mlp_adam(float* P, float* m1, float* m2, const float* grad, void* Wb, int step,
                       float lr, float b1, float b2, float eps, void* stream);
 
+/* Allocation-free FP32 residual, for callers that cannot let a library allocate device
+ * memory (an application whose own pool allocator owns the whole device, or a code path
+ * that must not pay for an allocation or for the synchronisation cudaFree can imply).
+ * The paper has no counterpart; it is the same FP32 residual as sd_residual, without a
+ * context: mesh, p, scheme and physics as for sd_init; U, R device FP32 arrays as for
+ * sd_residual (they must not overlap); work enqueued on `stream`.
+ * Scratch: a static device array of 32 MiB (8 Mi FP32 values) inside the library, held by
+ * every GPU that loads the library until the process exits. A grid needs
+ * nelem * 2 dim (nvar + ngrad) n^(dim-1) values (ngrad = 9 for Navier-Stokes, 1 otherwise;
+ * 3375 elements at p = 4 for Navier-Stokes); larger grids return SD_EINVAL with a message
+ * and nothing is launched. The first call on a device looks up the array's device address
+ * and uploads the operator tables for that device; make that first call before any stream
+ * capture. Every call shares the array: calls whose kernels overlap on the GPU race (give
+ * them one stream, or order them). No memory is allocated by this call. */
+sd_status sd_residual_f32_noalloc(const sd_mesh* mesh, int p, sd_scheme scheme,
+                                  const sd_physics* phys, const float* U, float* R, void* stream);
+
 const char* sd_status_str(sd_status s);
 /* Text of the last error raised on the calling thread ("" if none). */
 const char* sd_last_error(void);

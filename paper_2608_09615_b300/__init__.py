@@ -56,7 +56,7 @@ EXPORTS = ("sd_init", "sd_destroy", "sd_set_stream", "sd_state_size", "sd_nvar",
            "sd_residual", "sd_residual_host", "sd_rk_step", "sd_diagnostics", "sd_status_str",
            "sd_last_error", "sd_profile_enable", "sd_profile_read", "sd_launch_count",
            "sd_mlp_param_count", "sd_mlp_cast", "sd_mlp_forward", "sd_mlp_loss", "sd_mlp_backward",
-           "sd_mlp_adam")
+           "sd_mlp_adam", "sd_residual_f32_noalloc")
 KERNEL_CLASSES = ("trace", "grad", "flux_div", "other")
 
 _lib_handle = None
@@ -116,6 +116,9 @@ def load_library(path=LIB_PATH):
     lib.sd_mlp_adam.argtypes = [P, P, P, P, P, I, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                                 ctypes.c_float, P]
     lib.sd_mlp_adam.restype = I
+    lib.sd_residual_f32_noalloc.argtypes = [ctypes.POINTER(_Mesh), I, I, ctypes.POINTER(_Physics),
+                                            P, P, P]
+    lib.sd_residual_f32_noalloc.restype = I
     _lib_handle = lib
     return lib
 
@@ -170,6 +173,29 @@ def sd_init(dim, ne, lo, hi, p, scheme, physics, precision, stream=None):
                      PRECISIONS[precision], _stream_handle(stream), ctypes.byref(out))
     _check(st, "sd_init")
     return out
+
+
+def sd_residual_f32_noalloc(dim, ne, lo, hi, p, scheme, physics, U, R, stream=None):
+    """FP32 residual through the allocation-free entry point (no context, no device
+    allocation; the library's static scratch is shared by all calls). U, R: contiguous
+    CUDA float32 tensors in the state layout."""
+    import torch
+    for t, nm in ((U, "U"), (R, "R")):
+        if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float32 or \
+                not t.is_contiguous():
+            raise ValueError("%s must be a contiguous CUDA float32 tensor" % nm)
+    if U.numel() != R.numel():
+        raise ValueError("U and R differ in size")
+    ne = list(ne) + [1] * (3 - len(ne))
+    lo = list(lo) + [0.0] * (3 - len(lo))
+    hi = list(hi) + [1.0] * (3 - len(hi))
+    m = _Mesh(dim, (ctypes.c_int * 3)(*ne), (ctypes.c_double * 3)(*lo), (ctypes.c_double * 3)(*hi))
+    ph = physics.to_c()
+    _check(load_library().sd_residual_f32_noalloc(ctypes.byref(m), int(p), SCHEMES[scheme],
+                                                  ctypes.byref(ph), ctypes.c_void_p(U.data_ptr()),
+                                                  ctypes.c_void_p(R.data_ptr()),
+                                                  _stream_handle(stream)), "sd_residual_f32_noalloc")
+    return R
 
 
 def sd_destroy(ctx):

@@ -201,6 +201,8 @@ static void build_operators(sd_ctx* c) {
     c->beta = b;
 }
 
+void sdi_build_operators(sd_ctx* c) { build_operators(c); }
+
 // ------------------------------------------------------------------ life cycle
 static void free_all(sd_ctx* c) {
     void* ptrs[] = {c->Tu, c->Tg, c->S, c->K, c->rA, c->rB, c->rC, c->dW,

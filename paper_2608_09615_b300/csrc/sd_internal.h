@@ -71,3 +71,7 @@ sd_status sdi_upload_f64(const sd_ctx* c);
 sd_status sdi_diag(sd_ctx* c, const double* U64, double* host_out);
 sd_status sdi_check_smem(sd_ctx* c);
 void sdi_set_error(const char* fmt, ...);
+void sdi_build_operators(sd_ctx* c);
+
+// size of the static scratch of sd_residual_f32_noalloc (FP32 values, 32 MiB)
+#define SD_NOALLOC_SCRATCH_FLOATS (8 * 1024 * 1024)
