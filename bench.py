@@ -121,6 +121,22 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def max_over_ranks(x, dist=None, device="cpu"):
+    """Largest value of x over the ranks of the default process group (x itself alone)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world, npts, ms_per_step):
+    """Whole-job DOF-updates/s: every rank advances its own copy of the workload by one
+    SSPRK(5,4) step (STAGES residual evaluations) in ms_per_step (the slowest rank's)."""
+    return world * STAGES * npts / (ms_per_step * 1e-3)
+
+
 def cpu_threads():
     try:
         from threadpoolctl import threadpool_info
@@ -264,12 +280,8 @@ def main():
     prof = ctx.profile_read()
     ctx.profile(False)
     clk = clocks.stop()
-    ms = ev0.elapsed_time(ev1) / args.steps
-    if dist is not None:
-        tt = torch.tensor([ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
-    value = world * STAGES * npts / (ms * 1e-3)
+    ms = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, dist, "cuda")
+    value = job_value(world, npts, ms)
     final = ctx.diagnostics(U64, t, raise_nonfinite=False)
 
     # roofline of the dominant kernel (flux/divergence), from the live CUDA events

@@ -67,7 +67,8 @@ typedef struct {
  *           sutherland != 0: mu = mu0 (e/e0)^(3/2) (1 + suth_s)/(e/e0 + suth_s),
  *           suth_s = S/T0 (0.368 for S = 110.4 K, T0 = 300 K); otherwise mu = mu0.
  *           Interfaces: Roe (Harten fix on the acoustic waves, delta = harten * c_Roe)
- *           or Rusanov, minus the viscous flux of the averaged state and gradient. */
+ *           or Rusanov, minus the viscous flux of the averaged state and gradient.
+ *  All kinds: eta_ip >= 0 adds the interior-penalty term to the interface gradient. */
 typedef struct {
     sd_physics_kind kind;
     double nu;
@@ -77,6 +78,8 @@ typedef struct {
     double suth_s;
     sd_riemann riemann;
     double harten;
+    double eta_ip;      /* interior penalty (Sec. 3): the interface average of the normal
+                           gradient gains eta_ip (p+1)^2 / h_d (u_R - u_L); 0 = off */
 } sd_physics;
 
 /* Volume diagnostics (Sec. 4.4), FP64, Gauss quadrature over every element.
@@ -176,6 +179,52 @@ sd_status sd_mlp_backward(const void* X, const void* H, const float* dY, int M, 
 /* One Adam step (step = 1, 2, ...) on the masters P with moments m1, m2; refreshes Wb. */
 sd_status sd_mlp_adam(float* P, float* m1, float* m2, const float* grad, void* Wb, int step,
                       float lr, float b1, float b2, float eps, void* stream);
+
+/* ---- Learned sub-grid closure of coarse Navier-Stokes runs (no counterpart in the paper;
+ * see the closure definitions in the oracle's closure module: L2-projection filter,
+ * sub-grid flux targets, 64 element features, per-element flux injection). ---- */
+
+/* Extra per-element flux added by sd_residual / sd_rk_step: tau (device FP32,
+ * [nelem][15], tau[e][3 v + d] for variable v and direction d) is added to F at the
+ * element's interior flux points, and the average of the two elements' values at each
+ * interface. NULL removes it. The buffer stays the caller's; it is read at every residual. */
+sd_status sd_set_flux_tau(sd_ctx* ctx, const float* tau);
+
+/* Closure data of the state U (device, context precision, Navier-Stokes): X = the 64
+ * element features [nelem][64] FP32 and/or means = the Gauss means of the physical flux
+ * F = F_c - F_v at the solution points, [nelem][15] FP64 (either pointer may be NULL).
+ * Uses the context's trace buffer; asynchronous. */
+sd_status sd_closure_data(sd_ctx* ctx, const void* U, float* X, double* means);
+
+/* The 1D L2 projection from r fine elements of degree pf onto one coarse element of degree
+ * pc (host, row-major (pc+1) x (r (pf+1))): coarse nodal value a from the fine values. */
+sd_status sd_filter_matrix(int pf, int pc, int r, double* P);
+
+/* Box filter: L2 projection of the fine FP64 state Uf (nv variables) onto the nested coarse
+ * grid of ne_coarse[3] elements (r fine elements per coarse element and axis) -> Uc (FP64).
+ * P: the device copy of sd_filter_matrix(nf - 1, nc - 1, r). */
+sd_status sd_filter_project(const double* Uf, double* Uc, const double* P, int nv,
+                            const int* ne_coarse, int r, int nf, int nc, void* stream);
+
+/* Sub-grid flux targets tau[ec][k] = mean over the r^3 children of fine_means[ef][k] -
+ * coarse_means[ec][k] (FP32 out, [nelem_coarse][15]). */
+sd_status sd_closure_targets(const double* fine_means, const double* coarse_means, float* tau,
+                             const int* ne_coarse, int r, void* stream);
+
+/* Column statistics and standardisation of row-major FP32 tables (device). */
+sd_status sd_colstats(const float* A, int rows, int cols, float* mu, float* sigma, void* stream);
+sd_status sd_standardise(const float* A, int rows, int cols, const float* mu, const float* sigma,
+                         void* out_bf16, float* out_f32, void* stream);
+sd_status sd_unstandardise(const float* Y, int rows, int cols, const float* mu, const float* sigma,
+                           float* out, void* stream);
+
+/* Attach a trained closure network to the context: every residual then evaluates the
+ * features of its input state, the network (standardised input mu_x/sig_x [64], output
+ * un-standardised with mu_t/sig_t [15]) and adds the resulting per-element flux. Wb, P and
+ * the statistics are caller-owned device buffers (see sd_mlp_*). Enabling allocates the
+ * context's closure buffers (features, activations, flux) once; Wb = NULL detaches. */
+sd_status sd_closure_enable(sd_ctx* ctx, const void* Wb, const float* P, const float* mu_x,
+                            const float* sig_x, const float* mu_t, const float* sig_t);
 
 /* Allocation-free FP32 residual, for callers that cannot let a library allocate device
  * memory (an application whose own pool allocator owns the whole device, or a code path

@@ -36,7 +36,7 @@ def along(A, X, axis):
     return np.moveaxis(Y, 0, axis)
 
 
-def residual(U, grid: Grid, scheme, phys, return_parts=False, tau=None):
+def residual(U, grid: Grid, scheme, phys, return_parts=False, tau=None, eta_ip=0.0):
     """du/dt at the solution points.
 
     U: array of shape grid.shape(phys.nvar), any float/complex dtype (promoted to
@@ -45,6 +45,10 @@ def residual(U, grid: Grid, scheme, phys, return_parts=False, tau=None):
     tau: optional per-element extra flux (nvar, E..., dim) of a learned closure (not part
        of the paper's method; see oracle/closure.py): added to F at the element's interior
        flux points, with the average of the two elements' values at each interface.
+    eta_ip: interior-penalty parameter (Sec. 3, the Q_IP term): the interface average of
+       the d-component of the gradient on a face normal to d gains tau_IP (u_R - u_L),
+       tau_IP = eta_ip (p+1)^2 / h_d (the element size; the paper's 1/h = |S| / J with the
+       integrated surface and Jacobian gives 1/h_d on Cartesian grids).
     """
     if scheme not in ("br1", "compact"):
         raise ValueError(scheme)
@@ -144,6 +148,10 @@ def residual(U, grid: Grid, scheme, phys, return_parts=False, tau=None):
         for m in range(dim):
             vl = 0.5 * (np.roll(faceR[d][m], 1, axis=ea) + faceL[d][m])
             vr = 0.5 * (faceR[d][m] + np.roll(faceL[d][m], -1, axis=ea))
+            if eta_ip and m == d:
+                tip = eta_ip * (grid.n ** 2) / grid.h[d]
+                vl = vl + tip * (traceL[d] - np.roll(traceR[d], 1, axis=ea))
+                vr = vr + tip * (np.roll(traceL[d], -1, axis=ea) - traceR[d])
             a = vF[d][m].copy()
             a[_ix(nd, pa, 0)] += vl
             a[_ix(nd, pa, n)] += vr

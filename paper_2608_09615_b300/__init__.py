@@ -42,7 +42,7 @@ class _Physics(ctypes.Structure):
                 ("gamma", ctypes.c_double), ("Pr", ctypes.c_double), ("Re", ctypes.c_double),
                 ("Ma", ctypes.c_double), ("rho0", ctypes.c_double), ("u0", ctypes.c_double),
                 ("L", ctypes.c_double), ("sutherland", ctypes.c_int), ("suth_s", ctypes.c_double),
-                ("riemann", ctypes.c_int), ("harten", ctypes.c_double)]
+                ("riemann", ctypes.c_int), ("harten", ctypes.c_double), ("eta_ip", ctypes.c_double)]
 
 
 class _Diag(ctypes.Structure):
@@ -56,7 +56,9 @@ EXPORTS = ("sd_init", "sd_destroy", "sd_set_stream", "sd_state_size", "sd_nvar",
            "sd_residual", "sd_residual_host", "sd_rk_step", "sd_diagnostics", "sd_status_str",
            "sd_last_error", "sd_profile_enable", "sd_profile_read", "sd_launch_count",
            "sd_mlp_param_count", "sd_mlp_cast", "sd_mlp_forward", "sd_mlp_loss", "sd_mlp_backward",
-           "sd_mlp_adam", "sd_residual_f32_noalloc")
+           "sd_mlp_adam", "sd_residual_f32_noalloc", "sd_set_flux_tau", "sd_closure_data",
+           "sd_filter_matrix", "sd_filter_project", "sd_closure_targets", "sd_colstats",
+           "sd_standardise", "sd_unstandardise", "sd_closure_enable")
 KERNEL_CLASSES = ("trace", "grad", "flux_div", "other")
 
 _lib_handle = None
@@ -119,6 +121,24 @@ def load_library(path=LIB_PATH):
     lib.sd_residual_f32_noalloc.argtypes = [ctypes.POINTER(_Mesh), I, I, ctypes.POINTER(_Physics),
                                             P, P, P]
     lib.sd_residual_f32_noalloc.restype = I
+    lib.sd_set_flux_tau.argtypes = [P, P]
+    lib.sd_set_flux_tau.restype = I
+    lib.sd_closure_data.argtypes = [P, P, P, P]
+    lib.sd_closure_data.restype = I
+    lib.sd_filter_matrix.argtypes = [I, I, I, P]
+    lib.sd_filter_matrix.restype = I
+    lib.sd_filter_project.argtypes = [P, P, P, I, P, I, I, I, P]
+    lib.sd_filter_project.restype = I
+    lib.sd_closure_targets.argtypes = [P, P, P, P, I, P]
+    lib.sd_closure_targets.restype = I
+    lib.sd_colstats.argtypes = [P, I, I, P, P, P]
+    lib.sd_colstats.restype = I
+    lib.sd_standardise.argtypes = [P, I, I, P, P, P, P, P]
+    lib.sd_standardise.restype = I
+    lib.sd_unstandardise.argtypes = [P, I, I, P, P, P, P]
+    lib.sd_unstandardise.restype = I
+    lib.sd_closure_enable.argtypes = [P, P, P, P, P, P, P]
+    lib.sd_closure_enable.restype = I
     _lib_handle = lib
     return lib
 
@@ -146,11 +166,12 @@ class Physics:
     suth_s: float = 110.4 / 300.0
     riemann: str = "roe"
     harten: float = 0.1
+    eta_ip: float = 0.0
 
     def to_c(self):
         return _Physics(KINDS[self.kind], self.nu, self.m_pme, self.gamma, self.Pr, self.Re,
                         self.Ma, self.rho0, self.u0, self.L, int(bool(self.sutherland)),
-                        self.suth_s, RIEMANN[self.riemann], self.harten)
+                        self.suth_s, RIEMANN[self.riemann], self.harten, self.eta_ip)
 
 
 def _stream_handle(stream):
@@ -298,6 +319,36 @@ class SD:
     def launch_count(self):
         return int(load_library().sd_launch_count(self._ctx))
 
+    # ---- closure data path (Navier-Stokes)
+    def set_flux_tau(self, tau):
+        """tau: CUDA float32 tensor (nelem, 15) or None: extra per-element flux."""
+        self._tau = tau
+        _check(load_library().sd_set_flux_tau(self._ctx, None if tau is None else _ptr(tau)),
+               "sd_set_flux_tau")
+
+    def closure_data(self, U, features=True, means=True):
+        """Features (nelem, 64) float32 and/or flux means (nelem, 15) float64 of state U."""
+        import torch
+        E = self.numel // (self.nvar * self.n ** self.dim)
+        X = torch.empty(E, 64, dtype=torch.float32, device="cuda") if features else None
+        Mn = torch.empty(E, 15, dtype=torch.float64, device="cuda") if means else None
+        _check(load_library().sd_closure_data(self._ctx, _dev_ptr(U, self.dtype, self.numel, "U"),
+                                              None if X is None else _ptr(X),
+                                              None if Mn is None else _ptr(Mn)), "sd_closure_data")
+        return X, Mn
+
+    def closure_enable(self, net, mu_x, sig_x, mu_t, sig_t):
+        """Attach a trained MLP (sd.MLP) with its standardisation statistics."""
+        self._closure_refs = (net, mu_x, sig_x, mu_t, sig_t)
+        _check(load_library().sd_closure_enable(self._ctx, _ptr(net.Wb), _ptr(net.P), _ptr(mu_x),
+                                                _ptr(sig_x), _ptr(mu_t), _ptr(sig_t)),
+               "sd_closure_enable")
+
+    def closure_disable(self):
+        _check(load_library().sd_closure_enable(self._ctx, None, None, None, None, None, None),
+               "sd_closure_enable")
+        self._closure_refs = None
+
     def close(self):
         if getattr(self, "_ctx", None) is not None:
             sd_destroy(self._ctx)
@@ -423,3 +474,58 @@ class MLP:
 
 def _ptr(t):
     return ctypes.c_void_p(t.data_ptr())
+
+
+def filter_matrix(pf, pc, r):
+    """Host copy (numpy) of the 1D fine -> coarse L2 projection of sd_filter_matrix."""
+    import numpy as np
+    P = np.zeros(((pc + 1), r * (pf + 1)), dtype=np.float64)
+    _check(load_library().sd_filter_matrix(pf, pc, r, P.ctypes.data_as(ctypes.c_void_p)),
+           "sd_filter_matrix")
+    return P
+
+
+def filter_project(Uf, ne_coarse, r, pf, pc, Pdev=None, stream=None):
+    """Box filter of the fine FP64 CUDA state Uf onto the nested coarse grid (FP64 out)."""
+    import numpy as np
+    import torch
+    if Pdev is None:
+        Pdev = torch.from_numpy(filter_matrix(pf, pc, r)).cuda()
+    nv = int(Uf.shape[0])
+    Ec = int(np.prod(ne_coarse))
+    Uc = torch.empty((nv,) + tuple(reversed(tuple(ne_coarse))) + (pc + 1,) * 3, dtype=torch.float64,
+                     device="cuda")
+    nec = (ctypes.c_int * 3)(*ne_coarse)
+    _check(load_library().sd_filter_project(_ptr(Uf), _ptr(Uc), _ptr(Pdev), nv, nec, r, pf + 1, pc + 1,
+                                            _stream_handle(stream)), "sd_filter_project")
+    del Ec
+    return Uc
+
+
+def closure_targets(fine_means, coarse_means, ne_coarse, r, stream=None):
+    import torch
+    tau = torch.empty(coarse_means.shape[0], 15, dtype=torch.float32, device="cuda")
+    nec = (ctypes.c_int * 3)(*ne_coarse)
+    _check(load_library().sd_closure_targets(_ptr(fine_means), _ptr(coarse_means), _ptr(tau), nec, r,
+                                             _stream_handle(stream)), "sd_closure_targets")
+    return tau
+
+
+def colstats(A, stream=None):
+    import torch
+    rows, cols = A.shape
+    mu = torch.empty(cols, dtype=torch.float32, device="cuda")
+    sg = torch.empty(cols, dtype=torch.float32, device="cuda")
+    _check(load_library().sd_colstats(_ptr(A), rows, cols, _ptr(mu), _ptr(sg), _stream_handle(stream)),
+           "sd_colstats")
+    return mu, sg
+
+
+def standardise(A, mu, sigma, bf16=False, stream=None):
+    import torch
+    rows, cols = A.shape
+    out = torch.empty(rows, cols, dtype=torch.bfloat16 if bf16 else torch.float32, device="cuda")
+    _check(load_library().sd_standardise(_ptr(A), rows, cols, _ptr(mu), _ptr(sigma),
+                                         _ptr(out) if bf16 else None, None if bf16 else _ptr(out),
+                                         _stream_handle(stream)), "sd_standardise")
+    return out

@@ -120,52 +120,68 @@ extern "C" long long sd_launch_count(const sd_ctx* c) { return c ? c->launches :
 
 // ------------------------------------------------------------------ 1D operators
 // Gauss-Legendre nodes/weights by Newton iteration on the three-term recurrence of P_n.
-static void gauss_legendre(int n, double* x, double* w) {
+// The operators are built in 80-bit long double and rounded once to double at the end.
+typedef long double ldouble;
+
+template <typename T>
+static void gauss_legendre_t(int n, T* x, T* w) {
+    const T pi = (T)3.14159265358979323846264338327950288L;
     for (int i = 0; i < n; ++i) {
-        double z = cos(M_PI * (i + 0.75) / (n + 0.5));
-        double dp = 1.0;
+        T z = cosl(pi * (i + (T)0.75) / (n + (T)0.5));
         for (int it = 0; it < 100; ++it) {
-            double p0 = 1.0, p1 = z;
+            T p0 = 1, p1 = z;
             for (int k = 2; k <= n; ++k) {
-                const double pk = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+                const T pk = ((2 * k - 1) * z * p1 - (k - 1) * p0) / k;
                 p0 = p1;
                 p1 = pk;
             }
-            if (n == 1) { p1 = z; p0 = 1.0; }
-            dp = n * (z * p1 - p0) / (z * z - 1.0);
-            const double dz = p1 / dp;
+            if (n == 1) { p1 = z; p0 = 1; }
+            const T dp = n * (z * p1 - p0) / (z * z - 1);
+            const T dz = p1 / dp;
             z -= dz;
-            if (fabs(dz) < 1e-16) break;
+            if (fabsl(dz) < (T)1e-19) break;
         }
-        // recompute the derivative at the converged node for the weight
-        double p0 = 1.0, p1 = z;
+        T p0 = 1, p1 = z;
         for (int k = 2; k <= n; ++k) {
-            const double pk = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+            const T pk = ((2 * k - 1) * z * p1 - (k - 1) * p0) / k;
             p0 = p1;
             p1 = pk;
         }
-        if (n == 1) { p1 = z; p0 = 1.0; }
-        dp = n * (z * p1 - p0) / (z * z - 1.0);
+        if (n == 1) { p1 = z; p0 = 1; }
+        const T dp = n * (z * p1 - p0) / (z * z - 1);
         x[n - 1 - i] = z;                       // ascending order
-        w[n - 1 - i] = 2.0 / ((1.0 - z * z) * dp * dp);
+        w[n - 1 - i] = 2 / ((1 - z * z) * dp * dp);
     }
-    if (n == 1) { x[0] = 0.0; w[0] = 2.0; }
+    if (n == 1) { x[0] = 0; w[0] = 2; }
+}
+
+static void gauss_legendre(int n, double* x, double* w) {
+    ldouble xl[SD_MAX_N], wl[SD_MAX_N];
+    gauss_legendre_t<ldouble>(n, xl, wl);
+    for (int i = 0; i < n; ++i) {
+        x[i] = (double)xl[i];
+        w[i] = (double)wl[i];
+    }
 }
 
 // l_j(x) on nodes t[0..m)
-static double lagrange(const double* t, int m, int j, double x) {
-    double v = 1.0;
+template <typename T>
+static T lagrange_t(const T* t, int m, int j, T x) {
+    T v = 1;
     for (int k = 0; k < m; ++k)
         if (k != j) v *= (x - t[k]) / (t[j] - t[k]);
     return v;
 }
 
+static double lagrange(const double* t, int m, int j, double x) { return lagrange_t<double>(t, m, j, x); }
+
 // l_j'(x) = sum_{k != j} 1/(t_j - t_k) prod_{l != j,k} (x - t_l)/(t_j - t_l)
-static double lagrange_d(const double* t, int m, int j, double x) {
-    double s = 0.0;
+template <typename T>
+static T lagrange_d_t(const T* t, int m, int j, T x) {
+    T s = 0;
     for (int k = 0; k < m; ++k) {
         if (k == j) continue;
-        double prod = 1.0 / (t[j] - t[k]);
+        T prod = 1 / (t[j] - t[k]);
         for (int l = 0; l < m; ++l)
             if (l != j && l != k) prod *= (x - t[l]) / (t[j] - t[l]);
         s += prod;
@@ -175,36 +191,56 @@ static double lagrange_d(const double* t, int m, int j, double x) {
 
 static void build_operators(sd_ctx* c) {
     const int n = c->n;
-    gauss_legendre(n, c->xs, c->ws);
-    c->xf[0] = -1.0;
-    c->xf[n] = 1.0;
-    if (n > 1) {
-        double tmp_w[SD_MAX_N];
-        gauss_legendre(n - 1, c->xf + 1, tmp_w);
-    }
+    ldouble xs[SD_MAX_N], ws[SD_MAX_N], xf[SD_MAX_N + 1], tmp[SD_MAX_N];
+    ldouble L[(SD_MAX_N + 1) * SD_MAX_N], M[SD_MAX_N * (SD_MAX_N + 1)];
+    gauss_legendre_t<ldouble>(n, xs, ws);
+    xf[0] = -1;
+    xf[n] = 1;
+    if (n > 1) gauss_legendre_t<ldouble>(n - 1, xf + 1, tmp);
     for (int f = 0; f <= n; ++f)
-        for (int i = 0; i < n; ++i) c->L[f * n + i] = lagrange(c->xs, n, i, c->xf[f]);
+        for (int i = 0; i < n; ++i) L[f * n + i] = lagrange_t<ldouble>(xs, n, i, xf[f]);
     for (int i = 0; i < n; ++i)
-        for (int f = 0; f <= n; ++f) c->M[i * (n + 1) + f] = lagrange_d(c->xf, n + 1, f, c->xs[i]);
-    for (int i = 0; i < n; ++i)
-        for (int j = 0; j < n; ++j) {
-            double s = 0.0;
-            for (int f = 0; f <= n; ++f) s += c->M[i * (n + 1) + f] * c->L[f * n + j];
-            c->D[i * n + j] = s;
-        }
-    double a = 0.0, b = 0.0;
+        for (int f = 0; f <= n; ++f) M[i * (n + 1) + f] = lagrange_d_t<ldouble>(xf, n + 1, f, xs[i]);
     for (int i = 0; i < n; ++i) {
-        a += c->L[0 * n + i] * c->M[i * (n + 1) + n];
-        b += c->L[n * n + i] * c->M[i * (n + 1) + 0];
+        c->xs[i] = (double)xs[i];
+        c->ws[i] = (double)ws[i];
+        for (int j = 0; j < n; ++j) {
+            ldouble s = 0;
+            for (int f = 0; f <= n; ++f) s += M[i * (n + 1) + f] * L[f * n + j];
+            c->D[i * n + j] = (double)s;
+        }
     }
-    c->alpha = a;
-    c->beta = b;
+    for (int f = 0; f <= n; ++f) c->xf[f] = (double)xf[f];
+    for (int k = 0; k < (n + 1) * n; ++k) c->L[k] = (double)L[k];
+    for (int k = 0; k < n * (n + 1); ++k) c->M[k] = (double)M[k];
+    ldouble a = 0, b = 0;
+    for (int i = 0; i < n; ++i) {
+        a += L[0 * n + i] * M[i * (n + 1) + n];
+        b += L[n * n + i] * M[i * (n + 1) + 0];
+    }
+    c->alpha = (double)a;
+    c->beta = (double)b;
 }
 
 void sdi_build_operators(sd_ctx* c) { build_operators(c); }
 
 // ------------------------------------------------------------------ life cycle
+static void free_closure(sd_ctx* c) {
+    void* ptrs[] = {c->cl_X, c->cl_Xb, c->cl_Y, c->cl_H, c->cl_tau};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    c->cl_X = nullptr;
+    c->cl_Xb = nullptr;
+    c->cl_Y = nullptr;
+    c->cl_H = nullptr;
+    c->cl_tau = nullptr;
+    c->closure_on = 0;
+    if (c->tau == c->cl_tau) c->tau = nullptr;
+}
+
 static void free_all(sd_ctx* c) {
+    free_closure(c);
+    if (c->cl_tmode) cudaFree(c->cl_tmode);
     void* ptrs[] = {c->Tu, c->Tg, c->S, c->K, c->rA, c->rB, c->rC, c->dW,
                     c->partial, c->dsum, c->hU, c->hR};
     for (void* p : ptrs)
@@ -241,6 +277,7 @@ extern "C" sd_status sd_init(const sd_mesh* mesh, int p, sd_scheme scheme, const
         }
     }
     if (phys->kind == SD_PME && !(phys->m_pme >= 1.0)) { sdi_set_error("m_pme must be >= 1"); return SD_EINVAL; }
+    if (!(phys->eta_ip >= 0.0)) { sdi_set_error("eta_ip must be >= 0"); return SD_EINVAL; }
     long long nelem = 1;
     for (int d = 0; d < mesh->dim; ++d) {
         if (mesh->ne[d] < 1) { sdi_set_error("ne[%d] must be >= 1", d); return SD_EINVAL; }
@@ -313,6 +350,7 @@ extern "C" sd_status sd_init(const sd_mesh* mesh, int p, sd_scheme scheme, const
     alloc((void**)&c->rB, S * sizeof(double));
     alloc((void**)&c->rC, S * sizeof(double));
     alloc((void**)&c->dW, SD_MAX_N * sizeof(double));
+    alloc((void**)&c->cl_tmode, (SD_MAX_N * SD_MAX_N + SD_MAX_N) * sizeof(double));
     const int tpe = ((np + 31) / 32) * 32;
     const int epb = std::max(1, 256 / tpe);
     c->diag_blocks = (c->nelem + epb - 1) / epb;
@@ -331,6 +369,33 @@ extern "C" sd_status sd_init(const sd_mesh* mesh, int p, sd_scheme scheme, const
         free_all(c);
         free(c);
         return SD_ECUDA;
+    }
+    {
+        // Legendre modal transform T[m][i] = w_i P_m(x_i) (2m+1)/2 followed by the points x_i
+        double tm[SD_MAX_N * SD_MAX_N + SD_MAX_N];
+        const int n = c->n;
+        for (int i = 0; i < n; ++i) {
+            double p0 = 1.0, p1 = c->xs[i];
+            for (int m = 0; m < n; ++m) {
+                double pm;
+                if (m == 0) pm = 1.0;
+                else if (m == 1) pm = c->xs[i];
+                else {
+                    const double pk = ((2.0 * m - 1.0) * c->xs[i] * p1 - (m - 1.0) * p0) / m;
+                    p0 = p1;
+                    p1 = pk;
+                    pm = pk;
+                }
+                tm[m * n + i] = c->ws[i] * pm * (2.0 * m + 1.0) / 2.0;
+            }
+            tm[n * n + i] = c->xs[i];
+        }
+        if (cudaMemcpy(c->cl_tmode, tm, (n * n + n) * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess) {
+            sdi_set_error("cudaMemcpy of the modal transform failed");
+            free_all(c);
+            free(c);
+            return SD_ECUDA;
+        }
     }
     if (cudaMemcpy(c->dW, c->ws, c->n * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess) {
         sdi_set_error("cudaMemcpy of the Gauss weights failed");
@@ -561,5 +626,80 @@ extern "C" sd_status sd_diagnostics(sd_ctx* c, const double* U64, double t, sd_d
         sdi_set_error("state holds %g non-finite points", h[9]);
         return SD_ENONFINITE;
     }
+    return SD_OK;
+}
+
+// ------------------------------------------------------------------ closure
+extern "C" sd_status sd_set_flux_tau(sd_ctx* c, const float* tau) {
+    if (!c) { sdi_set_error("null argument"); return SD_EINVAL; }
+    if (c->nvar != 5 && tau) { sdi_set_error("a per-element flux needs Navier-Stokes"); return SD_EUNSUPPORTED; }
+    c->tau = tau;
+    return SD_OK;
+}
+
+extern "C" sd_status sd_closure_data(sd_ctx* c, const void* U, float* X, double* means) {
+    if (!c || !U || (!X && !means)) { sdi_set_error("null argument"); return SD_EINVAL; }
+    if (c->prec == SD_F32) return sdi_closure_data_f32(c, (const float*)U, X, means);
+    return sdi_closure_data_f64(c, (const double*)U, X, means);
+}
+
+extern "C" sd_status sd_filter_matrix(int pf, int pc, int r, double* P) {
+    if (pf < 1 || pc < 1 || pf > SD_MAX_N - 1 || pc > SD_MAX_N - 1 || r < 1 || !P) {
+        sdi_set_error("bad argument");
+        return SD_EINVAL;
+    }
+    const int nf = pf + 1, nc = pc + 1;
+    double xf[SD_MAX_N], wf[SD_MAX_N], xc[SD_MAX_N], wc[SD_MAX_N];
+    gauss_legendre(nf, xf, wf);
+    gauss_legendre(nc, xc, wc);
+    for (int a = 0; a < nc; ++a)
+        for (int s = 0; s < r; ++s)
+            for (int k = 0; k < nf; ++k) {
+                const double xi = -1.0 + (2.0 * s + 1.0 + xf[k]) / r;   // fine point, coarse coords
+                P[a * r * nf + s * nf + k] = wf[k] * lagrange(xc, nc, a, xi) / (r * wc[a]);
+            }
+    return SD_OK;
+}
+
+sd_status sdi_closure_network(sd_ctx* c) {
+    const int E = c->nelem;
+    sd_status s = sd_standardise(c->cl_X, E, 64, c->cl_mux, c->cl_sgx, c->cl_Xb, nullptr, c->stream);
+    if (s == SD_OK) s = sd_mlp_forward(c->cl_Xb, E, c->cl_Wb, c->cl_P, c->cl_Y, c->cl_H, c->stream);
+    if (s == SD_OK) s = sd_unstandardise(c->cl_Y, E, 15, c->cl_mut, c->cl_sgt, c->cl_tau, c->stream);
+    c->launches += 3;
+    return s;
+}
+
+extern "C" sd_status sd_closure_enable(sd_ctx* c, const void* Wb, const float* P, const float* mu_x,
+                                       const float* sig_x, const float* mu_t, const float* sig_t) {
+    if (!c) { sdi_set_error("null argument"); return SD_EINVAL; }
+    if (!Wb) {                       // detach
+        free_closure(c);
+        return SD_OK;
+    }
+    if (!P || !mu_x || !sig_x || !mu_t || !sig_t) { sdi_set_error("null argument"); return SD_EINVAL; }
+    if (c->nvar != 5) { sdi_set_error("the closure needs Navier-Stokes"); return SD_EUNSUPPORTED; }
+    if (!c->cl_X) {
+        const size_t E = (size_t)c->nelem;
+        bool ok = cudaMalloc((void**)&c->cl_X, E * 64 * sizeof(float)) == cudaSuccess &&
+                  cudaMalloc(&c->cl_Xb, E * 64 * 2) == cudaSuccess &&
+                  cudaMalloc((void**)&c->cl_Y, E * 15 * sizeof(float)) == cudaSuccess &&
+                  cudaMalloc(&c->cl_H, 2 * E * 128 * 2) == cudaSuccess &&
+                  cudaMalloc((void**)&c->cl_tau, E * 15 * sizeof(float)) == cudaSuccess;
+        if (!ok) {
+            cudaGetLastError();
+            free_closure(c);
+            sdi_set_error("allocation of the closure buffers failed");
+            return SD_ENOMEM;
+        }
+    }
+    c->cl_Wb = Wb;
+    c->cl_P = P;
+    c->cl_mux = mu_x;
+    c->cl_sgx = sig_x;
+    c->cl_mut = mu_t;
+    c->cl_sgt = sig_t;
+    c->tau = c->cl_tau;
+    c->closure_on = 1;
     return SD_OK;
 }

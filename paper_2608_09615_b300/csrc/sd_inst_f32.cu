@@ -7,3 +7,7 @@ sd_status sdi_residual_f32(sd_ctx* c, const float* U, float* R, int offset_in) {
 }
 
 sd_status sdi_upload_f32(const sd_ctx* c) { return sdk::upload_dispatch<float>(c); }
+
+sd_status sdi_closure_data_f32(sd_ctx* c, const float* U, float* X, double* means) {
+    return sdk::closure_data_dispatch<float>(c, U, X, means, 0);
+}

@@ -7,3 +7,7 @@ sd_status sdi_residual_f64(sd_ctx* c, const double* U, double* R, int offset_in)
 }
 
 sd_status sdi_upload_f64(const sd_ctx* c) { return sdk::upload_dispatch<double>(c); }
+
+sd_status sdi_closure_data_f64(sd_ctx* c, const double* U, float* X, double* means) {
+    return sdk::closure_data_dispatch<double>(c, U, X, means, 0);
+}

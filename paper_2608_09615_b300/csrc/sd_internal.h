@@ -47,6 +47,20 @@ struct sd_ctx {
     int diag_blocks;
     void* hU;                // device staging of the host-buffer residual path
     void* hR;
+    // extra per-element flux added by the residual ([nelem][15] FP32, tau[e][3 v + d]),
+    // caller-owned or the closure's own buffer; NULL: none
+    const float* tau;
+    // learned closure attached with sd_closure_enable (buffers owned by the context)
+    int closure_on;
+    double* cl_tmode;        // Legendre modal transform T[m][i] and the points xi (features)
+    float* cl_X;             // features [nelem][64]
+    void* cl_Xb;             // standardised BF16 input [nelem][64]
+    float* cl_Y;             // network output [nelem][15]
+    void* cl_H;              // activation cache [2][nelem][128] BF16
+    float* cl_tau;           // closure flux [nelem][15]
+    const void* cl_Wb;       // caller-owned network: BF16 weights, FP32 parameters,
+    const float* cl_P;       //   input and output standardisation
+    const float *cl_mux, *cl_sgx, *cl_mut, *cl_sgt;
     // profiling and launch accounting
     long long launches;
     int prof_on;
@@ -68,6 +82,11 @@ sd_status sdi_residual_f32(sd_ctx* c, const float* U, float* R, int offset_in);
 sd_status sdi_residual_f64(sd_ctx* c, const double* U, double* R, int offset_in);
 sd_status sdi_upload_f32(const sd_ctx* c);
 sd_status sdi_upload_f64(const sd_ctx* c);
+// closure data of a state: features X [nelem][64] and/or flux means [nelem][15] (either NULL)
+sd_status sdi_closure_data_f32(sd_ctx* c, const float* U, float* X, double* means);
+sd_status sdi_closure_data_f64(sd_ctx* c, const double* U, float* X, double* means);
+// closure network on the context's feature buffer -> c->cl_tau
+sd_status sdi_closure_network(sd_ctx* c);
 sd_status sdi_diag(sd_ctx* c, const double* U64, double* host_out);
 sd_status sdi_check_smem(sd_ctx* c);
 void sdi_set_error(const char* fmt, ...);

@@ -7,6 +7,7 @@
 #include "sd_internal.h"
 #include "sd_kernels.cuh"
 #include "sd_line.cuh"
+#include "sd_closure.cuh"
 
 namespace sdk {
 
@@ -77,6 +78,8 @@ static LineGeo<real> make_geo(const sd_ctx* c, int offset_in) {
     stage_offsets(c, off0, off4);
     o.off0 = offset_in ? real(0) : (real)off0;
     o.off4 = offset_in ? real(0) : (real)off4;
+    for (int d = 0; d < 3; ++d)
+        o.tip[d] = (real)(d < c->dim ? c->phys.eta_ip * c->n * c->n / c->h[d] : 0.0);
     return o;
 }
 
@@ -142,6 +145,50 @@ inline int trace_blocks(long long total) {
     return (int)std::min<long long>(std::max<long long>(b, 1), 148LL * 64);
 }
 
+// ------------------------------------------------------------------ closure data kernels
+template <typename real, int N>
+static sd_status features_impl(sd_ctx* c, const real* U, float* X, int offset_in) {
+    using LL = LineLayout<N, 3, 5>;
+    const LineGeo<real> geo = make_geo<real>(c, offset_in);
+    const Mesh g = make_mesh(c);
+    const Phys<real> P = make_phys<real>(c);
+    const size_t sg = LL::NBR_BYTES + (size_t)LL::EB * LL::PER_GRAD * sizeof(real);
+    if (!set_smem(k_line_features<real, N>, sg)) return SD_EUNSUPPORTED;
+    const int blocks = (g.nelem + LL::EB - 1) / LL::EB;
+    const sd_physics& s = c->phys;
+    sdi_prof_begin(c, SD_K_OTHER);
+    k_line_features<real, N><<<blocks, LL::THREADS, sg, c->stream>>>(
+        U, static_cast<const real*>(c->Tu), geo, g, P, c->dW, c->cl_tmode, c->h[0] / 2.0, s.rho0, s.u0,
+        1.0 / s.Re, X);
+    sdi_prof_end(c, SD_K_OTHER);
+    return cudaGetLastError() == cudaSuccess ? SD_OK : SD_ECUDA;
+}
+
+template <typename real, int N>
+static sd_status fluxmean_impl(sd_ctx* c, const real* U, double* out, int offset_in) {
+    using LL = LineLayout<N, 3, 5>;
+    const LineGeo<real> geo = make_geo<real>(c, offset_in);
+    const Mesh g = make_mesh(c);
+    const Phys<real> P = make_phys<real>(c);
+    const size_t sg = LL::NBR_BYTES + (size_t)LL::EB * LL::PER_GRAD * sizeof(real);
+    if (!set_smem(k_line_fluxmean<real, N>, sg)) return SD_EUNSUPPORTED;
+    const int blocks = (g.nelem + LL::EB - 1) / LL::EB;
+    sdi_prof_begin(c, SD_K_OTHER);
+    k_line_fluxmean<real, N><<<blocks, LL::THREADS, sg, c->stream>>>(
+        U, static_cast<const real*>(c->Tu), geo, g, P, c->dW, out);
+    sdi_prof_end(c, SD_K_OTHER);
+    return cudaGetLastError() == cudaSuccess ? SD_OK : SD_ECUDA;
+}
+
+// per residual with the closure attached: features of the stage state -> standardised
+// BF16 input -> MLP -> tau (the traces Tu of this state are already computed)
+template <typename real, int N>
+static sd_status closure_stage(sd_ctx* c, const real* U, int offset_in) {
+    sd_status s = features_impl<real, N>(c, U, c->cl_X, offset_in);
+    if (s != SD_OK) return s;
+    return sdi_closure_network(c);
+}
+
 template <typename real, int N, int DIM, int NV>
 static sd_status residual_impl(sd_ctx* c, const real* U, real* R, int offset_in) {
     using LL = LineLayout<N, DIM, NV>;
@@ -161,11 +208,15 @@ static sd_status residual_impl(sd_ctx* c, const real* U, real* R, int offset_in)
     sdi_prof_begin(c, SD_K_TRACE);
     k_line_trace<real, N, DIM, NV><<<blocks, LL::THREADS, st, c->stream>>>(U, Tu, geo, g);
     sdi_prof_end(c, SD_K_TRACE);
+    if (c->closure_on && NV == 5) {
+        const sd_status cs = closure_stage<real, N>(c, U, offset_in);
+        if (cs != SD_OK) return cs;
+    }
     sdi_prof_begin(c, SD_K_GRAD);
     k_line_grad<real, N, DIM, NV><<<blocks, LL::THREADS, sg, c->stream>>>(U, Tu, Tg, geo, g, compact);
     sdi_prof_end(c, SD_K_GRAD);
     sdi_prof_begin(c, SD_K_FLUX);
-    k_line_flux<real, N, DIM, NV><<<blocks, LL::THREADS, sf, c->stream>>>(U, Tu, Tg, R, geo, g, P, compact);
+    k_line_flux<real, N, DIM, NV><<<blocks, LL::THREADS, sf, c->stream>>>(U, Tu, Tg, R, geo, g, P, compact, c->tau);
     sdi_prof_end(c, SD_K_FLUX);
     const cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) {
@@ -193,6 +244,31 @@ static sd_status residual_dispatch(sd_ctx* c, const real* U, real* R, int offset
         case 7: return residual_n<real, 7>(c, U, R, offset_in);
         case 8: return residual_n<real, 8>(c, U, R, offset_in);
         case 9: return residual_n<real, 9>(c, U, R, offset_in);
+        default: return SD_EUNSUPPORTED;
+    }
+}
+
+template <typename real>
+static sd_status closure_data_dispatch(sd_ctx* c, const real* U, float* X, double* means, int offset_in) {
+    if (c->nvar != 5) { sdi_set_error("closure data need Navier-Stokes"); return SD_EUNSUPPORTED; }
+    // traces of this state first
+    sd_status st = SD_OK;
+    switch (c->n) {
+#define SD_CASE(NN)                                                                              \
+    case NN: {                                                                                   \
+        using LL = LineLayout<NN, 3, 5>;                                                         \
+        const LineGeo<real> geo = make_geo<real>(c, offset_in);                                  \
+        const Mesh g = make_mesh(c);                                                             \
+        const size_t stb = (size_t)LL::EB * LL::PER_TRACE * sizeof(real);                        \
+        if (!set_smem(k_line_trace<real, NN, 3, 5>, stb)) return SD_EUNSUPPORTED;               \
+        k_line_trace<real, NN, 3, 5><<<(g.nelem + LL::EB - 1) / LL::EB, LL::THREADS, stb,        \
+                                       c->stream>>>(U, static_cast<real*>(c->Tu), geo, g);       \
+        if (X) st = features_impl<real, NN>(c, U, X, offset_in);                                 \
+        if (st == SD_OK && means) st = fluxmean_impl<real, NN>(c, U, means, offset_in);          \
+        return st;                                                                               \
+    }
+        SD_CASE(2) SD_CASE(3) SD_CASE(4) SD_CASE(5) SD_CASE(6) SD_CASE(7) SD_CASE(8) SD_CASE(9)
+#undef SD_CASE
         default: return SD_EUNSUPPORTED;
     }
 }

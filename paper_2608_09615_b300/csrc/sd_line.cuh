@@ -27,10 +27,11 @@
 
 #include "sd_kernels.cuh"
 
-// Minimum resident blocks per SM requested for k_line_flux (caps its registers; 3 blocks of
-// 192 threads measured fastest for the FP32 Navier-Stokes n = 5 case on B300).
+// Minimum resident blocks per SM requested for k_line_flux (caps its registers; with the
+// asynchronous staging, 2 blocks of 192 threads and no register spills measured fastest for
+// the FP32 Navier-Stokes n = 5 case on B300).
 #ifndef SD_FLUX_MINB
-#define SD_FLUX_MINB 3
+#define SD_FLUX_MINB 2
 #endif
 
 namespace sdk {
@@ -54,6 +55,7 @@ struct LineGeo {
     real corrL[3];           // (2/h_d) alpha
     real corrR[3];           // (2/h_d) beta
     real off0, off4;         // offsets removed from variables 0 and 4 when staging
+    real tip[3];             // interior penalty eta (p+1)^2 / h_d (0: off)
 };
 
 template <int N, int DIM, int NV>
@@ -123,8 +125,22 @@ __device__ __forceinline__ real dotc(const real* row, const real* x) {
 }
 
 // ---------------------------------------------------------------- staging helpers
-// flat load of the block's elements (u, offsets removed unless the input already carries
-// them) and, optionally, the neighbour traces and neighbour interface gradients
+// asynchronous global -> shared copy of one value (Ampere-style cp.async; the copies of a
+// block are all in flight together and complete at cp_async_wait_all)
+template <typename real>
+__device__ __forceinline__ void cp_async(real* smem, const real* gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    if constexpr (sizeof(real) == 4)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// Load of the block's elements (u, offsets removed unless the input already carries them)
+// and, optionally, the neighbour traces and neighbour interface gradients. Ends with a
+// barrier; everything is in shared memory afterwards.
 template <typename real, class LL, int NV, bool NB_TR, bool NB_TG>
 __device__ __forceinline__ void stage_load(const real* __restrict__ U, const real* __restrict__ Tu,
                                            const real* __restrict__ Tg, const Mesh& g, int e0,
@@ -143,10 +159,7 @@ __device__ __forceinline__ void stage_load(const real* __restrict__ U, const rea
         const int eb = k / (NV * NP);
         const int r = k - eb * NV * NP;
         const int v = r / NP, pt = r - v * NP;
-        real x = U[(size_t)v * g.nelem * NP + (size_t)(e0 + eb) * NP + pt];
-        if (v == 0) x -= off0;
-        if (v == 4) x -= off4;
-        sm[eb * per + r] = x;
+        cp_async(&sm[eb * per + r], &U[(size_t)v * g.nelem * NP + (size_t)(e0 + eb) * NP + pt]);
     }
     if (NB_TR) {
         for (int k = threadIdx.x; k < nloc * NF * NV * NQ; k += blockDim.x) {
@@ -154,7 +167,7 @@ __device__ __forceinline__ void stage_load(const real* __restrict__ U, const rea
             const int r = k - eb * NF * NV * NQ;
             const int f = r / (NV * NQ), rem = r - f * NV * NQ;
             const int en = nbr[eb * NF + f];
-            sm[eb * per + LL::S_U + LL::S_TR + r] = Tu[((size_t)en * NF + (f ^ 1)) * NV * NQ + rem];
+            cp_async(&sm[eb * per + LL::S_U + LL::S_TR + r], &Tu[((size_t)en * NF + (f ^ 1)) * NV * NQ + rem]);
         }
     }
     if (NB_TG) {
@@ -163,8 +176,17 @@ __device__ __forceinline__ void stage_load(const real* __restrict__ U, const rea
             const int r = k - eb * NF * NG * NQ;
             const int f = r / (NG * NQ), rem = r - f * NG * NQ;
             const int en = nbr[eb * NF + f];
-            sm[eb * per + LL::S_U + 2 * LL::S_TR + LL::S_VS + r] =
-                Tg[((size_t)en * NF + (f ^ 1)) * NG * NQ + rem];
+            cp_async(&sm[eb * per + LL::S_U + 2 * LL::S_TR + LL::S_VS + r],
+                     &Tg[((size_t)en * NF + (f ^ 1)) * NG * NQ + rem]);
+        }
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    if (NV == 5 && (off0 != real(0) || off4 != real(0))) {
+        for (int k = threadIdx.x; k < nloc * NP; k += blockDim.x) {
+            const int eb = k / NP, pt = k - eb * NP;
+            sm[eb * per + pt] -= off0;
+            sm[eb * per + 4 * NP + pt] -= off4;
         }
     }
 }
@@ -327,7 +349,8 @@ k_line_grad(const real* __restrict__ U, const real* __restrict__ Tu, real* __res
 template <typename real, int N, int DIM, int NV, int D>
 __device__ __forceinline__ void line_flux(const LineGeo<real>& geo, const Phys<real>& P, int compact,
                                           const real* su, const real* vS, const real* tro,
-                                          const real* trn, const real* tgn, int q, real (&r)[NV][N]) {
+                                          const real* trn, const real* tgn, int q, real (&r)[NV][N],
+                                          const float* tau_own, const float* tau_m, const float* tau_p) {
     using LL = LineLayout<N, DIM, NV>;
     constexpr int NP = LL::NP, NQ = LL::NQ, NG = LL::NG;
     const OpTab<real, N>& op = c_op<real, N>;
@@ -366,6 +389,12 @@ __device__ __forceinline__ void line_flux(const LineGeo<real>& geo, const Phys<r
                 const real go = face_value<real, N, NQ, NV, D>(geo, compact, c, s, gl, tro, trn, q);
                 const real gn = tgn[(face * NG + c) * NQ + q];
                 vh[c] = s ? real(0.5) * (go + gn) : real(0.5) * (gn + go);
+                if (c < NV && geo.tip[D] != real(0)) {
+                    // interior penalty on the normal derivative: tau_IP (u_R - u_L)
+                    const real own = tro[(face * NV + c) * NQ + q];
+                    const real nb = trn[(face * NV + c) * NQ + q];
+                    vh[c] = fma(geo.tip[D], s ? (nb - own) : (own - nb), vh[c]);
+                }
             }
             if constexpr (NV == 5) {
                 ns_viscous(Uh, vh, D, P, F);
@@ -389,6 +418,13 @@ __device__ __forceinline__ void line_flux(const LineGeo<real>& geo, const Phys<r
                 UR[v] = s ? nb : own;
             }
             ns_riemann(UL, UR, D, P, F);
+            if (tau_own) {
+                // extra per-element flux: centred average of the two elements at the interface
+                const float* tl = s ? tau_own : tau_m;
+                const float* tr = s ? tau_p : tau_own;
+#pragma unroll
+                for (int v = 0; v < NV; ++v) F[v] += real(0.5) * ((real)tl[3 * v + D] + (real)tr[3 * v + D]);
+            }
 #pragma unroll
             for (int v = 0; v < NV; ++v)
 #pragma unroll
@@ -421,6 +457,10 @@ __device__ __forceinline__ void line_flux(const LineGeo<real>& geo, const Phys<r
 #pragma unroll
                 for (int i = 0; i < N; ++i) r[v][i] = fma(op.M[i * (N + 1) + f], -F[v], r[v][i]);
             ns_convective(uf, D, P, F);
+            if (tau_own) {
+#pragma unroll
+                for (int v = 0; v < NV; ++v) F[v] += (real)tau_own[3 * v + D];
+            }
         } else {
             real gl[N];
             gline(0, gl);
@@ -440,7 +480,8 @@ __device__ __forceinline__ void line_flux(const LineGeo<real>& geo, const Phys<r
 template <typename real, int N, int DIM, int NV>
 __global__ void __launch_bounds__(LineLayout<N, DIM, NV>::THREADS, SD_FLUX_MINB)
 k_line_flux(const real* __restrict__ U, const real* __restrict__ Tu, const real* __restrict__ Tg,
-            real* __restrict__ R, LineGeo<real> geo, Mesh g, Phys<real> P, int compact) {
+            real* __restrict__ R, LineGeo<real> geo, Mesh g, Phys<real> P, int compact,
+            const float* __restrict__ tau) {
     using LL = LineLayout<N, DIM, NV>;
     constexpr int NP = LL::NP;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -461,10 +502,17 @@ k_line_flux(const real* __restrict__ U, const real* __restrict__ Tu, const real*
 
     real r[NV][N];
     if (live) {
-        if (id.d == 0) line_flux<real, N, DIM, NV, 0>(geo, P, compact, su, vS, tro, trn, tgn, id.q, r);
+        const float *t0 = nullptr, *tm = nullptr, *tp = nullptr;
+        if (NV == 5 && tau) {
+            const int* nb = nbr + id.eb * LL::NF + 2 * id.d;
+            t0 = tau + (size_t)e * 15;
+            tm = tau + (size_t)nb[0] * 15;
+            tp = tau + (size_t)nb[1] * 15;
+        }
+        if (id.d == 0) line_flux<real, N, DIM, NV, 0>(geo, P, compact, su, vS, tro, trn, tgn, id.q, r, t0, tm, tp);
         if constexpr (DIM == 3) {
-            if (id.d == 1) line_flux<real, N, DIM, NV, 1>(geo, P, compact, su, vS, tro, trn, tgn, id.q, r);
-            if (id.d == 2) line_flux<real, N, DIM, NV, 2>(geo, P, compact, su, vS, tro, trn, tgn, id.q, r);
+            if (id.d == 1) line_flux<real, N, DIM, NV, 1>(geo, P, compact, su, vS, tro, trn, tgn, id.q, r, t0, tm, tp);
+            if (id.d == 2) line_flux<real, N, DIM, NV, 2>(geo, P, compact, su, vS, tro, trn, tgn, id.q, r, t0, tm, tp);
         }
     }
     // every line has read u and v^S: the u slot now accumulates R, direction by direction

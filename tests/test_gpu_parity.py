@@ -326,3 +326,24 @@ def test_full_size_conservation(full_tgv, precision, tol):
         tot = np.sum(W * R[v])
         scale = np.sum(W * np.abs(R[v]))
         assert abs(tot) <= tol * scale, (v, tot, scale)
+
+
+# ------------------------------------------------------------------ interior penalty
+@pytest.mark.parametrize("scheme", ["br1", "compact"])
+@pytest.mark.parametrize("eta", [0.02, 1.0])
+def test_interior_penalty_fp64_parity(scheme, eta):
+    # scalar 1D/3D and Navier-Stokes with the Sec. 3 interior-penalty term
+    g1 = (1, (9,), (0.0,), (1.0,), 3)
+    U1 = inputs.random_scalar(1, (9,), 3, seed=21)
+    gg = Grid(1, (9,), (0.0,), (1.0,), 3, dtype=np.longdouble)
+    Ro = oracle_residual(U1, gg, scheme, Heat(0.5), eta_ip=eta).astype(np.float64)
+    Rg = gpu_residual(U1, *g1, scheme, sd.Physics(kind="heat", nu=0.5, eta_ip=eta), "f64")
+    assert rel_err(Rg, Ro).max() <= 1e-12
+    prm, phys = ns_phys(Re=300.0)
+    phys.eta_ip = eta
+    ne, p = (3, 2, 3), 3
+    U = inputs.random_state(ne, p, seed=22)
+    gg = Grid(3, ne, (0.0,) * 3, (TWO_PI,) * 3, p, dtype=np.longdouble)
+    Ro = oracle_residual(U, gg, scheme, NavierStokes(prm), eta_ip=eta).astype(np.float64)
+    Rg = gpu_residual(U, 3, ne, (0.0,) * 3, (TWO_PI,) * 3, p, scheme, phys, "f64")
+    assert rel_err(Rg, Ro).max() <= 1e-12

@@ -66,9 +66,12 @@ def test_fp32_dissipation_matches_fp64(trajectories, capsys):
 
 
 def test_initial_state_and_conservation(trajectories):
-    # FP32 residuals conserve to FP32 round-off per step, FP64 ones to FP64 round-off;
-    # the state update adds that round-off every step (8000 steps)
-    tol = {"f64": (1e-11, 1e-10), "f32": (1e-9, 1e-7)}
+    # FP64 residuals conserve to FP64 round-off per step (accumulated over 8000 steps).
+    # FP32 residuals use FP32-rounded operator weights, for which sum_i w_i M_if equals
+    # +-delta only to ~6e-8 relative: each interface leaks that fraction of its flux, and
+    # the energy flux (rho E + p) u carries rho E ~ 180 at Ma = 0.1, so the total energy
+    # drifts systematically at the 1e-8 level over the run.
+    tol = {"f64": (1e-11, 1e-10), "f32": (1e-7, 1e-7)}
     for prec, rec in trajectories.items():
         r0 = rec[0]
         rel, mom = tol[prec]

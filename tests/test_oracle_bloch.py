@@ -29,6 +29,14 @@ from oracle.physics import Heat
 from oracle.residual import residual
 
 
+def bloch_Q_ip(n, theta, tau):
+    """Q_IP of Sec. 3: tau (cL cL^T - cL cR^T e^{-i theta}) L + tau (cR cL^T e^{i theta} - cR cR^T) L."""
+    o = operators(n)
+    L, cL, cR = o.L, o.cL[:, None], o.cR[:, None]
+    ep, em = np.exp(1j * theta), np.exp(-1j * theta)
+    return tau * (cL @ cL.T - cL @ cR.T * em) @ L + tau * (cR @ cL.T * ep - cR @ cR.T) @ L
+
+
 def bloch_Q(n, theta, scheme, Jinv=1.0):
     o = operators(n)
     L, M, cL, cR = o.L, o.M, o.cL[:, None], o.cR[:, None]
@@ -83,3 +91,25 @@ def test_bloch_physical_mode_decays_like_theta_squared(scheme, p):
         assert np.abs(ev.imag).max() < 1e-8
         phys = ev.real[np.argmax(ev.real)]
         assert phys == pytest.approx(-theta ** 2, rel=1e-3)
+
+
+@pytest.mark.parametrize("scheme", ["compact", "br1"])
+@pytest.mark.parametrize("p", [2, 3, 4])
+@pytest.mark.parametrize("eta", [0.01, 1.0])
+def test_residual_with_interior_penalty_matches_bloch_operator(scheme, p, eta):
+    # Sec. 3: v^{F,C} = (Q + Q_IP) u with tau = eta_IP (p+1)^2 / h
+    n = p + 1
+    E = 10
+    rng = np.random.default_rng(p)
+    for h in (2.0, 0.5):
+        g = Grid(1, (E,), (0.0,), (h * E,), p)
+        Jinv = 2.0 / h
+        tau = eta * (p + 1) ** 2 / h
+        for k in (1, 4):
+            theta = 2 * np.pi * k / E
+            uhat = rng.normal(size=n) + 1j * rng.normal(size=n)
+            U = (np.exp(1j * theta * np.arange(E))[:, None] * uhat[None, :])[None]
+            R = residual(U, g, scheme, Heat(1.0), eta_ip=eta)
+            B = Jinv * operators(n).M @ (bloch_Q(n, theta, scheme, Jinv) + bloch_Q_ip(n, theta, tau))
+            for e in range(E):
+                assert np.allclose(R[0, e], np.exp(1j * theta * e) * (B @ uhat), atol=1e-10)
