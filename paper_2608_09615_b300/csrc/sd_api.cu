@@ -241,7 +241,7 @@ static void free_closure(sd_ctx* c) {
 static void free_all(sd_ctx* c) {
     free_closure(c);
     if (c->cl_tmode) cudaFree(c->cl_tmode);
-    void* ptrs[] = {c->Tu, c->Tg, c->S, c->K, c->rA, c->rB, c->rC, c->dW,
+    void* ptrs[] = {c->Tu, c->Tg, c->S, c->K, c->rA, c->rB, c->rC, c->rX, c->dW,
                     c->partial, c->dsum, c->hU, c->hR};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -346,9 +346,10 @@ extern "C" sd_status sd_init(const sd_mesh* mesh, int p, sd_scheme scheme, const
     else alloc((void**)&c->Tu64, c->ntu * sizeof(double));
     alloc(&c->S, S * c->esize);
     alloc(&c->K, S * c->esize);
-    alloc((void**)&c->rA, S * sizeof(double));
-    alloc((void**)&c->rB, S * sizeof(double));
-    alloc((void**)&c->rC, S * sizeof(double));
+    alloc(&c->rA, S * c->esize);
+    alloc(&c->rB, S * c->esize);
+    alloc(&c->rC, S * c->esize);
+    if (prec == SD_F32) alloc(&c->rX, S * c->esize);
     alloc((void**)&c->dW, SD_MAX_N * sizeof(double));
     alloc((void**)&c->cl_tmode, (SD_MAX_N * SD_MAX_N + SD_MAX_N) * sizeof(double));
     const int tpe = ((np + 31) / 32) * 32;
@@ -467,62 +468,206 @@ static int grid_for(size_t n) {
     return (int)std::min<size_t>(std::max<size_t>(b, 1), 148 * 16);
 }
 
-template <typename real>
-static sd_status rk_step_t(sd_ctx* c, double* U, double dt, sd_rk rk) {
+// ------------------------------------------------------------------ Runge-Kutta kernels, FP32 residual
+// Each thread handles EWB values spaced one grid apart per iteration; all loads of an
+// iteration are issued before any arithmetic, so every thread keeps several independent
+// requests in flight (these kernels are bound by HBM bandwidth).
+namespace sdk {
+constexpr int EWB = 4;
+
+__global__ void k_ssp_inc(int k, double* __restrict__ U, float* __restrict__ A, float* __restrict__ B,
+                          float* __restrict__ C, const float* __restrict__ K, const float* __restrict__ X,
+                          float* __restrict__ S, SSPInc c, size_t n) {
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t base = (size_t)blockIdx.x * blockDim.x + threadIdx.x; base < n; base += EWB * stride) {
+        float kk[EWB], x[EWB], a[EWB], b[EWB], cc[EWB];
+        double u[EWB];
+#pragma unroll
+        for (int w = 0; w < EWB; ++w) {
+            const size_t i = base + w * stride;
+            if (i >= n) continue;
+            kk[w] = K[i];
+            if (k < 4) x[w] = X[i];
+            if (k == 1 || k == 3) b[w] = B[i];
+            if (k == 1 || k >= 3) a[w] = A[i];
+            if (k == 4) { cc[w] = C[i]; u[w] = U[i]; }
+            if (k == 2) b[w] = B[i];
+        }
+#pragma unroll
+        for (int w = 0; w < EWB; ++w) {
+            const size_t i = base + w * stride;
+            if (i >= n) continue;
+            if (k == 0) {
+                const float d = c.b10 * kk[w];
+                A[i] = d;
+                S[i] = x[w] + d;
+            } else if (k == 1) {
+                const float d = fmaf(c.a21, a[w], c.b21 * kk[w]);
+                B[i] = d;
+                S[i] = x[w] + d;
+            } else if (k == 2) {
+                const float d = fmaf(c.a32, b[w], c.b32 * kk[w]);
+                A[i] = d;
+                S[i] = x[w] + d;
+            } else if (k == 3) {
+                C[i] = fmaf(c.a52, b[w], fmaf(c.a53, a[w], c.b53 * kk[w]));
+                const float d = fmaf(c.a43, a[w], c.b43 * kk[w]);
+                A[i] = d;
+                S[i] = x[w] + d;
+            } else {
+                U[i] = u[w] + (double)fmaf(c.a54, a[w], fmaf(c.b54, kk[w], cc[w]));
+            }
+        }
+    }
+}
+
+__global__ void k_rk4_inc(int k, double* __restrict__ U, float* __restrict__ A, const float* __restrict__ K,
+                          const float* __restrict__ X, float* __restrict__ S, RK4Inc c, size_t n) {
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t base = (size_t)blockIdx.x * blockDim.x + threadIdx.x; base < n; base += EWB * stride) {
+        float kk[EWB], x[EWB], a[EWB];
+        double u[EWB];
+#pragma unroll
+        for (int w = 0; w < EWB; ++w) {
+            const size_t i = base + w * stride;
+            if (i >= n) continue;
+            kk[w] = K[i];
+            if (k < 3) x[w] = X[i];
+            if (k > 0) a[w] = A[i];
+            if (k == 3) u[w] = U[i];
+        }
+#pragma unroll
+        for (int w = 0; w < EWB; ++w) {
+            const size_t i = base + w * stride;
+            if (i >= n) continue;
+            if (k == 0) {
+                A[i] = c.h6 * kk[w];
+                S[i] = fmaf(c.h2, kk[w], x[w]);
+            } else if (k == 1) {
+                A[i] = fmaf(c.h3, kk[w], a[w]);
+                S[i] = fmaf(c.h2, kk[w], x[w]);
+            } else if (k == 2) {
+                A[i] = fmaf(c.h3, kk[w], a[w]);
+                S[i] = fmaf(c.h1, kk[w], x[w]);
+            } else {
+                U[i] = u[w] + (double)fmaf(c.h6, kk[w], a[w]);
+            }
+        }
+    }
+}
+
+__global__ void k_lsrk_inc(int k, int last, double* __restrict__ U, float* __restrict__ W,
+                           float* __restrict__ D, const float* __restrict__ K, const float* __restrict__ X,
+                           float* __restrict__ S, float a, float dt, float b, size_t n) {
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t base = (size_t)blockIdx.x * blockDim.x + threadIdx.x; base < n; base += EWB * stride) {
+        float kk[EWB], x[EWB], w0[EWB], d0[EWB];
+        double u[EWB];
+#pragma unroll
+        for (int w = 0; w < EWB; ++w) {
+            const size_t i = base + w * stride;
+            if (i >= n) continue;
+            kk[w] = K[i];
+            w0[w] = k > 0 ? W[i] : 0.0f;
+            d0[w] = k > 0 ? D[i] : 0.0f;
+            if (last) u[w] = U[i];
+            else x[w] = X[i];
+        }
+#pragma unroll
+        for (int w = 0; w < EWB; ++w) {
+            const size_t i = base + w * stride;
+            if (i >= n) continue;
+            const float wn = fmaf(a, w0[w], dt * kk[w]);
+            const float dn = fmaf(b, wn, d0[w]);
+            if (last) {
+                U[i] = u[w] + (double)dn;
+            } else {
+                W[i] = wn;
+                D[i] = dn;
+                S[i] = x[w] + dn;
+            }
+        }
+    }
+}
+}  // namespace sdk
+
+
+// Shu-Osher coefficients of SSPRK(5,4) (Spiteri & Ruuth 2002)
+static const sdk::SSPCoef kSSP = {0.391752226571890, 0.444370493651235, 0.555629506348765,
+                                  0.368410593050371, 0.620101851488403, 0.379898148511597,
+                                  0.251891774271694, 0.178079954393132, 0.821920045606868,
+                                  0.544974750228521, 0.517231671970585, 0.096059710526147,
+                                  0.063692468666290, 0.386708617503269, 0.226007483236906};
+// Carpenter & Kennedy (1994) LSRK(5,4) coefficients
+static const double kLSA[5] = {0.0, -567301805773.0 / 1357537059087.0, -2404267990393.0 / 2016746695238.0,
+                               -3550918686646.0 / 2091501179385.0, -1275806237668.0 / 842570457699.0};
+static const double kLSB[5] = {1432997174477.0 / 9575080441755.0, 5161836677717.0 / 13612068292357.0,
+                               1720146321549.0 / 2090206949498.0, 3134564353537.0 / 4481467310338.0,
+                               2277821191437.0 / 14882151754819.0};
+
+// FP64 contexts: full FP64 stage states (the parity build)
+static sd_status rk_step_f64(sd_ctx* c, double* U, double dt, sd_rk rk) {
     const size_t n = c->nstate;
-    real* S = (real*)c->S;
-    real* K = (real*)c->K;
+    double* S = (double*)c->S;
+    double* K = (double*)c->K;
+    double *rA = (double*)c->rA, *rB = (double*)c->rB, *rC = (double*)c->rC;
     const int gb = grid_for(n);
     cudaStream_t st = c->stream;
-    // every stage input, the first included, is a copy in the residual precision with the
-    // reference offsets removed in FP64 before rounding
     sdk::StageOff so;
     so.npts = c->npts;
     sdk::stage_offsets(c, so.off0, so.off4);
     auto res = [&](const void* in) -> sd_status { return residual_any(c, in, K, 1); };
-    const void* first = S;
     sdi_prof_begin(c, SD_K_OTHER);
-    sdk::k_to_real<real><<<gb, 256, 0, st>>>(U, S, n, so);
+    sdk::k_to_real<double><<<gb, 256, 0, st>>>(U, S, n, so);
     sdi_prof_end(c, SD_K_OTHER);
     sd_status s;
-    if (rk == SD_RK4) {
-        for (int k = 0; k < 4; ++k) {
-            if ((s = res(k == 0 ? first : (const void*)S)) != SD_OK) return s;
-            sdi_prof_begin(c, SD_K_OTHER);
-            sdk::k_rk4<real><<<gb, 256, 0, st>>>(k, U, c->rA, K, S, dt, n, so);
-            sdi_prof_end(c, SD_K_OTHER);
-        }
-    } else if (rk == SD_SSPRK54) {
-        const sdk::SSPCoef cf = {0.391752226571890, 0.444370493651235, 0.555629506348765,
-                                 0.368410593050371, 0.620101851488403, 0.379898148511597,
-                                 0.251891774271694, 0.178079954393132, 0.821920045606868,
-                                 0.544974750228521, 0.517231671970585, 0.096059710526147,
-                                 0.063692468666290, 0.386708617503269, 0.226007483236906};
-        for (int k = 0; k < 5; ++k) {
-            if ((s = res(k == 0 ? first : (const void*)S)) != SD_OK) return s;
-            sdi_prof_begin(c, SD_K_OTHER);
-            sdk::k_ssp<real><<<gb, 256, 0, st>>>(k, U, c->rA, c->rB, c->rC, K, S, dt, cf, n, so);
-            sdi_prof_end(c, SD_K_OTHER);
-        }
-    } else if (rk == SD_LSRK54) {
-        static const double A[5] = {0.0, -567301805773.0 / 1357537059087.0,
-                                    -2404267990393.0 / 2016746695238.0,
-                                    -3550918686646.0 / 2091501179385.0,
-                                    -1275806237668.0 / 842570457699.0};
-        static const double B[5] = {1432997174477.0 / 9575080441755.0,
-                                    5161836677717.0 / 13612068292357.0,
-                                    1720146321549.0 / 2090206949498.0,
-                                    3134564353537.0 / 4481467310338.0,
-                                    2277821191437.0 / 14882151754819.0};
-        for (int k = 0; k < 5; ++k) {
-            if ((s = res(k == 0 ? first : (const void*)S)) != SD_OK) return s;
-            sdi_prof_begin(c, SD_K_OTHER);
-            sdk::k_lsrk<real><<<gb, 256, 0, st>>>(U, c->rA, K, S, A[k], B[k], dt, n, so);
-            sdi_prof_end(c, SD_K_OTHER);
-        }
-    } else {
-        sdi_set_error("bad Runge-Kutta scheme");
-        return SD_EINVAL;
+    const int nst = rk == SD_RK4 ? 4 : 5;
+    for (int k = 0; k < nst; ++k) {
+        if ((s = res(S)) != SD_OK) return s;
+        sdi_prof_begin(c, SD_K_OTHER);
+        if (rk == SD_RK4) sdk::k_rk4<double><<<gb, 256, 0, st>>>(k, U, rA, K, S, dt, n, so);
+        else if (rk == SD_SSPRK54) sdk::k_ssp<double><<<gb, 256, 0, st>>>(k, U, rA, rB, rC, K, S, dt, kSSP, n, so);
+        else sdk::k_lsrk<double><<<gb, 256, 0, st>>>(U, rA, K, S, kLSA[k], kLSB[k], dt, n, so);
+        sdi_prof_end(c, SD_K_OTHER);
+    }
+    CK(cudaGetLastError());
+    return SD_OK;
+}
+
+// FP32 contexts: FP32 stage increments, FP64 accumulation of the state once per step
+static sd_status rk_step_f32(sd_ctx* c, double* U, double dt, sd_rk rk) {
+    const size_t n = c->nstate;
+    float* S = (float*)c->S;
+    float* K = (float*)c->K;
+    float* X = (float*)c->rX;
+    float *rA = (float*)c->rA, *rB = (float*)c->rB, *rC = (float*)c->rC;
+    const int gb = grid_for((n + sdk::EWB - 1) / sdk::EWB);
+    cudaStream_t st = c->stream;
+    sdk::StageOff so;
+    so.npts = c->npts;
+    sdk::stage_offsets(c, so.off0, so.off4);
+    auto res = [&](const void* in) -> sd_status { return residual_any(c, in, K, 1); };
+    sdi_prof_begin(c, SD_K_OTHER);
+    sdk::k_to_real<float><<<grid_for(n), 256, 0, st>>>(U, X, n, so);
+    sdi_prof_end(c, SD_K_OTHER);
+    sd_status s;
+    const int nst = rk == SD_RK4 ? 4 : 5;
+    const sdk::SSPCoef& a = kSSP;
+    const sdk::SSPInc ci = {(float)(a.a10 * dt), (float)a.a21, (float)(a.b21 * dt), (float)a.a32,
+                            (float)(a.b32 * dt), (float)a.a43, (float)(a.b43 * dt), (float)a.a52,
+                            (float)a.a53, (float)(a.b53 * dt), (float)a.a54, (float)(a.b54 * dt)};
+    const sdk::RK4Inc c4 = {(float)(0.5 * dt), (float)dt, (float)(dt / 6.0), (float)(dt / 3.0)};
+    for (int k = 0; k < nst; ++k) {
+        if ((s = res(k == 0 ? (const void*)X : (const void*)S)) != SD_OK) return s;
+        sdi_prof_begin(c, SD_K_OTHER);
+        if (rk == SD_RK4)
+            sdk::k_rk4_inc<<<gb, 256, 0, st>>>(k, U, rA, K, X, S, c4, n);
+        else if (rk == SD_SSPRK54)
+            sdk::k_ssp_inc<<<gb, 256, 0, st>>>(k, U, rA, rB, rC, K, X, S, ci, n);
+        else
+            sdk::k_lsrk_inc<<<gb, 256, 0, st>>>(k, k == 4, U, rA, rB, K, X, S, (float)kLSA[k], (float)dt,
+                                                (float)kLSB[k], n);
+        sdi_prof_end(c, SD_K_OTHER);
     }
     CK(cudaGetLastError());
     return SD_OK;
@@ -532,8 +677,12 @@ extern "C" sd_status sd_rk_step(sd_ctx* c, double* U64, double t, double dt, sd_
     (void)t;
     if (!c || !U64) { sdi_set_error("null argument"); return SD_EINVAL; }
     if (!(dt > 0.0) || !isfinite(dt)) { sdi_set_error("dt must be positive and finite"); return SD_EINVAL; }
-    if (c->prec == SD_F32) return rk_step_t<float>(c, U64, dt, rk);
-    return rk_step_t<double>(c, U64, dt, rk);
+    if (rk != SD_RK4 && rk != SD_SSPRK54 && rk != SD_LSRK54) {
+        sdi_set_error("bad Runge-Kutta scheme");
+        return SD_EINVAL;
+    }
+    if (c->prec == SD_F32) return rk_step_f32(c, U64, dt, rk);
+    return rk_step_f64(c, U64, dt, rk);
 }
 
 // ------------------------------------------------------------------ diagnostics

@@ -40,7 +40,10 @@ struct sd_ctx {
     double* Tu64;            // FP64 traces for diagnostics (== Tu when prec is F64)
     void* S;                 // stage input of the residual precision
     void* K;                 // stage residual of the residual precision
-    double *rA, *rB, *rC;    // FP64 Runge-Kutta registers
+    // Runge-Kutta registers, in the residual precision: FP64 contexts keep full stage
+    // states, FP32 contexts keep stage increments (the state itself accumulates in FP64)
+    void *rA, *rB, *rC;
+    void* rX;                // FP32 contexts: the step's start state minus the offsets
     double* dW;              // Gauss weights (device, n values)
     double* partial;         // diagnostics block partials
     double* dsum;            // diagnostics totals (device)

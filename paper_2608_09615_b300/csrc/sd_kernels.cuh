@@ -545,4 +545,32 @@ __global__ void k_lsrk(double* __restrict__ U, double* __restrict__ dU, const re
     }
 }
 
+// ------------------------------------------------------------------ Runge-Kutta, FP32 residual
+// Increment form used by FP32 contexts. Within one step every stage state is u_j = U + d_j,
+// with U the FP64 state at the start of the step and d_0 = 0. The Shu-Osher weights of each
+// stage sum to one, so the stage combination only involves the increments d_j = O(dt). The
+// increments live in FP32: their rounding (6e-8 of an O(dt) quantity) is far below the FP32
+// residual's own error. The conserved state accumulates in FP64 once per step: U <- U + d_s.
+// The stage input is X + d_j in FP32, where X = U - offsets is rounded once per step.
+// Coefficients arrive premultiplied by dt (FP64 products rounded once).
+struct SSPInc {
+    float b10, a21, b21, a32, b32, a43, b43, a52, a53, b53, a54, b54;
+};
+
+__global__ void k_ssp_inc(int k, double* __restrict__ U, float* __restrict__ A, float* __restrict__ B,
+                          float* __restrict__ C, const float* __restrict__ K, const float* __restrict__ X,
+                          float* __restrict__ S, SSPInc c, size_t n);
+
+struct RK4Inc {
+    float h2, h1, h6, h3;     // dt/2, dt, dt/6, dt/3
+};
+
+__global__ void k_rk4_inc(int k, double* __restrict__ U, float* __restrict__ A, const float* __restrict__ K,
+                          const float* __restrict__ X, float* __restrict__ S, RK4Inc c, size_t n);
+
+// Low-storage form: W <- a W + dt K, D <- D + b W (D = the running increment of U).
+__global__ void k_lsrk_inc(int k, int last, double* __restrict__ U, float* __restrict__ W,
+                           float* __restrict__ D, const float* __restrict__ K, const float* __restrict__ X,
+                           float* __restrict__ S, float a, float dt, float b, size_t n);
+
 }  // namespace sdk

@@ -27,11 +27,15 @@
 
 #include "sd_kernels.cuh"
 
-// Minimum resident blocks per SM requested for k_line_flux (caps its registers; with the
-// asynchronous staging, 2 blocks of 192 threads and no register spills measured fastest for
-// the FP32 Navier-Stokes n = 5 case on B300).
-#ifndef SD_FLUX_MINB
-#define SD_FLUX_MINB 2
+// Threads per block the line kernels aim for (whole element groups of DIM warps), and the
+// register cap of k_line_flux (further limited to what one block of the layout can use).
+// 192 threads and no cap below the 143 registers the FP32 Navier-Stokes n = 5 case needs
+// without spills measured fastest among the layouts tried on B300.
+#ifndef SD_LINE_THREADS
+#define SD_LINE_THREADS 192
+#endif
+#ifndef SD_FLUX_MAXNREG
+#define SD_FLUX_MAXNREG 168
 #endif
 
 namespace sdk {
@@ -67,7 +71,7 @@ struct LineLayout {
     static constexpr int EPW = NQ <= 32 ? 32 / NQ : 1;            // elements per warp
     static constexpr int WPD = NQ <= 32 ? 1 : (NQ + 31) / 32;     // warps per direction
     static constexpr int UNIT = DIM * WPD * 32;                   // threads per element group
-    static constexpr int UPB = UNIT >= 192 ? 1 : 192 / UNIT;      // groups per block
+    static constexpr int UPB = UNIT >= SD_LINE_THREADS ? 1 : SD_LINE_THREADS / UNIT;  // groups per block
     static constexpr int THREADS = UPB * UNIT;
     static constexpr int EB = UPB * EPW;                          // elements per block
     static constexpr int S_U = NV * NP;
@@ -78,6 +82,8 @@ struct LineLayout {
     static constexpr int PER_GRAD = S_U + 2 * S_TR + S_VS;
     static constexpr int PER_FLUX = S_U + 2 * S_TR + S_VS + S_TG;
     static constexpr int NBR_BYTES = ((EB * NF * 4 + 15) / 16) * 16;   // neighbour table
+    static constexpr int REG_FIT = (65536 / THREADS) / 8 * 8;
+    static constexpr int FLUX_REGS = SD_FLUX_MAXNREG < REG_FIT ? SD_FLUX_MAXNREG : (REG_FIT < 255 ? REG_FIT : 255);
 };
 
 struct LineId {
@@ -368,12 +374,12 @@ __device__ __forceinline__ void line_flux(const LineGeo<real>& geo, const Phys<r
 
     // interface flux points (f = 0 and f = N): Riemann flux of the two traces minus the
     // viscous flux of the averaged state and the averaged gradient; the viscous part is
-    // applied first so that its temporaries are dead before the Riemann solver runs
+    // evaluated first so that only its 5 results stay live while the Riemann solver runs
 #pragma unroll 1
     for (int s = 0; s < 2; ++s) {
         const int face = 2 * D + s;
         const int f = s ? N : 0;
-        real F[NV];
+        real F[NV], Fv[NV];
         {
             real Uh[NV], vh[NG];
 #pragma unroll
@@ -396,17 +402,8 @@ __device__ __forceinline__ void line_flux(const LineGeo<real>& geo, const Phys<r
                     vh[c] = fma(geo.tip[D], s ? (nb - own) : (own - nb), vh[c]);
                 }
             }
-            if constexpr (NV == 5) {
-                ns_viscous(Uh, vh, D, P, F);
-#pragma unroll
-                for (int v = 0; v < NV; ++v) F[v] = -F[v];
-            } else {
-                F[0] = scalar_flux(P, Uh[0], vh[0]);
-            }
-#pragma unroll
-            for (int v = 0; v < NV; ++v)
-#pragma unroll
-                for (int i = 0; i < N; ++i) r[v][i] = fma(op.M[i * (N + 1) + f], F[v], r[v][i]);
+            if constexpr (NV == 5) ns_viscous(Uh, vh, D, P, Fv);
+            else F[0] = scalar_flux(P, Uh[0], vh[0]);
         }
         if constexpr (NV == 5) {
             real UL[NV], UR[NV];
@@ -426,10 +423,12 @@ __device__ __forceinline__ void line_flux(const LineGeo<real>& geo, const Phys<r
                 for (int v = 0; v < NV; ++v) F[v] += real(0.5) * ((real)tl[3 * v + D] + (real)tr[3 * v + D]);
             }
 #pragma unroll
-            for (int v = 0; v < NV; ++v)
-#pragma unroll
-                for (int i = 0; i < N; ++i) r[v][i] = fma(op.M[i * (N + 1) + f], F[v], r[v][i]);
+            for (int v = 0; v < NV; ++v) F[v] -= Fv[v];
         }
+#pragma unroll
+        for (int v = 0; v < NV; ++v)
+#pragma unroll
+            for (int i = 0; i < N; ++i) r[v][i] = fma(op.M[i * (N + 1) + f], F[v], r[v][i]);
     }
     // interior flux points: extrapolated solution and gradient (Eq. aux:v:std:2d)
     real u[NV][N];
@@ -451,16 +450,15 @@ __device__ __forceinline__ void line_flux(const LineGeo<real>& geo, const Phys<r
                 gline(c, gl);
                 gf[c] = dotc<real, N>(Lr, gl);
             }
-            ns_viscous(uf, gf, D, P, F);
-#pragma unroll
-            for (int v = 0; v < NV; ++v)
-#pragma unroll
-                for (int i = 0; i < N; ++i) r[v][i] = fma(op.M[i * (N + 1) + f], -F[v], r[v][i]);
+            real Fv[NV];
+            ns_viscous(uf, gf, D, P, Fv);
             ns_convective(uf, D, P, F);
             if (tau_own) {
 #pragma unroll
                 for (int v = 0; v < NV; ++v) F[v] += (real)tau_own[3 * v + D];
             }
+#pragma unroll
+            for (int v = 0; v < NV; ++v) F[v] -= Fv[v];
         } else {
             real gl[N];
             gline(0, gl);
@@ -478,7 +476,7 @@ __device__ __forceinline__ void line_flux(const LineGeo<real>& geo, const Phys<r
 }
 
 template <typename real, int N, int DIM, int NV>
-__global__ void __launch_bounds__(LineLayout<N, DIM, NV>::THREADS, SD_FLUX_MINB)
+__global__ void __maxnreg__((LineLayout<N, DIM, NV>::FLUX_REGS))
 k_line_flux(const real* __restrict__ U, const real* __restrict__ Tu, const real* __restrict__ Tg,
             real* __restrict__ R, LineGeo<real> geo, Mesh g, Phys<real> P, int compact,
             const float* __restrict__ tau) {
