@@ -52,22 +52,25 @@ def peaks():
 
 
 def residual_flops_per_element(n, nv=5, ng=9, dim=3):
-    """Algorithmic FP32 flops of one NS residual per element (FMA = 2 flops), by the
-    operation counts of the method's steps: one 1D sweep of length n costs 2n - 1 flops;
-    per element: own face traces, v^S (D sweep + two corrections), solution and 9 gradient
-    components at the interior flux points, the flux there (~85 flops), each interface
-    once (own interface gradient + Roe ~150 + viscous ~60 + averages), the M divergence;
-    plus the gradient pass (traces, v^S, interface gradients)."""
+    """Algorithmic FP32 flops per element of the NS residual kernels (FMA = 2 flops), by the
+    operation counts of the method's steps; one 1D sweep of length n costs 2n - 1 flops.
+    k_line_grad: own face traces, v^S (D sweep + two corrections), the 9 own interface
+    gradient components of the 2 dim faces (compact correction included).
+    k_face_flux: the dim faces owned by the element (its +d faces), each point once:
+    averages of the state and gradient (2 (nv + ng)), viscous flux (~60) and Roe (~150) plus
+    the combination (~25).
+    k_line_flux: own face traces, v^S, the solution and 9 gradient components at the n - 1
+    interior flux points of every line, the flux there (~85 flops), and the M divergence of
+    all n + 1 flux points."""
     npnt, nq, nf = n ** dim, n ** (dim - 1), 2 * dim
     sw = 2 * n - 1
     trace = nf * nv * nq * sw
     vs = nv * dim * npnt * (sw + 4)
     interior = dim * (n - 1) * nq * ((nv + ng) * sw + 85)
-    faces = dim * nq * (ng * (sw + 2) + 235)
     div = dim * nv * npnt * (2 * (n + 1) - 1 + 2)
-    flux_kernel = trace + vs + interior + faces + div
-    grad_kernel = trace + vs + nf * ng * nq * (sw + 2)
-    return flux_kernel, grad_kernel
+    return {"flux": trace + vs + interior + div,
+            "face": dim * nq * (2 * (nv + ng) + 235),
+            "grad": trace + vs + nf * ng * nq * (sw + 2)}
 
 
 class ClockSampler:
@@ -284,19 +287,17 @@ def main():
     value = job_value(world, npts, ms)
     final = ctx.diagnostics(U64, t, raise_nonfinite=False)
 
-    # roofline of the dominant kernel (flux/divergence), from the live CUDA events
+    # roofline of the dominant kernel (k_line_flux), from the live CUDA events
     hbm, smax, peak_kind = peaks()
-    flux_ms, flux_n = prof["flux_div"]
-    grad_ms, grad_n = prof["grad"]
-    tr_ms, tr_n = prof["trace"]
-    ot_ms, ot_n = prof["other"]
-    f_flux, f_grad = residual_flops_per_element(P + 1)
+    kms = {k: prof[k][0] / max(prof[k][1], 1) for k in prof}
+    flops = residual_flops_per_element(P + 1)
     nelem = int(np.prod(ne))
-    flux_avg_ms = flux_ms / max(flux_n, 1)
+    flux_avg_ms = kms["flux_div"]
     fp32_peak = 148 * 128 * 2 * smax * 1e6 / 1e12      # TFLOP/s at the maximum SM clock
-    achieved = f_flux * nelem / (flux_avg_ms * 1e-3) / 1e12
+    achieved = flops["flux"] * nelem / (flux_avg_ms * 1e-3) / 1e12
     alg_bytes_res = 2 * 5 * npts * 4                    # read U, write R (FP32)
-    res_ms = (flux_ms + grad_ms + tr_ms) / max(flux_n, 1)
+    res_ms = sum(kms[k] for k in ("trace", "grad", "face", "flux_div"))
+    res_alu = sum(flops.values()) * nelem / (res_ms * 1e-3) / 1e12
 
     # standalone residual rates, FP32 and FP64
     Ug32 = U64.float()
@@ -362,19 +363,20 @@ def main():
                        "l2": "inputs larger than L2 (FP32 state %.0f MB, FP64 state %.0f MB)"
                              % (5 * npts * 4 / 1e6, 5 * npts * 8 / 1e6),
                        "parallelism": "replicas" if world > 1 else "single GPU"},
-            "roofline": {"bound": "alu", "kernel": "k_flux_div",
+            "roofline": {"bound": "alu", "kernel": "k_line_flux",
                          "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                          "frac": achieved / fp32_peak, "traffic": None,
                          "peak_source": "FP32 CUDA-core peak 148 SM x 128 lanes x 2 x %.0f MHz "
                                         "(derived)" % smax,
+                         "flops_per_element": flops["flux"],
                          "avg_launch_ms": flux_avg_ms,
-                         "hbm_frac_of_%s" % peak_kind:
-                             alg_bytes_res / (res_ms * 1e-3) / 1e9 / hbm,
+                         "residual": {"ms": res_ms, "alu_tflops": res_alu, "alu_frac": res_alu / fp32_peak,
+                                      "hbm_frac_of_%s" % peak_kind: alg_bytes_res / (res_ms * 1e-3) / 1e9 / hbm,
+                                      "algorithmic_bytes": alg_bytes_res},
                          "hbm_peak_gbs": hbm},
-            "kernels_ms": {"trace": tr_ms / max(tr_n, 1), "grad": grad_ms / max(grad_n, 1),
-                           "flux_div": flux_avg_ms, "rk_and_other_per_launch": ot_ms / max(ot_n, 1),
-                           "launches": {"trace": tr_n, "grad": grad_n, "flux_div": flux_n,
-                                        "other": ot_n}},
+            "kernels_ms": {"trace": kms["trace"], "grad": kms["grad"], "face": kms["face"],
+                           "flux_div": flux_avg_ms, "rk_and_other_per_launch": kms["other"],
+                           "launches": {k: prof[k][1] for k in prof}},
             "residual_dof_per_s": {"f32": npts / (res32_ms * 1e-3), "f64": npts / (res64_ms * 1e-3),
                                    "f32_ms": res32_ms, "f64_ms": res64_ms},
             "e2e": {"value": npts / e2e_s, "unit": UNIT, "call": "sd_residual_host (FP32)",

@@ -141,10 +141,10 @@ sd_status sd_diagnostics(sd_ctx* ctx, const double* U64, double t, sd_diag* out)
 
 /* Profiling (CUDA events on the context stream). While enabled, every kernel launch of
  * the context is bracketed by two events; sd_profile_read synchronises the stream and
- * returns, per kernel class (SD_K_TRACE, SD_K_GRAD, SD_K_FLUX, SD_K_OTHER), the summed
+ * returns, per kernel class (SD_K_TRACE, SD_K_GRAD, SD_K_FLUX, SD_K_OTHER, SD_K_FACE), the summed
  * device time in ms and the launch count since the last read, then resets them.
  * Enabling creates the events (no device memory); disabling destroys them. */
-enum { SD_K_TRACE = 0, SD_K_GRAD = 1, SD_K_FLUX = 2, SD_K_OTHER = 3, SD_K_COUNT = 4 };
+enum { SD_K_TRACE = 0, SD_K_GRAD = 1, SD_K_FLUX = 2, SD_K_OTHER = 3, SD_K_FACE = 4, SD_K_COUNT = 5 };
 sd_status sd_profile_enable(sd_ctx* ctx, int on);
 sd_status sd_profile_read(sd_ctx* ctx, double* ms, long long* launches);
 

@@ -59,7 +59,7 @@ EXPORTS = ("sd_init", "sd_destroy", "sd_set_stream", "sd_state_size", "sd_nvar",
            "sd_mlp_adam", "sd_residual_f32_noalloc", "sd_set_flux_tau", "sd_closure_data",
            "sd_filter_matrix", "sd_filter_project", "sd_closure_targets", "sd_colstats",
            "sd_standardise", "sd_unstandardise", "sd_closure_enable")
-KERNEL_CLASSES = ("trace", "grad", "flux_div", "other")
+KERNEL_CLASSES = ("trace", "grad", "flux_div", "other", "face")
 
 _lib_handle = None
 
@@ -311,8 +311,8 @@ class SD:
         _check(load_library().sd_profile_enable(self._ctx, int(bool(on))), "sd_profile_enable")
 
     def profile_read(self):
-        ms = (ctypes.c_double * 4)()
-        cnt = (ctypes.c_longlong * 4)()
+        ms = (ctypes.c_double * len(KERNEL_CLASSES))()
+        cnt = (ctypes.c_longlong * len(KERNEL_CLASSES))()
         _check(load_library().sd_profile_read(self._ctx, ms, cnt), "sd_profile_read")
         return {k: (ms[i], cnt[i]) for i, k in enumerate(KERNEL_CLASSES)}
 

@@ -241,7 +241,7 @@ static void free_closure(sd_ctx* c) {
 static void free_all(sd_ctx* c) {
     free_closure(c);
     if (c->cl_tmode) cudaFree(c->cl_tmode);
-    void* ptrs[] = {c->Tu, c->Tg, c->S, c->K, c->rA, c->rB, c->rC, c->rX, c->dW,
+    void* ptrs[] = {c->Tu, c->Tg, c->Fh, c->S, c->K, c->rA, c->rB, c->rC, c->rX, c->dW,
                     c->partial, c->dsum, c->hU, c->hR};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -312,6 +312,7 @@ extern "C" sd_status sd_init(const sd_mesh* mesh, int p, sd_scheme scheme, const
     c->nstate = c->npts * c->nvar;
     c->ntu = (size_t)c->nelem * 2 * c->dim * c->nvar * nq;
     c->ntg = (size_t)c->nelem * 2 * c->dim * c->ngrad * nq;
+    c->nfh = (size_t)c->nelem * c->dim * c->nvar * nq;
     c->esize = prec == SD_F32 ? sizeof(float) : sizeof(double);
 
     // shared memory feasibility of the element-staged kernels (line layout of sd_line.cuh:
@@ -342,6 +343,7 @@ extern "C" sd_status sd_init(const sd_mesh* mesh, int p, sd_scheme scheme, const
     };
     alloc(&c->Tu, c->ntu * c->esize);
     alloc(&c->Tg, c->ntg * c->esize);
+    alloc(&c->Fh, c->nfh * c->esize);
     if (prec == SD_F64) c->Tu64 = (double*)c->Tu;
     else alloc((void**)&c->Tu64, c->ntu * sizeof(double));
     alloc(&c->S, S * c->esize);

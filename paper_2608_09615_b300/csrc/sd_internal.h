@@ -32,11 +32,12 @@ struct sd_ctx {
     // sizes
     size_t npts;             // points per variable = nelem * n^dim
     size_t nstate;           // nvar * npts
-    size_t ntu, ntg;         // trace buffer sizes (values)
+    size_t ntu, ntg, nfh;    // trace and interface-flux buffer sizes (values)
     size_t esize;            // bytes per value of the residual precision
     // scratch owned by the context
     void* Tu;                // face traces of u        [nelem][2dim][nvar][n^(dim-1)]
     void* Tg;                // face gradient values    [nelem][2dim][ngrad][n^(dim-1)]
+    void* Fh;                // interface fluxes        [dim][nelem][nvar][n^(dim-1)] (+d face of each element)
     double* Tu64;            // FP64 traces for diagnostics (== Tu when prec is F64)
     void* S;                 // stage input of the residual precision
     void* K;                 // stage residual of the residual precision

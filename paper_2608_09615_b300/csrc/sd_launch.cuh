@@ -205,6 +205,7 @@ static sd_status residual_impl(sd_ctx* c, const real* U, real* R, int offset_in)
     if (!set_smem(k_line_trace<real, N, DIM, NV>, st) || !set_smem(k_line_grad<real, N, DIM, NV>, sg) ||
         !set_smem(k_line_flux<real, N, DIM, NV>, sf))
         return SD_EUNSUPPORTED;
+    real* Fh = static_cast<real*>(c->Fh);
     sdi_prof_begin(c, SD_K_TRACE);
     k_line_trace<real, N, DIM, NV><<<blocks, LL::THREADS, st, c->stream>>>(U, Tu, geo, g);
     sdi_prof_end(c, SD_K_TRACE);
@@ -215,8 +216,12 @@ static sd_status residual_impl(sd_ctx* c, const real* U, real* R, int offset_in)
     sdi_prof_begin(c, SD_K_GRAD);
     k_line_grad<real, N, DIM, NV><<<blocks, LL::THREADS, sg, c->stream>>>(U, Tu, Tg, geo, g, compact);
     sdi_prof_end(c, SD_K_GRAD);
+    sdi_prof_begin(c, SD_K_FACE);
+    k_face_flux<real, N, DIM, NV><<<trace_blocks((long long)g.nelem * DIM * LL::NQ), 256, 0, c->stream>>>(
+        Tu, Tg, Fh, geo, g, P, c->tau);
+    sdi_prof_end(c, SD_K_FACE);
     sdi_prof_begin(c, SD_K_FLUX);
-    k_line_flux<real, N, DIM, NV><<<blocks, LL::THREADS, sf, c->stream>>>(U, Tu, Tg, R, geo, g, P, compact, c->tau);
+    k_line_flux<real, N, DIM, NV><<<blocks, LL::THREADS, sf, c->stream>>>(U, Tu, Fh, R, geo, g, P, c->tau);
     sdi_prof_end(c, SD_K_FLUX);
     const cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) {

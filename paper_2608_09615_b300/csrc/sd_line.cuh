@@ -14,12 +14,15 @@
 //   k_line_trace  u at the 2*DIM faces (step 1, interface rows)            -> Tu
 //   k_line_grad   common-solution corrections, v^S (Eq. w:e), own interface
 //                 gradients (BR1 Eq. v:e / compact closed form)            -> Tg
-//   k_line_flux   interior gradients (Eq. aux:v:std:2d), interface averages
-//                 (Eq. c:aux:v:2d), fluxes (Sec. 4.4 / Eq. pme), divergence -> R
+//   k_face_flux   one thread per interface point, each interface once: the
+//                 Riemann flux of the two traces minus the viscous flux of the
+//                 averaged state and averaged gradient (Eqs. c:aux:v:2d, Sec. 4.4) -> Fh
+//   k_line_flux   interior gradients (Eq. aux:v:std:2d), interior fluxes
+//                 (Sec. 4.4 / Eq. pme) and the divergence with the interface
+//                 fluxes Fh at the line ends                               -> R
 // The three directions of k_line_flux add into R in the fixed order x, y, z, so results
-// are deterministic. Values that both elements of an interface compute (traces, delta,
-// own interface gradients) come from the same device functions with explicit fma
-// sequences, so the interface flux is single-valued and conservation holds to round-off.
+// are deterministic. The interface flux is computed once per interface point, so it is
+// single-valued and conservation holds to round-off.
 //
 // Navier-Stokes states are staged with the reference offsets removed from rho and rho E
 // (see ns_convective); Tu holds traces of the offset state.
@@ -78,9 +81,10 @@ struct LineLayout {
     static constexpr int S_TR = NF * NV * NQ;
     static constexpr int S_VS = NV * DIM * NP;
     static constexpr int S_TG = NF * NG * NQ;
+    static constexpr int S_FH = NF * NV * NQ;                      // interface fluxes of the 2*DIM faces
     static constexpr int PER_TRACE = S_U;
     static constexpr int PER_GRAD = S_U + 2 * S_TR + S_VS;
-    static constexpr int PER_FLUX = S_U + 2 * S_TR + S_VS + S_TG;
+    static constexpr int PER_FLUX = S_U + 2 * S_TR + S_VS + S_FH;
     static constexpr int NBR_BYTES = ((EB * NF * 4 + 15) / 16) * 16;   // neighbour table
     static constexpr int REG_FIT = (65536 / THREADS) / 8 * 8;
     static constexpr int FLUX_REGS = SD_FLUX_MAXNREG < REG_FIT ? SD_FLUX_MAXNREG : (REG_FIT < 255 ? REG_FIT : 255);
@@ -145,15 +149,16 @@ __device__ __forceinline__ void cp_async(real* smem, const real* gmem) {
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 // Load of the block's elements (u, offsets removed unless the input already carries them)
-// and, optionally, the neighbour traces and neighbour interface gradients. Ends with a
-// barrier; everything is in shared memory afterwards.
-template <typename real, class LL, int NV, bool NB_TR, bool NB_TG>
+// and, optionally, the neighbour traces and the interface fluxes of the element's faces.
+// Ends with a barrier; everything is in shared memory afterwards.
+// Fh layout: [d][e][v][q], the flux through the face between e and its +d neighbour.
+template <typename real, class LL, int NV, bool NB_TR, bool FH>
 __device__ __forceinline__ void stage_load(const real* __restrict__ U, const real* __restrict__ Tu,
-                                           const real* __restrict__ Tg, const Mesh& g, int e0,
+                                           const real* __restrict__ Fh, const Mesh& g, int e0,
                                            real* sm, int per, real off0, real off4, int* nbr) {
-    constexpr int NP = LL::NP, NQ = LL::NQ, NF = LL::NF, NG = LL::NG;
+    constexpr int NP = LL::NP, NQ = LL::NQ, NF = LL::NF;
     const int nloc = min(LL::EB, g.nelem - e0);
-    if (NB_TR || NB_TG) {
+    if (NB_TR || FH) {
         // neighbour element of every (element, face), computed once
         for (int k = threadIdx.x; k < nloc * NF; k += blockDim.x) {
             const int eb = k / NF, f = k - eb * NF;
@@ -176,14 +181,15 @@ __device__ __forceinline__ void stage_load(const real* __restrict__ U, const rea
             cp_async(&sm[eb * per + LL::S_U + LL::S_TR + r], &Tu[((size_t)en * NF + (f ^ 1)) * NV * NQ + rem]);
         }
     }
-    if (NB_TG) {
-        for (int k = threadIdx.x; k < nloc * NF * NG * NQ; k += blockDim.x) {
-            const int eb = k / (NF * NG * NQ);
-            const int r = k - eb * NF * NG * NQ;
-            const int f = r / (NG * NQ), rem = r - f * NG * NQ;
-            const int en = nbr[eb * NF + f];
+    if (FH) {
+        for (int k = threadIdx.x; k < nloc * NF * NV * NQ; k += blockDim.x) {
+            const int eb = k / (NF * NV * NQ);
+            const int r = k - eb * NF * NV * NQ;
+            const int f = r / (NV * NQ), rem = r - f * NV * NQ;
+            // face 2d+1 is this element's +d face; face 2d is the +d face of its -d neighbour
+            const int ef = (f & 1) ? e0 + eb : nbr[eb * NF + f];
             cp_async(&sm[eb * per + LL::S_U + 2 * LL::S_TR + LL::S_VS + r],
-                     &Tg[((size_t)en * NF + (f ^ 1)) * NG * NQ + rem]);
+                     &Fh[((size_t)(f >> 1) * g.nelem + ef) * NV * NQ + rem]);
         }
     }
     cp_async_wait_all();
@@ -351,84 +357,111 @@ k_line_grad(const real* __restrict__ U, const real* __restrict__ Tu, real* __res
     }
 }
 
-// fluxes along D at the n+1 flux points of line q and their divergence on the line
+// common flux through one interface point along compile-time direction D: UL, gL are the
+// traces and interface gradients of the element on the -D side, UR, gR of the one on the
+// +D side (Eqs. c:flux, c:aux:v:2d; Sec. 4.4 option (a): Riemann flux of the two traces
+// minus the viscous flux of the averaged state and gradient)
+template <typename real, int NV, int NG, int D>
+__device__ __forceinline__ void interface_flux(const LineGeo<real>& geo, const Phys<real>& P, const real* UL,
+                                               const real* UR, const real* gL, const real* gR,
+                                               const float* tauL, const float* tauR, real* F) {
+    real Uh[NV], vh[NG];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) Uh[v] = real(0.5) * (UL[v] + UR[v]);
+#pragma unroll
+    for (int c = 0; c < NG; ++c) {
+        vh[c] = real(0.5) * (gL[c] + gR[c]);
+        // interior penalty on the normal derivative: tau_IP (u_R - u_L)
+        if (c < NV && geo.tip[D] != real(0)) vh[c] = fma(geo.tip[D], UR[c] - UL[c], vh[c]);
+    }
+    if constexpr (NV == 5) {
+        real Fv[NV];
+        ns_viscous(Uh, vh, D, P, Fv);
+        ns_riemann(UL, UR, D, P, F);
+        if (tauL) {
+            // extra per-element flux: centred average of the two elements at the interface
+#pragma unroll
+            for (int v = 0; v < NV; ++v) F[v] += real(0.5) * ((real)tauL[3 * v + D] + (real)tauR[3 * v + D]);
+        }
+#pragma unroll
+        for (int v = 0; v < NV; ++v) F[v] -= Fv[v];
+    } else {
+        F[0] = scalar_flux(P, Uh[0], vh[0]);
+    }
+}
+
 template <typename real, int N, int DIM, int NV, int D>
-__device__ __forceinline__ void line_flux(const LineGeo<real>& geo, const Phys<real>& P, int compact,
-                                          const real* su, const real* vS, const real* tro,
-                                          const real* trn, const real* tgn, int q, real (&r)[NV][N],
-                                          const float* tau_own, const float* tau_m, const float* tau_p) {
+__device__ __forceinline__ void face_point(const real* __restrict__ Tu, const real* __restrict__ Tg,
+                                           real* __restrict__ Fh, const LineGeo<real>& geo, const Mesh& g,
+                                           const Phys<real>& P, const float* __restrict__ tau, int e, int q) {
+    using LL = LineLayout<N, DIM, NV>;
+    constexpr int NQ = LL::NQ, NF = LL::NF, NG = LL::NG;
+    const int en = neighbour(g, e, D, 1);
+    const real* tl = Tu + ((size_t)e * NF + 2 * D + 1) * NV * NQ + q;
+    const real* tr = Tu + ((size_t)en * NF + 2 * D) * NV * NQ + q;
+    const real* gl = Tg + ((size_t)e * NF + 2 * D + 1) * NG * NQ + q;
+    const real* gr = Tg + ((size_t)en * NF + 2 * D) * NG * NQ + q;
+    real UL[NV], UR[NV], gL[NG], gR[NG], F[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+        UL[v] = tl[v * NQ];
+        UR[v] = tr[v * NQ];
+    }
+#pragma unroll
+    for (int c = 0; c < NG; ++c) {
+        gL[c] = gl[c * NQ];
+        gR[c] = gr[c * NQ];
+    }
+    const float* tauL = nullptr;
+    const float* tauR = nullptr;
+    if (NV == 5 && tau) {
+        tauL = tau + (size_t)e * 15;
+        tauR = tau + (size_t)en * 15;
+    }
+    interface_flux<real, NV, NG, D>(geo, P, UL, UR, gL, gR, tauL, tauR, F);
+    real* out = Fh + ((size_t)D * g.nelem + e) * NV * NQ + q;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) out[v * NQ] = F[v];
+}
+
+// One thread per interface point; thread index (d, e, q) with q fastest, so the direction
+// is uniform over long runs of threads and each direction has its own code path.
+template <typename real, int N, int DIM, int NV>
+__global__ void __launch_bounds__(256)
+k_face_flux(const real* __restrict__ Tu, const real* __restrict__ Tg, real* __restrict__ Fh,
+            LineGeo<real> geo, Mesh g, Phys<real> P, const float* __restrict__ tau) {
+    constexpr int NQ = ipow(N, DIM - 1);
+    const long long per_d = (long long)g.nelem * NQ;
+    const long long total = per_d * DIM;
+    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int d = (int)(idx / per_d);
+        const long long r = idx - d * per_d;
+        const int e = (int)(r / NQ), q = (int)(r - (long long)e * NQ);
+        if (d == 0) face_point<real, N, DIM, NV, 0>(Tu, Tg, Fh, geo, g, P, tau, e, q);
+        if constexpr (DIM == 3) {
+            if (d == 1) face_point<real, N, DIM, NV, 1>(Tu, Tg, Fh, geo, g, P, tau, e, q);
+            if (d == 2) face_point<real, N, DIM, NV, 2>(Tu, Tg, Fh, geo, g, P, tau, e, q);
+        }
+    }
+}
+
+// fluxes along D at the n+1 flux points of line q and their divergence on the line: the
+// interface fluxes at f = 0 and f = N come from Fh, the n-1 interior ones are evaluated here
+template <typename real, int N, int DIM, int NV, int D>
+__device__ __forceinline__ void line_flux(const LineGeo<real>& geo, const Phys<real>& P, const real* su,
+                                          const real* vS, const real* fh, int q, real (&r)[NV][N],
+                                          const float* tau_own) {
     using LL = LineLayout<N, DIM, NV>;
     constexpr int NP = LL::NP, NQ = LL::NQ, NG = LL::NG;
     const OpTab<real, N>& op = c_op<real, N>;
-    // gradient line of component c, read from shared memory where it is needed
-    auto gline = [&](int c, real* gl) {
-        int v, m;
-        comp_map<NV>(D, c, v, m);
+    // interface flux points (f = 0 and f = N)
 #pragma unroll
-        for (int i = 0; i < N; ++i) gl[i] = vS[(v * DIM + m) * NP + lpt<N, D>(i, q)];
-    };
+    for (int v = 0; v < NV; ++v) {
+        const real F0 = fh[((2 * D) * NV + v) * NQ + q];
+        const real FN = fh[((2 * D + 1) * NV + v) * NQ + q];
 #pragma unroll
-    for (int v = 0; v < NV; ++v)
-#pragma unroll
-        for (int i = 0; i < N; ++i) r[v][i] = real(0);
-
-    // interface flux points (f = 0 and f = N): Riemann flux of the two traces minus the
-    // viscous flux of the averaged state and the averaged gradient; the viscous part is
-    // evaluated first so that only its 5 results stay live while the Riemann solver runs
-#pragma unroll 1
-    for (int s = 0; s < 2; ++s) {
-        const int face = 2 * D + s;
-        const int f = s ? N : 0;
-        real F[NV], Fv[NV];
-        {
-            real Uh[NV], vh[NG];
-#pragma unroll
-            for (int v = 0; v < NV; ++v) {
-                const real own = tro[(face * NV + v) * NQ + q];
-                const real nb = trn[(face * NV + v) * NQ + q];
-                Uh[v] = s ? real(0.5) * (own + nb) : real(0.5) * (nb + own);
-            }
-#pragma unroll
-            for (int c = 0; c < NG; ++c) {
-                real gl[N];
-                gline(c, gl);
-                const real go = face_value<real, N, NQ, NV, D>(geo, compact, c, s, gl, tro, trn, q);
-                const real gn = tgn[(face * NG + c) * NQ + q];
-                vh[c] = s ? real(0.5) * (go + gn) : real(0.5) * (gn + go);
-                if (c < NV && geo.tip[D] != real(0)) {
-                    // interior penalty on the normal derivative: tau_IP (u_R - u_L)
-                    const real own = tro[(face * NV + c) * NQ + q];
-                    const real nb = trn[(face * NV + c) * NQ + q];
-                    vh[c] = fma(geo.tip[D], s ? (nb - own) : (own - nb), vh[c]);
-                }
-            }
-            if constexpr (NV == 5) ns_viscous(Uh, vh, D, P, Fv);
-            else F[0] = scalar_flux(P, Uh[0], vh[0]);
-        }
-        if constexpr (NV == 5) {
-            real UL[NV], UR[NV];
-#pragma unroll
-            for (int v = 0; v < NV; ++v) {
-                const real own = tro[(face * NV + v) * NQ + q];
-                const real nb = trn[(face * NV + v) * NQ + q];
-                UL[v] = s ? own : nb;
-                UR[v] = s ? nb : own;
-            }
-            ns_riemann(UL, UR, D, P, F);
-            if (tau_own) {
-                // extra per-element flux: centred average of the two elements at the interface
-                const float* tl = s ? tau_own : tau_m;
-                const float* tr = s ? tau_p : tau_own;
-#pragma unroll
-                for (int v = 0; v < NV; ++v) F[v] += real(0.5) * ((real)tl[3 * v + D] + (real)tr[3 * v + D]);
-            }
-#pragma unroll
-            for (int v = 0; v < NV; ++v) F[v] -= Fv[v];
-        }
-#pragma unroll
-        for (int v = 0; v < NV; ++v)
-#pragma unroll
-            for (int i = 0; i < N; ++i) r[v][i] = fma(op.M[i * (N + 1) + f], F[v], r[v][i]);
+        for (int i = 0; i < N; ++i) r[v][i] = fma(op.M[i * (N + 1) + N], FN, op.M[i * (N + 1)] * F0);
     }
     // interior flux points: extrapolated solution and gradient (Eq. aux:v:std:2d)
     real u[NV][N];
@@ -446,8 +479,11 @@ __device__ __forceinline__ void line_flux(const LineGeo<real>& geo, const Phys<r
             real gf[NG];
 #pragma unroll
             for (int c = 0; c < NG; ++c) {
+                int v, m;
+                comp_map<NV>(D, c, v, m);
                 real gl[N];
-                gline(c, gl);
+#pragma unroll
+                for (int i = 0; i < N; ++i) gl[i] = vS[(v * DIM + m) * NP + lpt<N, D>(i, q)];
                 gf[c] = dotc<real, N>(Lr, gl);
             }
             real Fv[NV];
@@ -461,7 +497,8 @@ __device__ __forceinline__ void line_flux(const LineGeo<real>& geo, const Phys<r
             for (int v = 0; v < NV; ++v) F[v] -= Fv[v];
         } else {
             real gl[N];
-            gline(0, gl);
+#pragma unroll
+            for (int i = 0; i < N; ++i) gl[i] = vS[D * NP + lpt<N, D>(i, q)];
             F[0] = scalar_flux(P, uf[0], dotc<real, N>(Lr, gl));
         }
 #pragma unroll
@@ -477,16 +514,15 @@ __device__ __forceinline__ void line_flux(const LineGeo<real>& geo, const Phys<r
 
 template <typename real, int N, int DIM, int NV>
 __global__ void __maxnreg__((LineLayout<N, DIM, NV>::FLUX_REGS))
-k_line_flux(const real* __restrict__ U, const real* __restrict__ Tu, const real* __restrict__ Tg,
-            real* __restrict__ R, LineGeo<real> geo, Mesh g, Phys<real> P, int compact,
-            const float* __restrict__ tau) {
+k_line_flux(const real* __restrict__ U, const real* __restrict__ Tu, const real* __restrict__ Fh,
+            real* __restrict__ R, LineGeo<real> geo, Mesh g, Phys<real> P, const float* __restrict__ tau) {
     using LL = LineLayout<N, DIM, NV>;
     constexpr int NP = LL::NP;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     int* nbr = reinterpret_cast<int*>(smem_raw);
     real* sm = reinterpret_cast<real*>(smem_raw + LL::NBR_BYTES);
     const int e0 = blockIdx.x * LL::EB;
-    stage_load<real, LL, NV, true, true>(U, Tu, Tg, g, e0, sm, LL::PER_FLUX, geo.off0, geo.off4, nbr);
+    stage_load<real, LL, NV, true, true>(U, Tu, Fh, g, e0, sm, LL::PER_FLUX, geo.off0, geo.off4, nbr);
     __syncthreads();
     const LineId id = line_id<LL>(threadIdx.x);
     const int e = e0 + id.eb;
@@ -495,22 +531,16 @@ k_line_flux(const real* __restrict__ U, const real* __restrict__ Tu, const real*
     real* tro = su + LL::S_U;
     real* trn = tro + LL::S_TR;
     real* vS = trn + LL::S_TR;
-    real* tgn = vS + LL::S_VS;
+    real* fh = vS + LL::S_VS;
     prologue<real, N, DIM, NV>(geo, id, live, su, tro, trn, vS);
 
     real r[NV][N];
     if (live) {
-        const float *t0 = nullptr, *tm = nullptr, *tp = nullptr;
-        if (NV == 5 && tau) {
-            const int* nb = nbr + id.eb * LL::NF + 2 * id.d;
-            t0 = tau + (size_t)e * 15;
-            tm = tau + (size_t)nb[0] * 15;
-            tp = tau + (size_t)nb[1] * 15;
-        }
-        if (id.d == 0) line_flux<real, N, DIM, NV, 0>(geo, P, compact, su, vS, tro, trn, tgn, id.q, r, t0, tm, tp);
+        const float* t0 = (NV == 5 && tau) ? tau + (size_t)e * 15 : nullptr;
+        if (id.d == 0) line_flux<real, N, DIM, NV, 0>(geo, P, su, vS, fh, id.q, r, t0);
         if constexpr (DIM == 3) {
-            if (id.d == 1) line_flux<real, N, DIM, NV, 1>(geo, P, compact, su, vS, tro, trn, tgn, id.q, r, t0, tm, tp);
-            if (id.d == 2) line_flux<real, N, DIM, NV, 2>(geo, P, compact, su, vS, tro, trn, tgn, id.q, r, t0, tm, tp);
+            if (id.d == 1) line_flux<real, N, DIM, NV, 1>(geo, P, su, vS, fh, id.q, r, t0);
+            if (id.d == 2) line_flux<real, N, DIM, NV, 2>(geo, P, su, vS, fh, id.q, r, t0);
         }
     }
     // every line has read u and v^S: the u slot now accumulates R, direction by direction

@@ -14,8 +14,8 @@
 
 #include "sd_internal.h"
 
-// Scratch of the allocation-free path: the face traces of u followed by the interface
-// gradient components of every element. Every call rewrites all the values it reads, so
+// Scratch of the allocation-free path: the face traces of u, the interface gradient
+// components and the interface fluxes of every element. Every call rewrites all the values it reads, so
 // nothing has to be cleared between calls; calls that overlap on the GPU share it and race.
 static __device__ __align__(256) float g_noalloc_scratch[SD_NOALLOC_SCRATCH_FLOATS];
 
@@ -89,6 +89,7 @@ static sd_status prepare(const sd_mesh* mesh, int p, sd_scheme scheme, const sd_
     c->nstate = c->npts * c->nvar;
     c->ntu = (size_t)c->nelem * 2 * c->dim * c->nvar * nq;
     c->ntg = (size_t)c->nelem * 2 * c->dim * c->ngrad * nq;
+    c->nfh = (size_t)c->nelem * c->dim * c->nvar * nq;
     c->esize = sizeof(float);
     return SD_OK;
 }
@@ -100,11 +101,12 @@ extern "C" sd_status sd_residual_f32_noalloc(const sd_mesh* mesh, int p, sd_sche
     sd_ctx c;
     sd_status st = prepare(mesh, p, scheme, phys, stream, &c);
     if (st != SD_OK) return st;
-    const size_t tu = ((c.ntu + 63) / 64) * 64;            // keeps Tg 256-byte aligned
-    if (tu + c.ntg > (size_t)SD_NOALLOC_SCRATCH_FLOATS) {
+    const size_t tu = ((c.ntu + 63) / 64) * 64;            // keeps Tg and Fh 256-byte aligned
+    const size_t tg = ((c.ntg + 63) / 64) * 64;
+    if (tu + tg + c.nfh > (size_t)SD_NOALLOC_SCRATCH_FLOATS) {
         sdi_set_error("sd_residual_f32_noalloc: this grid needs %zu scratch values; the static "
                       "scratch holds %d (use sd_init / sd_residual for larger grids)",
-                      tu + c.ntg, SD_NOALLOC_SCRATCH_FLOATS);
+                      tu + tg + c.nfh, SD_NOALLOC_SCRATCH_FLOATS);
         return SD_EINVAL;
     }
     if ((const void*)U < (const void*)(R + c.nstate) && (const void*)R < (const void*)(U + c.nstate)) {
@@ -117,5 +119,6 @@ extern "C" sd_status sd_residual_f32_noalloc(const sd_mesh* mesh, int p, sd_sche
     if ((st = sdi_upload_f32(&c)) != SD_OK) return st;
     c.Tu = base;
     c.Tg = base + tu;
+    c.Fh = base + tu + tg;
     return sdi_residual_f32(&c, U, R, 0);
 }
