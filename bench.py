@@ -73,6 +73,27 @@ def residual_flops_per_element(n, nv=5, ng=9, dim=3):
             "grad": trace + vs + nf * ng * nq * (sw + 2)}
 
 
+# DRAM traffic of one k_line_flux launch at 48^3 p=4 (FP32, compact), from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum; profiles/dram_residual_kernels_tgv48_p4_f32.md),
+# valid only while the kernel sources hash to the value recorded with it.
+FLUX_TRAFFIC = {"ne": 48, "bytes": 776636928 + 253750016,
+                "sources_sha256": "8ade5a60f41aedcb50b5ebfd26e47aad903b9128fc7e84b48e3c79480a3c2ad5"}
+FLUX_SOURCES = ("paper_2608_09615_b300/csrc/sd_line.cuh", "paper_2608_09615_b300/csrc/sd_kernels.cuh")
+
+
+def flux_traffic(ne):
+    """Recorded per-launch DRAM bytes of k_line_flux for this grid, or None when the grid
+    differs or the kernel sources changed since the capture."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in FLUX_SOURCES:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), f), "rb") as fh:
+            h.update(fh.read())
+    if h.hexdigest() != FLUX_TRAFFIC["sources_sha256"] or tuple(ne) != (FLUX_TRAFFIC["ne"],) * 3:
+        return None
+    return FLUX_TRAFFIC["bytes"]
+
+
 class ClockSampler:
     """nvidia-smi samples (200 ms) during the timed region."""
 
@@ -194,6 +215,57 @@ def run_reference(args, world):
     print(json.dumps(line), flush=True)
 
 
+def residual_rate(sd, torch, dim, ne, p, scheme, phys, precision, U, reps=10, lo=0.0, hi=2 * math.pi):
+    """ms per sd_residual call (CUDA events, after 2 warm-up calls) and DOF-updates/s."""
+    lo, hi = (lo,) * dim, (hi,) * dim
+    ctx = sd.SD(dim, ne, lo, hi, p, scheme, phys, precision)
+    Ug = torch.from_numpy(np.ascontiguousarray(U)).to("cuda", ctx.dtype)
+    R = torch.empty_like(Ug)
+    for _ in range(2):
+        ctx.residual(Ug, R)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        ctx.residual(Ug, R)
+    e1.record()
+    torch.cuda.synchronize()
+    ok = bool(torch.isfinite(R).all())
+    ctx.close()
+    ms = e0.elapsed_time(e1) / reps
+    npts = int(np.prod(ne)) * (p + 1) ** dim
+    return {"ms": ms, "dof_per_s": npts / (ms * 1e-3), "dof": npts, "finite": ok}
+
+
+def other_configs(sd, torch):
+    """Residual rates on the other workloads the method is run on: 3D heat (32^3, p = 3
+    and 4, nu = 0.01), the Taylor-Green grid with the BR1 scheme, Taylor-Green Re = 5000 on
+    64^3 p = 4, and the small 1D cases (heat 16 elements p = 3; porous medium m = 2,
+    128 elements p = 4), whose times are launch latency."""
+    out = {}
+    heat = sd.Physics(kind="heat", nu=0.01)
+    for p in (3, 4):
+        U, _, _ = inputs.heat_modes_3d((32,) * 3, p, seed=0)
+        for prec in ("f32", "f64"):
+            out["heat3d_32_p%d_compact_%s" % (p, prec)] = residual_rate(sd, torch, 3, (32,) * 3, p, "compact",
+                                                                          heat, prec, U)
+    U = inputs.tgv_3d(NE, P, perturb_seed=0)
+    out["tgv48_p4_re1600_br1_f32"] = residual_rate(sd, torch, 3, NE, P, "br1", sd.Physics(kind="ns"), "f32", U)
+    del U
+    U = inputs.tgv_3d((64,) * 3, P, perturb_seed=0)
+    out["tgv64_p4_re5000_compact_f32"] = residual_rate(sd, torch, 3, (64,) * 3, P, "compact",
+                                                       sd.Physics(kind="ns", Re=5000.0), "f32", U, reps=5)
+    del U
+    U = inputs.sin_1d(16, 3)
+    out["heat1d_16_p3_compact_f64"] = residual_rate(sd, torch, 1, (16,), 3, "compact",
+                                                    sd.Physics(kind="heat", nu=1.0), "f64", U, reps=100)
+    U = inputs.barenblatt_1d(128, 4, m=2.0)
+    out["pme1d_128_p4_compact_f64"] = residual_rate(sd, torch, 1, (128,), 4, "compact",
+                                                    sd.Physics(kind="pme", m_pme=2.0), "f64", U, reps=100,
+                                                    lo=-10.0, hi=10.0)
+    return out
+
+
 def residual_only(sd, torch, args, ne, lo, hi, phys):
     ctx = sd.SD(3, ne, lo, hi, P, args.scheme, phys, args.precision)
     npts = int(np.prod(ne)) * (P + 1) ** 3
@@ -226,6 +298,8 @@ def main():
                     help="only evaluate K residuals (FP32 unless --precision f64) and print the "
                          "per-kernel CUDA-event times; the small command used for ncu captures")
     ap.add_argument("--precision", default="f32", choices=["f32", "f64"])
+    ap.add_argument("--no-other-configs", action="store_true",
+                    help="skip the residual rates of the other workloads")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if args.impl == "reference":
@@ -341,6 +415,10 @@ def main():
     res64_ms = e0.elapsed_time(e1) / nrep64
     ctx64.close()
 
+    others = None
+    if rank == 0 and not args.no_other_configs:
+        others = other_configs(sd, torch)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         s = args.cpu_sample
@@ -365,7 +443,8 @@ def main():
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "roofline": {"bound": "alu", "kernel": "k_line_flux",
                          "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                         "frac": achieved / fp32_peak, "traffic": None,
+                         "frac": achieved / fp32_peak, "traffic": flux_traffic(ne),
+                         "traffic_unit": "bytes per launch (ncu dram read + write)",
                          "peak_source": "FP32 CUDA-core peak 148 SM x 128 lanes x 2 x %.0f MHz "
                                         "(derived)" % smax,
                          "flops_per_element": flops["flux"],
@@ -379,6 +458,7 @@ def main():
                            "launches": {k: prof[k][1] for k in prof}},
             "residual_dof_per_s": {"f32": npts / (res32_ms * 1e-3), "f64": npts / (res64_ms * 1e-3),
                                    "f32_ms": res32_ms, "f64_ms": res64_ms},
+            "other_configs_residual": others,
             "e2e": {"value": npts / e2e_s, "unit": UNIT, "call": "sd_residual_host (FP32)",
                     "h2d_bytes_per_step": 5 * npts * 4, "d2h_bytes_per_step": 5 * npts * 4},
             "gpu_launches": launches,

@@ -140,6 +140,31 @@ static bool set_smem(K kernel, size_t bytes) {
                                 (int)bytes) == cudaSuccess;
 }
 
+// number of SMs of a device (cached)
+inline int sm_count(int device) {
+    static std::mutex mu;
+    static int cache[64] = {0};
+    std::lock_guard<std::mutex> lock(mu);
+    const int d = device >= 0 && device < 64 ? device : 0;
+    if (!cache[d]) {
+        int n = 0;
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || n < 1) n = 1;
+        cache[d] = n;
+    }
+    return cache[d];
+}
+
+// grid of a persistent kernel: as many blocks as can be resident on the device, at most
+// one per element group
+template <typename K>
+static int persistent_grid(K kernel, int threads, size_t smem, long long ngroups, int device) {
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, threads, smem) != cudaSuccess || occ < 1)
+        occ = 1;
+    const long long g = (long long)occ * sm_count(device);
+    return (int)std::max<long long>(1, std::min<long long>(g, ngroups));
+}
+
 inline int trace_blocks(long long total) {
     long long b = (total + 255) / 256;
     return (int)std::min<long long>(std::max<long long>(b, 1), 148LL * 64);
@@ -198,30 +223,33 @@ static sd_status residual_impl(sd_ctx* c, const real* U, real* R, int offset_in)
     const int compact = c->scheme == SD_COMPACT ? 1 : 0;
     real* Tu = static_cast<real*>(c->Tu);
     real* Tg = static_cast<real*>(c->Tg);
-    const int blocks = (g.nelem + LL::EB - 1) / LL::EB;
-    const size_t st = (size_t)LL::EB * LL::PER_TRACE * sizeof(real);
-    const size_t sg = LL::NBR_BYTES + (size_t)LL::EB * LL::PER_GRAD * sizeof(real);
-    const size_t sf = LL::NBR_BYTES + (size_t)LL::EB * LL::PER_FLUX * sizeof(real);
+    const long long ngroups = (g.nelem + LL::EB - 1) / LL::EB;
+    const size_t st = TracePipe<real, LL>::BYTES;
+    const size_t sg = GradPipe<real, LL>::BYTES;
+    const size_t sf = FluxPipe<real, LL>::BYTES;
     if (!set_smem(k_line_trace<real, N, DIM, NV>, st) || !set_smem(k_line_grad<real, N, DIM, NV>, sg) ||
         !set_smem(k_line_flux<real, N, DIM, NV>, sf))
         return SD_EUNSUPPORTED;
+    const int bt = persistent_grid(k_line_trace<real, N, DIM, NV>, LL::THREADS, st, ngroups, c->device);
+    const int bg = persistent_grid(k_line_grad<real, N, DIM, NV>, LL::THREADS, sg, ngroups, c->device);
+    const int bf = persistent_grid(k_line_flux<real, N, DIM, NV>, LL::THREADS, sf, ngroups, c->device);
     real* Fh = static_cast<real*>(c->Fh);
     sdi_prof_begin(c, SD_K_TRACE);
-    k_line_trace<real, N, DIM, NV><<<blocks, LL::THREADS, st, c->stream>>>(U, Tu, geo, g);
+    k_line_trace<real, N, DIM, NV><<<bt, LL::THREADS, st, c->stream>>>(U, Tu, geo, g);
     sdi_prof_end(c, SD_K_TRACE);
     if (c->closure_on && NV == 5) {
         const sd_status cs = closure_stage<real, N>(c, U, offset_in);
         if (cs != SD_OK) return cs;
     }
     sdi_prof_begin(c, SD_K_GRAD);
-    k_line_grad<real, N, DIM, NV><<<blocks, LL::THREADS, sg, c->stream>>>(U, Tu, Tg, geo, g, compact);
+    k_line_grad<real, N, DIM, NV><<<bg, LL::THREADS, sg, c->stream>>>(U, Tu, Tg, geo, g, compact);
     sdi_prof_end(c, SD_K_GRAD);
     sdi_prof_begin(c, SD_K_FACE);
     k_face_flux<real, N, DIM, NV><<<trace_blocks((long long)g.nelem * DIM * LL::NQ), 256, 0, c->stream>>>(
         Tu, Tg, Fh, geo, g, P, c->tau);
     sdi_prof_end(c, SD_K_FACE);
     sdi_prof_begin(c, SD_K_FLUX);
-    k_line_flux<real, N, DIM, NV><<<blocks, LL::THREADS, sf, c->stream>>>(U, Tu, Fh, R, geo, g, P, c->tau);
+    k_line_flux<real, N, DIM, NV><<<bf, LL::THREADS, sf, c->stream>>>(U, Tu, Fh, R, geo, g, P, c->tau);
     sdi_prof_end(c, SD_K_FLUX);
     const cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) {
@@ -264,10 +292,12 @@ static sd_status closure_data_dispatch(sd_ctx* c, const real* U, float* X, doubl
         using LL = LineLayout<NN, 3, 5>;                                                         \
         const LineGeo<real> geo = make_geo<real>(c, offset_in);                                  \
         const Mesh g = make_mesh(c);                                                             \
-        const size_t stb = (size_t)LL::EB * LL::PER_TRACE * sizeof(real);                        \
+        const size_t stb = TracePipe<real, LL>::BYTES;                                           \
         if (!set_smem(k_line_trace<real, NN, 3, 5>, stb)) return SD_EUNSUPPORTED;               \
-        k_line_trace<real, NN, 3, 5><<<(g.nelem + LL::EB - 1) / LL::EB, LL::THREADS, stb,        \
-                                       c->stream>>>(U, static_cast<real*>(c->Tu), geo, g);       \
+        const int btr = persistent_grid(k_line_trace<real, NN, 3, 5>, LL::THREADS, stb,          \
+                                        (g.nelem + LL::EB - 1) / LL::EB, c->device);            \
+        k_line_trace<real, NN, 3, 5><<<btr, LL::THREADS, stb, c->stream>>>(                      \
+            U, static_cast<real*>(c->Tu), geo, g);                                               \
         if (X) st = features_impl<real, NN>(c, U, X, offset_in);                                 \
         if (st == SD_OK && means) st = fluxmean_impl<real, NN>(c, U, means, offset_in);          \
         return st;                                                                               \

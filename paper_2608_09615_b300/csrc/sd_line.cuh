@@ -147,6 +147,13 @@ __device__ __forceinline__ void cp_async(real* smem, const real* gmem) {
 }
 
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+
+// wait until at most NPEND of this thread's committed copy groups are still in flight
+template <int NPEND>
+__device__ __forceinline__ void cp_async_wait_group() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(NPEND) : "memory");
+}
 
 // Load of the block's elements (u, offsets removed unless the input already carries them)
 // and, optionally, the neighbour traces and the interface fluxes of the element's faces.
@@ -200,6 +207,127 @@ __device__ __forceinline__ void stage_load(const real* __restrict__ U, const rea
             sm[eb * per + pt] -= off0;
             sm[eb * per + 4 * NP + pt] -= off4;
         }
+    }
+}
+
+// ---------------------------------------------------------------- pipelined staging
+// The residual kernels are persistent: block b walks over the element groups b, b + grid,
+// b + 2 grid, ... and keeps two shared-memory copies of the loaded data, so the copies of
+// the next group are in flight while the current group is computed. Per element, the
+// double-buffered part holds u, then (NB_TR) the neighbour traces, then (FH) the interface
+// fluxes; the values the kernel computes itself (own traces, v^S: WORK values per element)
+// live in a single work area. Where two copies do not fit in shared memory (the largest n
+// in FP64) one copy is used and the loads of a group are not overlapped.
+template <class LL, bool NB_TR, bool FH, typename real, int WORK>
+struct Pipe {
+    static constexpr int LOAD = LL::S_U + (NB_TR ? LL::S_TR : 0) + (FH ? LL::S_FH : 0);
+    static constexpr int OFF_TR = LL::S_U;                           // neighbour traces
+    static constexpr int OFF_FH = LL::S_U + (NB_TR ? LL::S_TR : 0);  // interface fluxes
+    static constexpr int NBR_INTS = LL::NBR_BYTES / 4;
+    static constexpr size_t bytes_n(int nbuf) {
+        return 2 * (size_t)LL::NBR_BYTES + sizeof(real) * (size_t)LL::EB * ((size_t)nbuf * LOAD + WORK);
+    }
+    static constexpr int NBUF = bytes_n(2) <= 227 * 1024 ? 2 : 1;
+    static constexpr size_t BYTES = bytes_n(NBUF);
+};
+
+template <typename real, class LL>
+using TracePipe = Pipe<LL, false, false, real, 0>;
+template <typename real, class LL>
+using GradPipe = Pipe<LL, true, false, real, LL::S_TR + LL::S_VS>;
+template <typename real, class LL>
+using FluxPipe = Pipe<LL, true, true, real, LL::S_TR + LL::S_VS>;
+
+// neighbour element of every (element, face) of the group starting at e0 (no barrier)
+template <class LL>
+__device__ __forceinline__ void nbr_table(const Mesh& g, int e0, int nloc, int* nbr) {
+    for (int k = threadIdx.x; k < nloc * LL::NF; k += blockDim.x) {
+        const int eb = k / LL::NF, f = k - eb * LL::NF;
+        nbr[k] = neighbour(g, e0 + eb, f >> 1, f & 1);
+    }
+}
+
+// issue (do not wait for) the copies of one group into buf; nbr must be complete
+template <typename real, class LL, class PL, int NV, bool NB_TR, bool FH>
+__device__ __forceinline__ void stage_issue(const real* __restrict__ U, const real* __restrict__ Tu,
+                                            const real* __restrict__ Fh, const Mesh& g, int e0, int nloc,
+                                            real* buf, const int* nbr) {
+    constexpr int NP = LL::NP, NQ = LL::NQ, NF = LL::NF;
+    for (int k = threadIdx.x; k < nloc * NV * NP; k += blockDim.x) {
+        const int eb = k / (NV * NP);
+        const int r = k - eb * NV * NP;
+        const int v = r / NP, pt = r - v * NP;
+        cp_async(&buf[eb * PL::LOAD + r], &U[(size_t)v * g.nelem * NP + (size_t)(e0 + eb) * NP + pt]);
+    }
+    if (NB_TR) {
+        for (int k = threadIdx.x; k < nloc * NF * NV * NQ; k += blockDim.x) {
+            const int eb = k / (NF * NV * NQ);
+            const int r = k - eb * NF * NV * NQ;
+            const int f = r / (NV * NQ), rem = r - f * NV * NQ;
+            const int en = nbr[eb * NF + f];
+            cp_async(&buf[eb * PL::LOAD + PL::OFF_TR + r], &Tu[((size_t)en * NF + (f ^ 1)) * NV * NQ + rem]);
+        }
+    }
+    if (FH) {
+        for (int k = threadIdx.x; k < nloc * NF * NV * NQ; k += blockDim.x) {
+            const int eb = k / (NF * NV * NQ);
+            const int r = k - eb * NF * NV * NQ;
+            const int f = r / (NV * NQ), rem = r - f * NV * NQ;
+            // face 2d+1 is this element's +d face; face 2d is the +d face of its -d neighbour
+            const int ef = (f & 1) ? e0 + eb : nbr[eb * NF + f];
+            cp_async(&buf[eb * PL::LOAD + PL::OFF_FH + r], &Fh[((size_t)(f >> 1) * g.nelem + ef) * NV * NQ + rem]);
+        }
+    }
+}
+
+// neighbour table and copies of group grp into buf, as one committed copy group
+template <typename real, class LL, class PL, int NV, bool NB_TR, bool FH>
+__device__ __forceinline__ void stage_group(const real* __restrict__ U, const real* __restrict__ Tu,
+                                            const real* __restrict__ Fh, const Mesh& g, int grp, real* buf,
+                                            int* nbr) {
+    const int e0 = grp * LL::EB, nloc = min(LL::EB, g.nelem - e0);
+    if (NB_TR || FH) {
+        nbr_table<LL>(g, e0, nloc, nbr);
+        __syncthreads();
+    }
+    stage_issue<real, LL, PL, NV, NB_TR, FH>(U, Tu, Fh, g, e0, nloc, buf, nbr);
+    cp_async_commit();
+}
+
+// before the first group of the block: with two copies, start loading it
+template <typename real, class LL, class PL, int NV, bool NB_TR, bool FH>
+__device__ __forceinline__ void pipe_start(const real* __restrict__ U, const real* __restrict__ Tu,
+                                           const real* __restrict__ Fh, const Mesh& g, int grp, real* buf,
+                                           int* nbr) {
+    if constexpr (PL::NBUF == 2) stage_group<real, LL, PL, NV, NB_TR, FH>(U, Tu, Fh, g, grp, buf, nbr);
+}
+
+// at the top of each group: with two copies, start loading the next group (if any) into
+// the other copy; with one, load this group. Then wait for this group's copies, make them
+// visible to the block and remove the reference offsets.
+template <typename real, class LL, class PL, int NV, bool NB_TR, bool FH>
+__device__ __forceinline__ void pipe_next(const real* __restrict__ U, const real* __restrict__ Tu,
+                                          const real* __restrict__ Fh, const Mesh& g, int grp, int ngroups,
+                                          real* buf, int* nbr, real* nbuf, int* nnbr, real off0, real off4) {
+    if constexpr (PL::NBUF == 2) {
+        const int gn = grp + gridDim.x;
+        if (gn < ngroups) stage_group<real, LL, PL, NV, NB_TR, FH>(U, Tu, Fh, g, gn, nbuf, nnbr);
+        else cp_async_commit();
+        cp_async_wait_group<1>();
+    } else {
+        stage_group<real, LL, PL, NV, NB_TR, FH>(U, Tu, Fh, g, grp, buf, nbr);
+        cp_async_wait_group<0>();
+    }
+    __syncthreads();
+    if (NV == 5 && (off0 != real(0) || off4 != real(0))) {
+        constexpr int NP = LL::NP;
+        const int nloc = min(LL::EB, g.nelem - grp * LL::EB);
+        for (int k = threadIdx.x; k < nloc * NP; k += blockDim.x) {
+            const int eb = k / NP, pt = k - eb * NP;
+            buf[eb * PL::LOAD + pt] -= off0;
+            buf[eb * PL::LOAD + 4 * NP + pt] -= off4;
+        }
+        __syncthreads();
     }
 }
 
@@ -267,22 +395,32 @@ template <typename real, int N, int DIM, int NV>
 __global__ void __launch_bounds__(LineLayout<N, DIM, NV>::THREADS)
 k_line_trace(const real* __restrict__ U, real* __restrict__ Tu, LineGeo<real> geo, Mesh g) {
     using LL = LineLayout<N, DIM, NV>;
+    using PL = TracePipe<real, LL>;
     constexpr int NP = LL::NP, NQ = LL::NQ, NF = LL::NF;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    real* sm = reinterpret_cast<real*>(smem_raw);
-    const int e0 = blockIdx.x * LL::EB;
-    stage_load<real, LL, NV, false, false>(U, nullptr, nullptr, g, e0, sm, LL::PER_TRACE, geo.off0, geo.off4,
-                                           nullptr);
-    __syncthreads();
+    real* buf0 = reinterpret_cast<real*>(smem_raw + 2 * LL::NBR_BYTES);
+    real* buf1 = buf0 + (PL::NBUF - 1) * LL::EB * PL::LOAD;
+    const int ngroups = (g.nelem + LL::EB - 1) / LL::EB;
+    int grp = blockIdx.x;
+    if (grp >= ngroups) return;
     const LineId id = line_id<LL>(threadIdx.x);
-    const int e = e0 + id.eb;
-    if (!id.ok || e >= g.nelem) return;
-    const real* su = sm + id.eb * LL::PER_TRACE;
-    real* out = Tu + (size_t)e * NF * NV * NQ + id.q;
-    if (id.d == 0) line_traces<real, N, NP, NQ, NV, 0>(su, id.q, out, out + NV * NQ, NQ);
-    if constexpr (DIM == 3) {
-        if (id.d == 1) line_traces<real, N, NP, NQ, NV, 1>(su, id.q, out + 2 * NV * NQ, out + 3 * NV * NQ, NQ);
-        if (id.d == 2) line_traces<real, N, NP, NQ, NV, 2>(su, id.q, out + 4 * NV * NQ, out + 5 * NV * NQ, NQ);
+    pipe_start<real, LL, PL, NV, false, false>(U, nullptr, nullptr, g, grp, buf0, nullptr);
+    for (int b = 0; grp < ngroups; grp += gridDim.x, b ^= 1) {
+        real* buf = b ? buf1 : buf0;
+        const int e0 = grp * LL::EB;
+        pipe_next<real, LL, PL, NV, false, false>(U, nullptr, nullptr, g, grp, ngroups, buf, nullptr,
+                                                  b ? buf0 : buf1, nullptr, geo.off0, geo.off4);
+        const int e = e0 + id.eb;
+        if (id.ok && e < g.nelem) {
+            const real* su = buf + id.eb * PL::LOAD;
+            real* out = Tu + (size_t)e * NF * NV * NQ + id.q;
+            if (id.d == 0) line_traces<real, N, NP, NQ, NV, 0>(su, id.q, out, out + NV * NQ, NQ);
+            if constexpr (DIM == 3) {
+                if (id.d == 1) line_traces<real, N, NP, NQ, NV, 1>(su, id.q, out + 2 * NV * NQ, out + 3 * NV * NQ, NQ);
+                if (id.d == 2) line_traces<real, N, NP, NQ, NV, 2>(su, id.q, out + 4 * NV * NQ, out + 5 * NV * NQ, NQ);
+            }
+        }
+        __syncthreads();
     }
 }
 
@@ -333,27 +471,40 @@ __global__ void __launch_bounds__(LineLayout<N, DIM, NV>::THREADS)
 k_line_grad(const real* __restrict__ U, const real* __restrict__ Tu, real* __restrict__ Tg,
             LineGeo<real> geo, Mesh g, int compact) {
     using LL = LineLayout<N, DIM, NV>;
+    using PL = GradPipe<real, LL>;
     constexpr int NQ = LL::NQ, NF = LL::NF, NG = LL::NG;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    int* nbr = reinterpret_cast<int*>(smem_raw);
-    real* sm = reinterpret_cast<real*>(smem_raw + LL::NBR_BYTES);
-    const int e0 = blockIdx.x * LL::EB;
-    stage_load<real, LL, NV, true, false>(U, Tu, nullptr, g, e0, sm, LL::PER_GRAD, geo.off0, geo.off4, nbr);
-    __syncthreads();
+    int* nbr0 = reinterpret_cast<int*>(smem_raw);
+    int* nbr1 = nbr0 + PL::NBR_INTS;
+    real* buf0 = reinterpret_cast<real*>(smem_raw + 2 * LL::NBR_BYTES);
+    real* buf1 = buf0 + (PL::NBUF - 1) * LL::EB * PL::LOAD;
+    real* work = buf0 + PL::NBUF * LL::EB * PL::LOAD;
+    const int ngroups = (g.nelem + LL::EB - 1) / LL::EB;
+    int grp = blockIdx.x;
+    if (grp >= ngroups) return;
     const LineId id = line_id<LL>(threadIdx.x);
-    const int e = e0 + id.eb;
-    const bool live = id.ok && e < g.nelem;
-    real* su = sm + id.eb * LL::PER_GRAD;
-    real* tro = su + LL::S_U;
-    real* trn = tro + LL::S_TR;
-    real* vS = trn + LL::S_TR;
-    prologue<real, N, DIM, NV>(geo, id, live, su, tro, trn, vS);
-    if (!live) return;
-    real* out = Tg + (size_t)e * NF * NG * NQ;
-    if (id.d == 0) grad_faces<real, N, DIM, NV, 0>(geo, compact, vS, tro, trn, out, id.q);
-    if constexpr (DIM == 3) {
-        if (id.d == 1) grad_faces<real, N, DIM, NV, 1>(geo, compact, vS, tro, trn, out, id.q);
-        if (id.d == 2) grad_faces<real, N, DIM, NV, 2>(geo, compact, vS, tro, trn, out, id.q);
+    real* tro = work + id.eb * (LL::S_TR + LL::S_VS);
+    real* vS = tro + LL::S_TR;
+    pipe_start<real, LL, PL, NV, true, false>(U, Tu, nullptr, g, grp, buf0, nbr0);
+    for (int b = 0; grp < ngroups; grp += gridDim.x, b ^= 1) {
+        real* buf = b ? buf1 : buf0;
+        const int e0 = grp * LL::EB;
+        pipe_next<real, LL, PL, NV, true, false>(U, Tu, nullptr, g, grp, ngroups, buf, b ? nbr1 : nbr0,
+                                                 b ? buf0 : buf1, b ? nbr0 : nbr1, geo.off0, geo.off4);
+        const int e = e0 + id.eb;
+        const bool live = id.ok && e < g.nelem;
+        real* su = buf + id.eb * PL::LOAD;
+        real* trn = su + PL::OFF_TR;
+        prologue<real, N, DIM, NV>(geo, id, live, su, tro, trn, vS);
+        if (live) {
+            real* out = Tg + (size_t)e * NF * NG * NQ;
+            if (id.d == 0) grad_faces<real, N, DIM, NV, 0>(geo, compact, vS, tro, trn, out, id.q);
+            if constexpr (DIM == 3) {
+                if (id.d == 1) grad_faces<real, N, DIM, NV, 1>(geo, compact, vS, tro, trn, out, id.q);
+                if (id.d == 2) grad_faces<real, N, DIM, NV, 2>(geo, compact, vS, tro, trn, out, id.q);
+            }
+        }
+        __syncthreads();
     }
 }
 
@@ -517,58 +668,69 @@ __global__ void __maxnreg__((LineLayout<N, DIM, NV>::FLUX_REGS))
 k_line_flux(const real* __restrict__ U, const real* __restrict__ Tu, const real* __restrict__ Fh,
             real* __restrict__ R, LineGeo<real> geo, Mesh g, Phys<real> P, const float* __restrict__ tau) {
     using LL = LineLayout<N, DIM, NV>;
+    using PL = FluxPipe<real, LL>;
     constexpr int NP = LL::NP;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    int* nbr = reinterpret_cast<int*>(smem_raw);
-    real* sm = reinterpret_cast<real*>(smem_raw + LL::NBR_BYTES);
-    const int e0 = blockIdx.x * LL::EB;
-    stage_load<real, LL, NV, true, true>(U, Tu, Fh, g, e0, sm, LL::PER_FLUX, geo.off0, geo.off4, nbr);
-    __syncthreads();
+    int* nbr0 = reinterpret_cast<int*>(smem_raw);
+    int* nbr1 = nbr0 + PL::NBR_INTS;
+    real* buf0 = reinterpret_cast<real*>(smem_raw + 2 * LL::NBR_BYTES);
+    real* buf1 = buf0 + (PL::NBUF - 1) * LL::EB * PL::LOAD;
+    real* work = buf0 + PL::NBUF * LL::EB * PL::LOAD;
+    const int ngroups = (g.nelem + LL::EB - 1) / LL::EB;
+    int grp = blockIdx.x;
+    if (grp >= ngroups) return;
     const LineId id = line_id<LL>(threadIdx.x);
-    const int e = e0 + id.eb;
-    const bool live = id.ok && e < g.nelem;
-    real* su = sm + id.eb * LL::PER_FLUX;
-    real* tro = su + LL::S_U;
-    real* trn = tro + LL::S_TR;
-    real* vS = trn + LL::S_TR;
-    real* fh = vS + LL::S_VS;
-    prologue<real, N, DIM, NV>(geo, id, live, su, tro, trn, vS);
+    real* tro = work + id.eb * (LL::S_TR + LL::S_VS);
+    real* vS = tro + LL::S_TR;
+    pipe_start<real, LL, PL, NV, true, true>(U, Tu, Fh, g, grp, buf0, nbr0);
+    for (int b = 0; grp < ngroups; grp += gridDim.x, b ^= 1) {
+        real* buf = b ? buf1 : buf0;
+        const int e0 = grp * LL::EB, nloc = min(LL::EB, g.nelem - e0);
+        pipe_next<real, LL, PL, NV, true, true>(U, Tu, Fh, g, grp, ngroups, buf, b ? nbr1 : nbr0,
+                                                b ? buf0 : buf1, b ? nbr0 : nbr1, geo.off0, geo.off4);
+        const int e = e0 + id.eb;
+        const bool live = id.ok && e < g.nelem;
+        real* su = buf + id.eb * PL::LOAD;
+        real* trn = su + PL::OFF_TR;
+        real* fh = su + PL::OFF_FH;
+        prologue<real, N, DIM, NV>(geo, id, live, su, tro, trn, vS);
 
-    real r[NV][N];
-    if (live) {
-        const float* t0 = (NV == 5 && tau) ? tau + (size_t)e * 15 : nullptr;
-        if (id.d == 0) line_flux<real, N, DIM, NV, 0>(geo, P, su, vS, fh, id.q, r, t0);
-        if constexpr (DIM == 3) {
-            if (id.d == 1) line_flux<real, N, DIM, NV, 1>(geo, P, su, vS, fh, id.q, r, t0);
-            if (id.d == 2) line_flux<real, N, DIM, NV, 2>(geo, P, su, vS, fh, id.q, r, t0);
+        real r[NV][N];
+        if (live) {
+            const float* t0 = (NV == 5 && tau) ? tau + (size_t)e * 15 : nullptr;
+            if (id.d == 0) line_flux<real, N, DIM, NV, 0>(geo, P, su, vS, fh, id.q, r, t0);
+            if constexpr (DIM == 3) {
+                if (id.d == 1) line_flux<real, N, DIM, NV, 1>(geo, P, su, vS, fh, id.q, r, t0);
+                if (id.d == 2) line_flux<real, N, DIM, NV, 2>(geo, P, su, vS, fh, id.q, r, t0);
+            }
         }
-    }
-    // every line has read u and v^S: the u slot now accumulates R, direction by direction
-    // in the fixed order x, y, z (deterministic sums)
-    __syncthreads();
+        // every line has read u and v^S: the u slot now accumulates R, direction by
+        // direction in the fixed order x, y, z (deterministic sums)
+        __syncthreads();
 #pragma unroll 1
-    for (int dd = 0; dd < DIM; ++dd) {
-        if (live && id.d == dd) {
+        for (int dd = 0; dd < DIM; ++dd) {
+            if (live && id.d == dd) {
 #pragma unroll
-            for (int v = 0; v < NV; ++v)
+                for (int v = 0; v < NV; ++v)
 #pragma unroll
-                for (int i = 0; i < N; ++i) {
-                    int pt;
-                    if (dd == 0) pt = lpt<N, 0>(i, id.q);
-                    else if (dd == 1) pt = lpt<N, (DIM == 3 ? 1 : 0)>(i, id.q);
-                    else pt = lpt<N, (DIM == 3 ? 2 : 0)>(i, id.q);
-                    real* dst = su + v * NP + pt;
-                    *dst = (dd == 0) ? r[v][i] : *dst + r[v][i];
-                }
+                    for (int i = 0; i < N; ++i) {
+                        int pt;
+                        if (dd == 0) pt = lpt<N, 0>(i, id.q);
+                        else if (dd == 1) pt = lpt<N, (DIM == 3 ? 1 : 0)>(i, id.q);
+                        else pt = lpt<N, (DIM == 3 ? 2 : 0)>(i, id.q);
+                        real* dst = su + v * NP + pt;
+                        *dst = (dd == 0) ? r[v][i] : *dst + r[v][i];
+                    }
+            }
+            __syncthreads();
+        }
+        for (int k = threadIdx.x; k < nloc * NV * NP; k += blockDim.x) {
+            const int eb = k / (NV * NP);
+            const int rr = k - eb * NV * NP;
+            const int v = rr / NP, pt = rr - v * NP;
+            R[(size_t)v * g.nelem * NP + (size_t)(e0 + eb) * NP + pt] = buf[eb * PL::LOAD + rr];
         }
         __syncthreads();
-    }
-    const int nloc = min(LL::EB, g.nelem - e0);
-    for (int k = threadIdx.x; k < nloc * NV * NP; k += blockDim.x) {
-        const int eb = k / (NV * NP);
-        const int rr = k - eb * NV * NP;
-        const int v = rr / NP, pt = rr - v * NP;
-        R[(size_t)v * g.nelem * NP + (size_t)(e0 + eb) * NP + pt] = sm[eb * LL::PER_FLUX + rr];
     }
 }
 
