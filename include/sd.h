@@ -232,10 +232,11 @@ sd_status sd_closure_enable(sd_ctx* ctx, const void* Wb, const float* P, const f
  * The paper has no counterpart; it is the same FP32 residual as sd_residual, without a
  * context: mesh, p, scheme and physics as for sd_init; U, R device FP32 arrays as for
  * sd_residual (they must not overlap); work enqueued on `stream`.
- * Scratch: a static device array of 32 MiB (8 Mi FP32 values) inside the library, held by
- * every GPU that loads the library until the process exits. A grid needs
- * nelem * 2 dim (nvar + ngrad) n^(dim-1) values (ngrad = 9 for Navier-Stokes, 1 otherwise;
- * 3375 elements at p = 4 for Navier-Stokes); larger grids return SD_EINVAL with a message
+ * Scratch: a static device array of 36 MiB (9 Mi FP32 values) inside the library, held by
+ * every GPU that loads the library until the process exits. A grid needs about
+ * nelem * (2 dim (F + G) + dim F) values, with F = nvar n^(dim-1) and G = ngrad n^(dim-1)
+ * each rounded up to a multiple of 4 (ngrad = 9 for Navier-Stokes, 1 otherwise; 3375
+ * elements at p = 4 for Navier-Stokes fit); larger grids return SD_EINVAL with a message
  * and nothing is launched. The first call on a device looks up the array's device address
  * and uploads the operator tables for that device; make that first call before any stream
  * capture. Every call shares the array: calls whose kernels overlap on the GPU race (give

@@ -310,9 +310,11 @@ extern "C" sd_status sd_init(const sd_mesh* mesh, int p, sd_scheme scheme, const
     const int np = ipow_h(c->n, c->dim), nq = ipow_h(c->n, c->dim - 1);
     c->npts = (size_t)c->nelem * np;
     c->nstate = c->npts * c->nvar;
-    c->ntu = (size_t)c->nelem * 2 * c->dim * c->nvar * nq;
-    c->ntg = (size_t)c->nelem * 2 * c->dim * c->ngrad * nq;
-    c->nfh = (size_t)c->nelem * c->dim * c->nvar * nq;
+    // face blocks padded to a multiple of 4 values (16-byte aligned, copied in 16-byte pieces)
+    const size_t fst = ((size_t)c->nvar * nq + 3) / 4 * 4, gst = ((size_t)c->ngrad * nq + 3) / 4 * 4;
+    c->ntu = (size_t)c->nelem * 2 * c->dim * fst;
+    c->ntg = (size_t)c->nelem * 2 * c->dim * gst;
+    c->nfh = (size_t)c->nelem * c->dim * fst;
     c->esize = prec == SD_F32 ? sizeof(float) : sizeof(double);
 
     // shared memory feasibility of the element-staged kernels (line layout of sd_line.cuh:

@@ -46,7 +46,7 @@ k_line_fluxmean(const real* __restrict__ U, const real* __restrict__ Tu, LineGeo
     int* nbr = reinterpret_cast<int*>(smem_raw);
     real* sm = reinterpret_cast<real*>(smem_raw + LL::NBR_BYTES);
     const int e0 = blockIdx.x * LL::EB;
-    stage_load<real, LL, 5, true, false>(U, Tu, nullptr, g, e0, sm, LL::PER_GRAD, geo.off0, geo.off4, nbr);
+    stage_load<real, LL, 5>(U, Tu, g, e0, sm, LL::PER_GRAD, geo.off0, geo.off4, nbr);
     __syncthreads();
     const LineId id = line_id<LL>(threadIdx.x);
     const bool live = id.ok && e0 + id.eb < g.nelem;
@@ -55,7 +55,7 @@ k_line_fluxmean(const real* __restrict__ U, const real* __restrict__ Tu, LineGeo
         real* tro = su + LL::S_U;
         real* trn = tro + LL::S_TR;
         real* vS = trn + LL::S_TR;
-        prologue<real, N, 3, 5>(geo, id, live, su, tro, trn, vS);
+        prologue<real, N, 3, 5, ElemStrides<LL>>(geo, id, live, su, tro, trn, vS);
     }
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (warp >= LL::EB || e0 + warp >= g.nelem) return;
@@ -103,7 +103,7 @@ k_line_features(const real* __restrict__ U, const real* __restrict__ Tu, LineGeo
     int* nbr = reinterpret_cast<int*>(smem_raw);
     real* sm = reinterpret_cast<real*>(smem_raw + LL::NBR_BYTES);
     const int e0 = blockIdx.x * LL::EB;
-    stage_load<real, LL, 5, true, false>(U, Tu, nullptr, g, e0, sm, LL::PER_GRAD, geo.off0, geo.off4, nbr);
+    stage_load<real, LL, 5>(U, Tu, g, e0, sm, LL::PER_GRAD, geo.off0, geo.off4, nbr);
     __syncthreads();
     const LineId id = line_id<LL>(threadIdx.x);
     const bool live = id.ok && e0 + id.eb < g.nelem;
@@ -112,7 +112,7 @@ k_line_features(const real* __restrict__ U, const real* __restrict__ Tu, LineGeo
         real* tro = su + LL::S_U;
         real* trn = tro + LL::S_TR;
         real* vS = trn + LL::S_TR;
-        prologue<real, N, 3, 5>(geo, id, live, su, tro, trn, vS);
+        prologue<real, N, 3, 5, ElemStrides<LL>>(geo, id, live, su, tro, trn, vS);
     }
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (warp >= LL::EB || e0 + warp >= g.nelem) return;

@@ -35,9 +35,9 @@ struct sd_ctx {
     size_t ntu, ntg, nfh;    // trace and interface-flux buffer sizes (values)
     size_t esize;            // bytes per value of the residual precision
     // scratch owned by the context
-    void* Tu;                // face traces of u        [nelem][2dim][nvar][n^(dim-1)]
-    void* Tg;                // face gradient values    [nelem][2dim][ngrad][n^(dim-1)]
-    void* Fh;                // interface fluxes        [dim][nelem][nvar][n^(dim-1)] (+d face of each element)
+    void* Tu;                // face traces of u        [nelem][2dim][F] ([nvar][n^(dim-1)] padded to F, a multiple of 4)
+    void* Tg;                // face gradient values    [nelem][2dim][G] ([ngrad][n^(dim-1)] padded to G)
+    void* Fh;                // interface fluxes        [dim][nelem][F] (+d face of each element)
     double* Tu64;            // FP64 traces for diagnostics (== Tu when prec is F64)
     void* S;                 // stage input of the residual precision
     void* K;                 // stage residual of the residual precision
@@ -96,5 +96,5 @@ sd_status sdi_check_smem(sd_ctx* c);
 void sdi_set_error(const char* fmt, ...);
 void sdi_build_operators(sd_ctx* c);
 
-// size of the static scratch of sd_residual_f32_noalloc (FP32 values, 32 MiB)
-#define SD_NOALLOC_SCRATCH_FLOATS (8 * 1024 * 1024)
+// size of the static scratch of sd_residual_f32_noalloc (FP32 values, 36 MiB)
+#define SD_NOALLOC_SCRATCH_FLOATS (9 * 1024 * 1024)

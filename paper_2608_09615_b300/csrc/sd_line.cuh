@@ -65,6 +65,8 @@ struct LineGeo {
     real tip[3];             // interior penalty eta (p+1)^2 / h_d (0: off)
 };
 
+constexpr int round4(int x) { return (x + 3) / 4 * 4; }
+
 template <int N, int DIM, int NV>
 struct LineLayout {
     static constexpr int NP = ipow(N, DIM);
@@ -77,17 +79,30 @@ struct LineLayout {
     static constexpr int UPB = UNIT >= SD_LINE_THREADS ? 1 : SD_LINE_THREADS / UNIT;  // groups per block
     static constexpr int THREADS = UPB * UNIT;
     static constexpr int EB = UPB * EPW;                          // elements per block
+    // Global scratch layouts: Tu[e][f][FST] and Fh[d][e][FST] hold [v][q] in the first NV*NQ
+    // values of each block, Tg[e][f][GST] holds [c][q]; blocks are padded to a multiple of
+    // 4 values so that each starts on a 16-byte boundary and is copied in 16-byte pieces.
+    static constexpr int FST = round4(NV * NQ);
+    static constexpr int GST = round4(NG * NQ);
+    // per-element sizes of the contiguous element staging of the closure kernels
     static constexpr int S_U = NV * NP;
     static constexpr int S_TR = NF * NV * NQ;
     static constexpr int S_VS = NV * DIM * NP;
-    static constexpr int S_TG = NF * NG * NQ;
-    static constexpr int S_FH = NF * NV * NQ;                      // interface fluxes of the 2*DIM faces
-    static constexpr int PER_TRACE = S_U;
     static constexpr int PER_GRAD = S_U + 2 * S_TR + S_VS;
-    static constexpr int PER_FLUX = S_U + 2 * S_TR + S_VS + S_FH;
     static constexpr int NBR_BYTES = ((EB * NF * 4 + 15) / 16) * 16;   // neighbour table
     static constexpr int REG_FIT = (65536 / THREADS) / 8 * 8;
     static constexpr int FLUX_REGS = SD_FLUX_MAXNREG < REG_FIT ? SD_FLUX_MAXNREG : (REG_FIT < 255 ? REG_FIT : 255);
+};
+
+// Strides of the staged arrays as the line functions see them: US between the variables
+// of u, FS between the faces of the trace (and interface flux) arrays; within a face the
+// layout is [v][q]. The residual kernels stage u variable-major over the block's elements
+// (US = EB NP) and traces in the padded global face blocks (FS = FST); the closure
+// kernels stage each element contiguously (US = NP, FS = NV NQ).
+template <int US_, int FS_>
+struct Strides {
+    static constexpr int US = US_;
+    static constexpr int FS = FS_;
 };
 
 struct LineId {
@@ -135,8 +150,7 @@ __device__ __forceinline__ real dotc(const real* row, const real* x) {
 }
 
 // ---------------------------------------------------------------- staging helpers
-// asynchronous global -> shared copy of one value (Ampere-style cp.async; the copies of a
-// block are all in flight together and complete at cp_async_wait_all)
+// asynchronous global -> shared copy of one value (Ampere-style cp.async)
 template <typename real>
 __device__ __forceinline__ void cp_async(real* smem, const real* gmem) {
     const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
@@ -144,6 +158,12 @@ __device__ __forceinline__ void cp_async(real* smem, const real* gmem) {
         asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
     else
         asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+
+// asynchronous copy of 16 bytes; both addresses must be 16-byte aligned
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
 }
 
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
@@ -155,49 +175,32 @@ __device__ __forceinline__ void cp_async_wait_group() {
     asm volatile("cp.async.wait_group %0;\n" ::"n"(NPEND) : "memory");
 }
 
-// Load of the block's elements (u, offsets removed unless the input already carries them)
-// and, optionally, the neighbour traces and the interface fluxes of the element's faces.
-// Ends with a barrier; everything is in shared memory afterwards.
-// Fh layout: [d][e][v][q], the flux through the face between e and its +d neighbour.
-template <typename real, class LL, int NV, bool NB_TR, bool FH>
+// Contiguous element staging used by the closure kernels: u (offsets removed unless the
+// input already carries them) and the neighbour traces of EB elements, each element's data
+// at sm + eb * per in the layout Strides<NP, NV NQ>. Ends with a barrier.
+template <typename real, class LL, int NV>
 __device__ __forceinline__ void stage_load(const real* __restrict__ U, const real* __restrict__ Tu,
-                                           const real* __restrict__ Fh, const Mesh& g, int e0,
-                                           real* sm, int per, real off0, real off4, int* nbr) {
+                                           const Mesh& g, int e0, real* sm, int per, real off0, real off4,
+                                           int* nbr) {
     constexpr int NP = LL::NP, NQ = LL::NQ, NF = LL::NF;
     const int nloc = min(LL::EB, g.nelem - e0);
-    if (NB_TR || FH) {
-        // neighbour element of every (element, face), computed once
-        for (int k = threadIdx.x; k < nloc * NF; k += blockDim.x) {
-            const int eb = k / NF, f = k - eb * NF;
-            nbr[k] = neighbour(g, e0 + eb, f >> 1, f & 1);
-        }
-        __syncthreads();
+    for (int k = threadIdx.x; k < nloc * NF; k += blockDim.x) {
+        const int eb = k / NF, f = k - eb * NF;
+        nbr[k] = neighbour(g, e0 + eb, f >> 1, f & 1);
     }
+    __syncthreads();
     for (int k = threadIdx.x; k < nloc * NV * NP; k += blockDim.x) {
         const int eb = k / (NV * NP);
         const int r = k - eb * NV * NP;
         const int v = r / NP, pt = r - v * NP;
         cp_async(&sm[eb * per + r], &U[(size_t)v * g.nelem * NP + (size_t)(e0 + eb) * NP + pt]);
     }
-    if (NB_TR) {
-        for (int k = threadIdx.x; k < nloc * NF * NV * NQ; k += blockDim.x) {
-            const int eb = k / (NF * NV * NQ);
-            const int r = k - eb * NF * NV * NQ;
-            const int f = r / (NV * NQ), rem = r - f * NV * NQ;
-            const int en = nbr[eb * NF + f];
-            cp_async(&sm[eb * per + LL::S_U + LL::S_TR + r], &Tu[((size_t)en * NF + (f ^ 1)) * NV * NQ + rem]);
-        }
-    }
-    if (FH) {
-        for (int k = threadIdx.x; k < nloc * NF * NV * NQ; k += blockDim.x) {
-            const int eb = k / (NF * NV * NQ);
-            const int r = k - eb * NF * NV * NQ;
-            const int f = r / (NV * NQ), rem = r - f * NV * NQ;
-            // face 2d+1 is this element's +d face; face 2d is the +d face of its -d neighbour
-            const int ef = (f & 1) ? e0 + eb : nbr[eb * NF + f];
-            cp_async(&sm[eb * per + LL::S_U + 2 * LL::S_TR + LL::S_VS + r],
-                     &Fh[((size_t)(f >> 1) * g.nelem + ef) * NV * NQ + rem]);
-        }
+    for (int k = threadIdx.x; k < nloc * NF * NV * NQ; k += blockDim.x) {
+        const int eb = k / (NF * NV * NQ);
+        const int r = k - eb * NF * NV * NQ;
+        const int f = r / (NV * NQ), rem = r - f * NV * NQ;
+        const int en = nbr[eb * NF + f];
+        cp_async(&sm[eb * per + LL::S_U + LL::S_TR + r], &Tu[((size_t)en * NF + (f ^ 1)) * LL::FST + rem]);
     }
     cp_async_wait_all();
     __syncthreads();
@@ -213,19 +216,24 @@ __device__ __forceinline__ void stage_load(const real* __restrict__ U, const rea
 // ---------------------------------------------------------------- pipelined staging
 // The residual kernels are persistent: block b walks over the element groups b, b + grid,
 // b + 2 grid, ... and keeps two shared-memory copies of the loaded data, so the copies of
-// the next group are in flight while the current group is computed. Per element, the
-// double-buffered part holds u, then (NB_TR) the neighbour traces, then (FH) the interface
-// fluxes; the values the kernel computes itself (own traces, v^S: WORK values per element)
-// live in a single work area. Where two copies do not fit in shared memory (the largest n
-// in FP64) one copy is used and the loads of a group are not overlapped.
+// the next group are in flight while the current group is computed. A copy holds
+//   u       [NV][EB][NP] (variable-major over the block's elements), padded to 4 values,
+//   (NB_TR) the neighbour traces [EB][NF][FST],
+//   (FH)    the interface fluxes of the element's faces [EB][NF][FST];
+// the trace and flux blocks are copied as whole padded global blocks, in 16-byte pieces.
+// The values the kernel computes itself (own traces [EB][NF][FST], v^S: WORK values per
+// element) live in one work area. Where two copies do not fit in shared memory (the
+// largest n in FP64) one copy is used and the loads of a group are not overlapped.
 template <class LL, bool NB_TR, bool FH, typename real, int WORK>
 struct Pipe {
-    static constexpr int LOAD = LL::S_U + (NB_TR ? LL::S_TR : 0) + (FH ? LL::S_FH : 0);
-    static constexpr int OFF_TR = LL::S_U;                           // neighbour traces
-    static constexpr int OFF_FH = LL::S_U + (NB_TR ? LL::S_TR : 0);  // interface fluxes
+    static constexpr int UPAD = round4(LL::S_U * LL::EB);
+    static constexpr int TRB = LL::EB * LL::NF * LL::FST;            // one [EB][NF][FST] block
+    static constexpr int OFF_TR = UPAD;                              // neighbour traces
+    static constexpr int OFF_FH = UPAD + (NB_TR ? TRB : 0);          // interface fluxes
+    static constexpr int LOAD = UPAD + (NB_TR ? TRB : 0) + (FH ? TRB : 0);   // per copy
     static constexpr int NBR_INTS = LL::NBR_BYTES / 4;
     static constexpr size_t bytes_n(int nbuf) {
-        return 2 * (size_t)LL::NBR_BYTES + sizeof(real) * (size_t)LL::EB * ((size_t)nbuf * LOAD + WORK);
+        return 2 * (size_t)LL::NBR_BYTES + sizeof(real) * ((size_t)nbuf * LOAD + (size_t)LL::EB * WORK);
     }
     static constexpr int NBUF = bytes_n(2) <= 227 * 1024 ? 2 : 1;
     static constexpr size_t BYTES = bytes_n(NBUF);
@@ -234,9 +242,14 @@ struct Pipe {
 template <typename real, class LL>
 using TracePipe = Pipe<LL, false, false, real, 0>;
 template <typename real, class LL>
-using GradPipe = Pipe<LL, true, false, real, LL::S_TR + LL::S_VS>;
+using GradPipe = Pipe<LL, true, false, real, LL::NF * LL::FST + LL::S_VS>;
 template <typename real, class LL>
-using FluxPipe = Pipe<LL, true, true, real, LL::S_TR + LL::S_VS>;
+using FluxPipe = Pipe<LL, true, true, real, LL::NF * LL::FST + LL::S_VS>;
+
+template <class LL>
+using ResStrides = Strides<LL::EB * LL::NP, LL::FST>;
+template <class LL>
+using ElemStrides = Strides<LL::NP, LL::S_TR / LL::NF>;
 
 // neighbour element of every (element, face) of the group starting at e0 (no barrier)
 template <class LL>
@@ -252,30 +265,32 @@ template <typename real, class LL, class PL, int NV, bool NB_TR, bool FH>
 __device__ __forceinline__ void stage_issue(const real* __restrict__ U, const real* __restrict__ Tu,
                                             const real* __restrict__ Fh, const Mesh& g, int e0, int nloc,
                                             real* buf, const int* nbr) {
-    constexpr int NP = LL::NP, NQ = LL::NQ, NF = LL::NF;
-    for (int k = threadIdx.x; k < nloc * NV * NP; k += blockDim.x) {
-        const int eb = k / (NV * NP);
-        const int r = k - eb * NV * NP;
-        const int v = r / NP, pt = r - v * NP;
-        cp_async(&buf[eb * PL::LOAD + r], &U[(size_t)v * g.nelem * NP + (size_t)(e0 + eb) * NP + pt]);
+    constexpr int NP = LL::NP, NF = LL::NF, FST = LL::FST, EB = LL::EB;
+    constexpr int CH = 16 / (int)sizeof(real);          // values per 16-byte piece
+    constexpr int CPB = FST / CH;                       // pieces per face block
+    const int span = nloc * NP;                         // u values of one variable
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+        const real* src = U + (size_t)v * g.nelem * NP + (size_t)e0 * NP;
+        real* dst = buf + v * EB * NP;
+        for (int j = threadIdx.x; j < span; j += blockDim.x) cp_async(dst + j, src + j);
     }
     if (NB_TR) {
-        for (int k = threadIdx.x; k < nloc * NF * NV * NQ; k += blockDim.x) {
-            const int eb = k / (NF * NV * NQ);
-            const int r = k - eb * NF * NV * NQ;
-            const int f = r / (NV * NQ), rem = r - f * NV * NQ;
-            const int en = nbr[eb * NF + f];
-            cp_async(&buf[eb * PL::LOAD + PL::OFF_TR + r], &Tu[((size_t)en * NF + (f ^ 1)) * NV * NQ + rem]);
+        for (int k = threadIdx.x; k < nloc * NF * CPB; k += blockDim.x) {
+            const int c = k / CPB, w = k - c * CPB;     // c = eb * NF + f
+            const int f = c % NF;
+            const real* src = Tu + ((size_t)nbr[c] * NF + (f ^ 1)) * FST + w * CH;
+            cp_async16(buf + PL::OFF_TR + c * FST + w * CH, src);
         }
     }
     if (FH) {
-        for (int k = threadIdx.x; k < nloc * NF * NV * NQ; k += blockDim.x) {
-            const int eb = k / (NF * NV * NQ);
-            const int r = k - eb * NF * NV * NQ;
-            const int f = r / (NV * NQ), rem = r - f * NV * NQ;
+        for (int k = threadIdx.x; k < nloc * NF * CPB; k += blockDim.x) {
+            const int c = k / CPB, w = k - c * CPB;
+            const int eb = c / NF, f = c - eb * NF;
             // face 2d+1 is this element's +d face; face 2d is the +d face of its -d neighbour
-            const int ef = (f & 1) ? e0 + eb : nbr[eb * NF + f];
-            cp_async(&buf[eb * PL::LOAD + PL::OFF_FH + r], &Fh[((size_t)(f >> 1) * g.nelem + ef) * NV * NQ + rem]);
+            const int ef = (f & 1) ? e0 + eb : nbr[c];
+            const real* src = Fh + ((size_t)(f >> 1) * g.nelem + ef) * FST + w * CH;
+            cp_async16(buf + PL::OFF_FH + c * FST + w * CH, src);
         }
     }
 }
@@ -320,27 +335,28 @@ __device__ __forceinline__ void pipe_next(const real* __restrict__ U, const real
     }
     __syncthreads();
     if (NV == 5 && (off0 != real(0) || off4 != real(0))) {
-        constexpr int NP = LL::NP;
-        const int nloc = min(LL::EB, g.nelem - grp * LL::EB);
-        for (int k = threadIdx.x; k < nloc * NP; k += blockDim.x) {
-            const int eb = k / NP, pt = k - eb * NP;
-            buf[eb * PL::LOAD + pt] -= off0;
-            buf[eb * PL::LOAD + 4 * NP + pt] -= off4;
+        const int span = min(LL::EB, g.nelem - grp * LL::EB) * LL::NP;
+        real* u0 = buf;
+        real* u4 = buf + 4 * LL::EB * LL::NP;
+        for (int k = threadIdx.x; k < span; k += blockDim.x) {
+            u0[k] -= off0;
+            u4[k] -= off4;
         }
         __syncthreads();
     }
 }
 
-// own traces at the two faces of direction D for every variable of line q
-template <typename real, int N, int NP, int NQ, int NV, int D>
-__device__ __forceinline__ void line_traces(const real* su, int q, real* outL, real* outR,
-                                            int ostride) {
+// ---------------------------------------------------------------- line functions
+// own traces at the two faces of direction D for every variable of line q; outL/outR
+// point at the face blocks, ostride between variables
+template <typename real, int N, int NQ, int NV, int D, class ST>
+__device__ __forceinline__ void line_traces(const real* su, int q, real* outL, real* outR, int ostride) {
     const OpTab<real, N>& op = c_op<real, N>;
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
         real u[N];
 #pragma unroll
-        for (int i = 0; i < N; ++i) u[i] = su[v * NP + lpt<N, D>(i, q)];
+        for (int i = 0; i < N; ++i) u[i] = su[v * ST::US + lpt<N, D>(i, q)];
         outL[v * ostride] = dotc<real, N>(op.L, u);
         outR[v * ostride] = dotc<real, N>(op.L + N * N, u);
     }
@@ -348,7 +364,7 @@ __device__ __forceinline__ void line_traces(const real* su, int q, real* outL, r
 
 // v^S along D for every variable of line q (Eq. w:e in Cartesian form):
 // v_D = (2/h_D) (D u + M[:,0] delta_L + M[:,N] delta_R)
-template <typename real, int N, int DIM, int NV, int D>
+template <typename real, int N, int DIM, int NV, int D, class ST>
 __device__ __forceinline__ void line_vs(const LineGeo<real>& geo, const real* su, const real* tro,
                                         const real* trn, real* vS, int q) {
     constexpr int NP = ipow(N, DIM), NQ = ipow(N, DIM - 1);
@@ -357,8 +373,8 @@ __device__ __forceinline__ void line_vs(const LineGeo<real>& geo, const real* su
     for (int v = 0; v < NV; ++v) {
         real u[N];
 #pragma unroll
-        for (int i = 0; i < N; ++i) u[i] = su[v * NP + lpt<N, D>(i, q)];
-        const int il = ((2 * D) * NV + v) * NQ + q, ir = ((2 * D + 1) * NV + v) * NQ + q;
+        for (int i = 0; i < N; ++i) u[i] = su[v * ST::US + lpt<N, D>(i, q)];
+        const int il = (2 * D) * ST::FS + v * NQ + q, ir = (2 * D + 1) * ST::FS + v * NQ + q;
         const real dl = real(0.5) * (trn[il] - tro[il]);
         const real dr = real(0.5) * (trn[ir] - tro[ir]);
 #pragma unroll
@@ -374,7 +390,7 @@ __device__ __forceinline__ void line_vs(const LineGeo<real>& geo, const real* su
 // own interface gradient of component c on side s (0: face 2D, 1: face 2D+1) from the
 // loaded line g[] (BR1: Eq. v:e at the interface row; compact: minus (2/h) alpha (beta)
 // times the opposite-face correction on the d-component)
-template <typename real, int N, int NQ, int NV, int D>
+template <typename real, int N, int NQ, int NV, int D, class ST>
 __device__ __forceinline__ real face_value(const LineGeo<real>& geo, int compact, int c, int s,
                                            const real* g, const real* tro, const real* trn, int q) {
     const OpTab<real, N>& op = c_op<real, N>;
@@ -383,11 +399,54 @@ __device__ __forceinline__ real face_value(const LineGeo<real>& geo, int compact
     comp_map<NV>(D, c, v, m);
     if (compact && m == D) {
         const int fo = 2 * D + (1 - s);
-        const int io = (fo * NV + v) * NQ + q;
+        const int io = fo * ST::FS + v * NQ + q;
         const real dop = real(0.5) * (trn[io] - tro[io]);
         a = fma(-(s ? geo.corrR[D] : geo.corrL[D]), dop, a);
     }
     return a;
+}
+
+// shared prologue of the gradient, flux and closure kernels: own traces, then v^S
+template <typename real, int N, int DIM, int NV, class ST>
+__device__ __forceinline__ void prologue(const LineGeo<real>& geo, const LineId& id, bool live,
+                                         real* su, real* tro, real* trn, real* vS) {
+    constexpr int NQ = ipow(N, DIM - 1), FS = ST::FS;
+    if (live) {
+        real* o = tro + id.q;
+        if (id.d == 0) line_traces<real, N, NQ, NV, 0, ST>(su, id.q, o, o + FS, NQ);
+        if constexpr (DIM == 3) {
+            if (id.d == 1) line_traces<real, N, NQ, NV, 1, ST>(su, id.q, o + 2 * FS, o + 3 * FS, NQ);
+            if (id.d == 2) line_traces<real, N, NQ, NV, 2, ST>(su, id.q, o + 4 * FS, o + 5 * FS, NQ);
+        }
+    }
+    __syncthreads();
+    if (live) {
+        if (id.d == 0) line_vs<real, N, DIM, NV, 0, ST>(geo, su, tro, trn, vS, id.q);
+        if constexpr (DIM == 3) {
+            if (id.d == 1) line_vs<real, N, DIM, NV, 1, ST>(geo, su, tro, trn, vS, id.q);
+            if (id.d == 2) line_vs<real, N, DIM, NV, 2, ST>(geo, su, tro, trn, vS, id.q);
+        }
+    }
+    __syncthreads();
+}
+
+// own interface gradients of the two faces of direction D, written to the padded global
+// blocks out[f][GST] ([c][q] within a block)
+template <typename real, int N, int DIM, int NV, int D, class ST>
+__device__ __forceinline__ void grad_faces(const LineGeo<real>& geo, int compact, const real* vS,
+                                           const real* tro, const real* trn, real* out, int q) {
+    using LL = LineLayout<N, DIM, NV>;
+    constexpr int NP = LL::NP, NQ = LL::NQ, NG = LL::NG, GST = LL::GST;
+#pragma unroll
+    for (int c = 0; c < NG; ++c) {
+        int v, m;
+        comp_map<NV>(D, c, v, m);
+        real gl[N];
+#pragma unroll
+        for (int i = 0; i < N; ++i) gl[i] = vS[(v * DIM + m) * NP + lpt<N, D>(i, q)];
+        out[(2 * D) * GST + c * NQ + q] = face_value<real, N, NQ, NV, D, ST>(geo, compact, c, 0, gl, tro, trn, q);
+        out[(2 * D + 1) * GST + c * NQ + q] = face_value<real, N, NQ, NV, D, ST>(geo, compact, c, 1, gl, tro, trn, q);
+    }
 }
 
 // ---------------------------------------------------------------- kernels
@@ -396,10 +455,11 @@ __global__ void __launch_bounds__(LineLayout<N, DIM, NV>::THREADS)
 k_line_trace(const real* __restrict__ U, real* __restrict__ Tu, LineGeo<real> geo, Mesh g) {
     using LL = LineLayout<N, DIM, NV>;
     using PL = TracePipe<real, LL>;
-    constexpr int NP = LL::NP, NQ = LL::NQ, NF = LL::NF;
+    using ST = ResStrides<LL>;
+    constexpr int NP = LL::NP, NQ = LL::NQ, NF = LL::NF, FST = LL::FST;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     real* buf0 = reinterpret_cast<real*>(smem_raw + 2 * LL::NBR_BYTES);
-    real* buf1 = buf0 + (PL::NBUF - 1) * LL::EB * PL::LOAD;
+    real* buf1 = buf0 + (PL::NBUF - 1) * PL::LOAD;
     const int ngroups = (g.nelem + LL::EB - 1) / LL::EB;
     int grp = blockIdx.x;
     if (grp >= ngroups) return;
@@ -412,57 +472,15 @@ k_line_trace(const real* __restrict__ U, real* __restrict__ Tu, LineGeo<real> ge
                                                   b ? buf0 : buf1, nullptr, geo.off0, geo.off4);
         const int e = e0 + id.eb;
         if (id.ok && e < g.nelem) {
-            const real* su = buf + id.eb * PL::LOAD;
-            real* out = Tu + (size_t)e * NF * NV * NQ + id.q;
-            if (id.d == 0) line_traces<real, N, NP, NQ, NV, 0>(su, id.q, out, out + NV * NQ, NQ);
+            const real* su = buf + id.eb * NP;
+            real* out = Tu + (size_t)e * NF * FST + id.q;
+            if (id.d == 0) line_traces<real, N, NQ, NV, 0, ST>(su, id.q, out, out + FST, NQ);
             if constexpr (DIM == 3) {
-                if (id.d == 1) line_traces<real, N, NP, NQ, NV, 1>(su, id.q, out + 2 * NV * NQ, out + 3 * NV * NQ, NQ);
-                if (id.d == 2) line_traces<real, N, NP, NQ, NV, 2>(su, id.q, out + 4 * NV * NQ, out + 5 * NV * NQ, NQ);
+                if (id.d == 1) line_traces<real, N, NQ, NV, 1, ST>(su, id.q, out + 2 * FST, out + 3 * FST, NQ);
+                if (id.d == 2) line_traces<real, N, NQ, NV, 2, ST>(su, id.q, out + 4 * FST, out + 5 * FST, NQ);
             }
         }
         __syncthreads();
-    }
-}
-
-// shared prologue of the gradient and flux kernels: own traces, then v^S
-template <typename real, int N, int DIM, int NV>
-__device__ __forceinline__ void prologue(const LineGeo<real>& geo, const LineId& id, bool live,
-                                         real* su, real* tro, real* trn, real* vS) {
-    using LL = LineLayout<N, DIM, NV>;
-    constexpr int NP = LL::NP, NQ = LL::NQ;
-    if (live) {
-        real* o = tro + id.q;
-        if (id.d == 0) line_traces<real, N, NP, NQ, NV, 0>(su, id.q, o, o + NV * NQ, NQ);
-        if constexpr (DIM == 3) {
-            if (id.d == 1) line_traces<real, N, NP, NQ, NV, 1>(su, id.q, o + 2 * NV * NQ, o + 3 * NV * NQ, NQ);
-            if (id.d == 2) line_traces<real, N, NP, NQ, NV, 2>(su, id.q, o + 4 * NV * NQ, o + 5 * NV * NQ, NQ);
-        }
-    }
-    __syncthreads();
-    if (live) {
-        if (id.d == 0) line_vs<real, N, DIM, NV, 0>(geo, su, tro, trn, vS, id.q);
-        if constexpr (DIM == 3) {
-            if (id.d == 1) line_vs<real, N, DIM, NV, 1>(geo, su, tro, trn, vS, id.q);
-            if (id.d == 2) line_vs<real, N, DIM, NV, 2>(geo, su, tro, trn, vS, id.q);
-        }
-    }
-    __syncthreads();
-}
-
-template <typename real, int N, int DIM, int NV, int D>
-__device__ __forceinline__ void grad_faces(const LineGeo<real>& geo, int compact, const real* vS,
-                                           const real* tro, const real* trn, real* out, int q) {
-    using LL = LineLayout<N, DIM, NV>;
-    constexpr int NP = LL::NP, NQ = LL::NQ, NG = LL::NG;
-#pragma unroll
-    for (int c = 0; c < NG; ++c) {
-        int v, m;
-        comp_map<NV>(D, c, v, m);
-        real gl[N];
-#pragma unroll
-        for (int i = 0; i < N; ++i) gl[i] = vS[(v * DIM + m) * NP + lpt<N, D>(i, q)];
-        out[((2 * D) * NG + c) * NQ + q] = face_value<real, N, NQ, NV, D>(geo, compact, c, 0, gl, tro, trn, q);
-        out[((2 * D + 1) * NG + c) * NQ + q] = face_value<real, N, NQ, NV, D>(geo, compact, c, 1, gl, tro, trn, q);
     }
 }
 
@@ -472,19 +490,20 @@ k_line_grad(const real* __restrict__ U, const real* __restrict__ Tu, real* __res
             LineGeo<real> geo, Mesh g, int compact) {
     using LL = LineLayout<N, DIM, NV>;
     using PL = GradPipe<real, LL>;
-    constexpr int NQ = LL::NQ, NF = LL::NF, NG = LL::NG;
+    using ST = ResStrides<LL>;
+    constexpr int NP = LL::NP, NF = LL::NF, GST = LL::GST;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     int* nbr0 = reinterpret_cast<int*>(smem_raw);
     int* nbr1 = nbr0 + PL::NBR_INTS;
     real* buf0 = reinterpret_cast<real*>(smem_raw + 2 * LL::NBR_BYTES);
-    real* buf1 = buf0 + (PL::NBUF - 1) * LL::EB * PL::LOAD;
-    real* work = buf0 + PL::NBUF * LL::EB * PL::LOAD;
+    real* buf1 = buf0 + (PL::NBUF - 1) * PL::LOAD;
+    real* work = buf0 + PL::NBUF * PL::LOAD;
     const int ngroups = (g.nelem + LL::EB - 1) / LL::EB;
     int grp = blockIdx.x;
     if (grp >= ngroups) return;
     const LineId id = line_id<LL>(threadIdx.x);
-    real* tro = work + id.eb * (LL::S_TR + LL::S_VS);
-    real* vS = tro + LL::S_TR;
+    real* tro = work + id.eb * (NF * LL::FST + LL::S_VS);
+    real* vS = tro + NF * LL::FST;
     pipe_start<real, LL, PL, NV, true, false>(U, Tu, nullptr, g, grp, buf0, nbr0);
     for (int b = 0; grp < ngroups; grp += gridDim.x, b ^= 1) {
         real* buf = b ? buf1 : buf0;
@@ -493,15 +512,15 @@ k_line_grad(const real* __restrict__ U, const real* __restrict__ Tu, real* __res
                                                  b ? buf0 : buf1, b ? nbr0 : nbr1, geo.off0, geo.off4);
         const int e = e0 + id.eb;
         const bool live = id.ok && e < g.nelem;
-        real* su = buf + id.eb * PL::LOAD;
-        real* trn = su + PL::OFF_TR;
-        prologue<real, N, DIM, NV>(geo, id, live, su, tro, trn, vS);
+        real* su = buf + id.eb * NP;
+        real* trn = buf + PL::OFF_TR + id.eb * NF * LL::FST;
+        prologue<real, N, DIM, NV, ST>(geo, id, live, su, tro, trn, vS);
         if (live) {
-            real* out = Tg + (size_t)e * NF * NG * NQ;
-            if (id.d == 0) grad_faces<real, N, DIM, NV, 0>(geo, compact, vS, tro, trn, out, id.q);
+            real* out = Tg + (size_t)e * NF * GST;
+            if (id.d == 0) grad_faces<real, N, DIM, NV, 0, ST>(geo, compact, vS, tro, trn, out, id.q);
             if constexpr (DIM == 3) {
-                if (id.d == 1) grad_faces<real, N, DIM, NV, 1>(geo, compact, vS, tro, trn, out, id.q);
-                if (id.d == 2) grad_faces<real, N, DIM, NV, 2>(geo, compact, vS, tro, trn, out, id.q);
+                if (id.d == 1) grad_faces<real, N, DIM, NV, 1, ST>(geo, compact, vS, tro, trn, out, id.q);
+                if (id.d == 2) grad_faces<real, N, DIM, NV, 2, ST>(geo, compact, vS, tro, trn, out, id.q);
             }
         }
         __syncthreads();
@@ -546,12 +565,12 @@ __device__ __forceinline__ void face_point(const real* __restrict__ Tu, const re
                                            real* __restrict__ Fh, const LineGeo<real>& geo, const Mesh& g,
                                            const Phys<real>& P, const float* __restrict__ tau, int e, int q) {
     using LL = LineLayout<N, DIM, NV>;
-    constexpr int NQ = LL::NQ, NF = LL::NF, NG = LL::NG;
+    constexpr int NQ = LL::NQ, NF = LL::NF, NG = LL::NG, FST = LL::FST, GST = LL::GST;
     const int en = neighbour(g, e, D, 1);
-    const real* tl = Tu + ((size_t)e * NF + 2 * D + 1) * NV * NQ + q;
-    const real* tr = Tu + ((size_t)en * NF + 2 * D) * NV * NQ + q;
-    const real* gl = Tg + ((size_t)e * NF + 2 * D + 1) * NG * NQ + q;
-    const real* gr = Tg + ((size_t)en * NF + 2 * D) * NG * NQ + q;
+    const real* tl = Tu + ((size_t)e * NF + 2 * D + 1) * FST + q;
+    const real* tr = Tu + ((size_t)en * NF + 2 * D) * FST + q;
+    const real* gl = Tg + ((size_t)e * NF + 2 * D + 1) * GST + q;
+    const real* gr = Tg + ((size_t)en * NF + 2 * D) * GST + q;
     real UL[NV], UR[NV], gL[NG], gR[NG], F[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
@@ -570,7 +589,7 @@ __device__ __forceinline__ void face_point(const real* __restrict__ Tu, const re
         tauR = tau + (size_t)en * 15;
     }
     interface_flux<real, NV, NG, D>(geo, P, UL, UR, gL, gR, tauL, tauR, F);
-    real* out = Fh + ((size_t)D * g.nelem + e) * NV * NQ + q;
+    real* out = Fh + ((size_t)D * g.nelem + e) * FST + q;
 #pragma unroll
     for (int v = 0; v < NV; ++v) out[v * NQ] = F[v];
 }
@@ -599,7 +618,7 @@ k_face_flux(const real* __restrict__ Tu, const real* __restrict__ Tg, real* __re
 
 // fluxes along D at the n+1 flux points of line q and their divergence on the line: the
 // interface fluxes at f = 0 and f = N come from Fh, the n-1 interior ones are evaluated here
-template <typename real, int N, int DIM, int NV, int D>
+template <typename real, int N, int DIM, int NV, int D, class ST>
 __device__ __forceinline__ void line_flux(const LineGeo<real>& geo, const Phys<real>& P, const real* su,
                                           const real* vS, const real* fh, int q, real (&r)[NV][N],
                                           const float* tau_own) {
@@ -609,8 +628,8 @@ __device__ __forceinline__ void line_flux(const LineGeo<real>& geo, const Phys<r
     // interface flux points (f = 0 and f = N)
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
-        const real F0 = fh[((2 * D) * NV + v) * NQ + q];
-        const real FN = fh[((2 * D + 1) * NV + v) * NQ + q];
+        const real F0 = fh[(2 * D) * ST::FS + v * NQ + q];
+        const real FN = fh[(2 * D + 1) * ST::FS + v * NQ + q];
 #pragma unroll
         for (int i = 0; i < N; ++i) r[v][i] = fma(op.M[i * (N + 1) + N], FN, op.M[i * (N + 1)] * F0);
     }
@@ -619,7 +638,7 @@ __device__ __forceinline__ void line_flux(const LineGeo<real>& geo, const Phys<r
 #pragma unroll
     for (int v = 0; v < NV; ++v)
 #pragma unroll
-        for (int i = 0; i < N; ++i) u[v][i] = su[v * NP + lpt<N, D>(i, q)];
+        for (int i = 0; i < N; ++i) u[v][i] = su[v * ST::US + lpt<N, D>(i, q)];
 #pragma unroll 1
     for (int f = 1; f < N; ++f) {
         const real* Lr = op.L + f * N;
@@ -669,42 +688,43 @@ k_line_flux(const real* __restrict__ U, const real* __restrict__ Tu, const real*
             real* __restrict__ R, LineGeo<real> geo, Mesh g, Phys<real> P, const float* __restrict__ tau) {
     using LL = LineLayout<N, DIM, NV>;
     using PL = FluxPipe<real, LL>;
-    constexpr int NP = LL::NP;
+    using ST = ResStrides<LL>;
+    constexpr int NP = LL::NP, NF = LL::NF, EB = LL::EB;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     int* nbr0 = reinterpret_cast<int*>(smem_raw);
     int* nbr1 = nbr0 + PL::NBR_INTS;
     real* buf0 = reinterpret_cast<real*>(smem_raw + 2 * LL::NBR_BYTES);
-    real* buf1 = buf0 + (PL::NBUF - 1) * LL::EB * PL::LOAD;
-    real* work = buf0 + PL::NBUF * LL::EB * PL::LOAD;
-    const int ngroups = (g.nelem + LL::EB - 1) / LL::EB;
+    real* buf1 = buf0 + (PL::NBUF - 1) * PL::LOAD;
+    real* work = buf0 + PL::NBUF * PL::LOAD;
+    const int ngroups = (g.nelem + EB - 1) / EB;
     int grp = blockIdx.x;
     if (grp >= ngroups) return;
     const LineId id = line_id<LL>(threadIdx.x);
-    real* tro = work + id.eb * (LL::S_TR + LL::S_VS);
-    real* vS = tro + LL::S_TR;
+    real* tro = work + id.eb * (NF * LL::FST + LL::S_VS);
+    real* vS = tro + NF * LL::FST;
     pipe_start<real, LL, PL, NV, true, true>(U, Tu, Fh, g, grp, buf0, nbr0);
     for (int b = 0; grp < ngroups; grp += gridDim.x, b ^= 1) {
         real* buf = b ? buf1 : buf0;
-        const int e0 = grp * LL::EB, nloc = min(LL::EB, g.nelem - e0);
+        const int e0 = grp * EB, nloc = min(EB, g.nelem - e0);
         pipe_next<real, LL, PL, NV, true, true>(U, Tu, Fh, g, grp, ngroups, buf, b ? nbr1 : nbr0,
                                                 b ? buf0 : buf1, b ? nbr0 : nbr1, geo.off0, geo.off4);
         const int e = e0 + id.eb;
         const bool live = id.ok && e < g.nelem;
-        real* su = buf + id.eb * PL::LOAD;
-        real* trn = su + PL::OFF_TR;
-        real* fh = su + PL::OFF_FH;
-        prologue<real, N, DIM, NV>(geo, id, live, su, tro, trn, vS);
+        real* su = buf + id.eb * NP;
+        real* trn = buf + PL::OFF_TR + id.eb * NF * LL::FST;
+        real* fh = buf + PL::OFF_FH + id.eb * NF * LL::FST;
+        prologue<real, N, DIM, NV, ST>(geo, id, live, su, tro, trn, vS);
 
         real r[NV][N];
         if (live) {
             const float* t0 = (NV == 5 && tau) ? tau + (size_t)e * 15 : nullptr;
-            if (id.d == 0) line_flux<real, N, DIM, NV, 0>(geo, P, su, vS, fh, id.q, r, t0);
+            if (id.d == 0) line_flux<real, N, DIM, NV, 0, ST>(geo, P, su, vS, fh, id.q, r, t0);
             if constexpr (DIM == 3) {
-                if (id.d == 1) line_flux<real, N, DIM, NV, 1>(geo, P, su, vS, fh, id.q, r, t0);
-                if (id.d == 2) line_flux<real, N, DIM, NV, 2>(geo, P, su, vS, fh, id.q, r, t0);
+                if (id.d == 1) line_flux<real, N, DIM, NV, 1, ST>(geo, P, su, vS, fh, id.q, r, t0);
+                if (id.d == 2) line_flux<real, N, DIM, NV, 2, ST>(geo, P, su, vS, fh, id.q, r, t0);
             }
         }
-        // every line has read u and v^S: the u slot now accumulates R, direction by
+        // every line has read u and v^S: the u slots now accumulate R, direction by
         // direction in the fixed order x, y, z (deterministic sums)
         __syncthreads();
 #pragma unroll 1
@@ -718,17 +738,19 @@ k_line_flux(const real* __restrict__ U, const real* __restrict__ Tu, const real*
                         if (dd == 0) pt = lpt<N, 0>(i, id.q);
                         else if (dd == 1) pt = lpt<N, (DIM == 3 ? 1 : 0)>(i, id.q);
                         else pt = lpt<N, (DIM == 3 ? 2 : 0)>(i, id.q);
-                        real* dst = su + v * NP + pt;
+                        real* dst = su + v * ST::US + pt;
                         *dst = (dd == 0) ? r[v][i] : *dst + r[v][i];
                     }
             }
             __syncthreads();
         }
-        for (int k = threadIdx.x; k < nloc * NV * NP; k += blockDim.x) {
-            const int eb = k / (NV * NP);
-            const int rr = k - eb * NV * NP;
-            const int v = rr / NP, pt = rr - v * NP;
-            R[(size_t)v * g.nelem * NP + (size_t)(e0 + eb) * NP + pt] = buf[eb * PL::LOAD + rr];
+        // R of the group: per variable one contiguous run in both R and the copy
+        const int span = nloc * NP;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            real* dst = R + (size_t)v * g.nelem * NP + (size_t)e0 * NP;
+            const real* src = buf + v * EB * NP;
+            for (int j = threadIdx.x; j < span; j += blockDim.x) dst[j] = src[j];
         }
         __syncthreads();
     }
