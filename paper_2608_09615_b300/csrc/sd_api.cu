@@ -201,14 +201,32 @@ static void build_operators(sd_ctx* c) {
         for (int i = 0; i < n; ++i) L[f * n + i] = lagrange_t<ldouble>(xs, n, i, xf[f]);
     for (int i = 0; i < n; ++i)
         for (int f = 0; f <= n; ++f) M[i * (n + 1) + f] = lagrange_d_t<ldouble>(xf, n + 1, f, xs[i]);
+    ldouble D[SD_MAX_N * SD_MAX_N];
     for (int i = 0; i < n; ++i) {
         c->xs[i] = (double)xs[i];
         c->ws[i] = (double)ws[i];
         for (int j = 0; j < n; ++j) {
             ldouble s = 0;
             for (int f = 0; f <= n; ++f) s += M[i * (n + 1) + f] * L[f * n + j];
+            D[i * n + j] = s;
             c->D[i * n + j] = (double)s;
         }
+    }
+    // products with L, used to evaluate the derivative along a line directly at the flux
+    // points: L_f (D u + M[:,0] d_L + M[:,n] d_R) = (L D)_f u + (L M)_{f0} d_L + (L M)_{fn} d_R
+    for (int f = 0; f <= n; ++f) {
+        for (int i = 0; i < n; ++i) {
+            ldouble s = 0;
+            for (int j = 0; j < n; ++j) s += L[f * n + j] * D[j * n + i];
+            c->LD[f * n + i] = (double)s;
+        }
+        ldouble s0 = 0, sn = 0;
+        for (int j = 0; j < n; ++j) {
+            s0 += L[f * n + j] * M[j * (n + 1) + 0];
+            sn += L[f * n + j] * M[j * (n + 1) + n];
+        }
+        c->LM0[f] = (double)s0;
+        c->LMN[f] = (double)sn;
     }
     for (int f = 0; f <= n; ++f) c->xf[f] = (double)xf[f];
     for (int k = 0; k < (n + 1) * n; ++k) c->L[k] = (double)L[k];

@@ -28,6 +28,8 @@ struct sd_ctx {
     double L[(SD_MAX_N + 1) * SD_MAX_N];     // L[f*n + i]
     double M[SD_MAX_N * (SD_MAX_N + 1)];     // M[i*(n+1) + f]
     double D[SD_MAX_N * SD_MAX_N];           // D = M L
+    double LD[(SD_MAX_N + 1) * SD_MAX_N];    // LD[f*n + i] = (L D)[f][i]: derivative of the interpolant at flux point f
+    double LM0[SD_MAX_N + 1], LMN[SD_MAX_N + 1];   // (L M)[f][0], (L M)[f][n]: weights of the face corrections
     double alpha, beta;
     // sizes
     size_t npts;             // points per variable = nelem * n^dim

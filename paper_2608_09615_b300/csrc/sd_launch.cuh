@@ -95,6 +95,11 @@ static sd_status upload_ops(const sd_ctx* c) {
     for (int k = 0; k < (N + 1) * N; ++k) t.L[k] = (real)c->L[k];
     for (int k = 0; k < N * (N + 1); ++k) t.M[k] = (real)c->M[k];
     for (int k = 0; k < N * N; ++k) t.D[k] = (real)c->D[k];
+    for (int k = 0; k < (N + 1) * N; ++k) t.LD[k] = (real)c->LD[k];
+    for (int f = 0; f <= N; ++f) {
+        t.LM0[f] = (real)c->LM0[f];
+        t.LMN[f] = (real)c->LMN[f];
+    }
     if (cudaMemcpyToSymbol(c_op<real, N>, &t, sizeof(t)) != cudaSuccess) {
         sdi_set_error("upload of the operator table failed");
         return SD_ECUDA;

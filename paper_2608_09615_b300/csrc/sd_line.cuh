@@ -50,6 +50,9 @@ struct OpTab {
     real L[(N + 1) * N];     // L[f*N + i]     = l_i(xi_{f-1/2})          (Eq. Lmat)
     real M[N * (N + 1)];     // M[i*(N+1) + f] = l'_{f-1/2}(xi_i)         (Eq. Mmat)
     real D[N * N];           // D = M L
+    real LD[(N + 1) * N];    // LD[f*N + i] = (L D)[f][i]
+    real LM0[N + 1];         // (L M)[f][0]
+    real LMN[N + 1];         // (L M)[f][N]
 };
 
 template <typename real, int N>
@@ -88,6 +91,8 @@ struct LineLayout {
     static constexpr int S_U = NV * NP;
     static constexpr int S_TR = NF * NV * NQ;
     static constexpr int S_VS = NV * DIM * NP;
+    // v^S components the residual kernels keep (vslot): 9 for Navier-Stokes, none for scalars
+    static constexpr int S_VR = (NV == 5 ? 9 : 0) * NP;
     static constexpr int PER_GRAD = S_U + 2 * S_TR + S_VS;
     static constexpr int NBR_BYTES = ((EB * NF * 4 + 15) / 16) * 16;   // neighbour table
     static constexpr int REG_FIT = (65536 / THREADS) / 8 * 8;
@@ -147,6 +152,26 @@ __device__ __forceinline__ real dotc(const real* row, const real* x) {
 #pragma unroll
     for (int i = 1; i < N; ++i) s = fma(row[i], x[i], s);
     return s;
+}
+
+// Slot of the v^S component (variable v, derivative direction m) the residual kernels
+// keep: the derivative along m of rho and of the two momentum components across m. These
+// are the transverse gradient components the lines of the other two directions need (the
+// viscous flux along d uses d/dx_t of rho and rho u_d, t != d); a line's own normal
+// derivatives are evaluated from u directly (dline).
+__host__ __device__ constexpr int vslot(int v, int m) {
+    return v == 0 ? 3 * m : (v - 1 == (m + 1) % 3 ? 3 * m + 1 : 3 * m + 2);
+}
+
+// derivative along the line of the variable with line values u[] at flux point f:
+// L_f v = (2/h) L_f (D u + M[:,0] dl + M[:,N] dr) = (2/h) ((L D)_f u + (L M)_{f0} dl + (L M)_{fN} dr)
+template <typename real, int N>
+__device__ __forceinline__ real dline(const OpTab<real, N>& op, int f, const real* u, real dl, real dr,
+                                      real two_h) {
+    real a = dotc<real, N>(op.LD + f * N, u);
+    a = fma(op.LM0[f], dl, a);
+    a = fma(op.LMN[f], dr, a);
+    return two_h * a;
 }
 
 // ---------------------------------------------------------------- staging helpers
@@ -242,9 +267,9 @@ struct Pipe {
 template <typename real, class LL>
 using TracePipe = Pipe<LL, false, false, real, 0>;
 template <typename real, class LL>
-using GradPipe = Pipe<LL, true, false, real, LL::NF * LL::FST + LL::S_VS>;
+using GradPipe = Pipe<LL, true, false, real, LL::NF * LL::FST + LL::S_VR>;
 template <typename real, class LL>
-using FluxPipe = Pipe<LL, true, true, real, LL::NF * LL::FST + LL::S_VS>;
+using FluxPipe = Pipe<LL, true, true, real, LL::NF * LL::FST + LL::S_VR>;
 
 template <class LL>
 using ResStrides = Strides<LL::EB * LL::NP, LL::FST>;
@@ -449,6 +474,107 @@ __device__ __forceinline__ void grad_faces(const LineGeo<real>& geo, int compact
     }
 }
 
+// residual form of v^S along D: only the three components other lines need (vslot)
+template <typename real, int N, int DIM, int D, class ST>
+__device__ __forceinline__ void line_vs_res(const LineGeo<real>& geo, const real* su, const real* tro,
+                                            const real* trn, real* vS, int q) {
+    constexpr int NP = ipow(N, DIM), NQ = ipow(N, DIM - 1);
+    const OpTab<real, N>& op = c_op<real, N>;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const int v = k == 0 ? 0 : 1 + (D + k) % 3;
+        real u[N];
+#pragma unroll
+        for (int i = 0; i < N; ++i) u[i] = su[v * ST::US + lpt<N, D>(i, q)];
+        const int il = (2 * D) * ST::FS + v * NQ + q, ir = (2 * D + 1) * ST::FS + v * NQ + q;
+        const real dl = real(0.5) * (trn[il] - tro[il]);
+        const real dr = real(0.5) * (trn[ir] - tro[ir]);
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            real acc = dotc<real, N>(op.D + i * N, u);
+            acc = fma(op.M[i * (N + 1)], dl, acc);
+            acc = fma(op.M[i * (N + 1) + N], dr, acc);
+            vS[vslot(v, D) * NP + lpt<N, D>(i, q)] = geo.two_h[D] * acc;
+        }
+    }
+}
+
+// prologue of the residual gradient and flux kernels: own traces, then the kept v^S
+template <typename real, int N, int DIM, int NV, class ST>
+__device__ __forceinline__ void prologue_res(const LineGeo<real>& geo, const LineId& id, bool live,
+                                             real* su, real* tro, real* trn, real* vS) {
+    constexpr int NQ = ipow(N, DIM - 1), FS = ST::FS;
+    if (live) {
+        real* o = tro + id.q;
+        if (id.d == 0) line_traces<real, N, NQ, NV, 0, ST>(su, id.q, o, o + FS, NQ);
+        if constexpr (DIM == 3) {
+            if (id.d == 1) line_traces<real, N, NQ, NV, 1, ST>(su, id.q, o + 2 * FS, o + 3 * FS, NQ);
+            if (id.d == 2) line_traces<real, N, NQ, NV, 2, ST>(su, id.q, o + 4 * FS, o + 5 * FS, NQ);
+        }
+    }
+    __syncthreads();
+    if constexpr (NV == 5) {
+        if (live) {
+            if (id.d == 0) line_vs_res<real, N, DIM, 0, ST>(geo, su, tro, trn, vS, id.q);
+            if (id.d == 1) line_vs_res<real, N, DIM, 1, ST>(geo, su, tro, trn, vS, id.q);
+            if (id.d == 2) line_vs_res<real, N, DIM, 2, ST>(geo, su, tro, trn, vS, id.q);
+        }
+        __syncthreads();
+    }
+}
+
+// face corrections delta_L, delta_R of every variable of line q (Eq. c:flux)
+template <typename real, int NQ, int NV, int D, class ST>
+__device__ __forceinline__ void line_deltas(const real* tro, const real* trn, int q, real* dl, real* dr) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+        const int il = (2 * D) * ST::FS + v * NQ + q, ir = (2 * D + 1) * ST::FS + v * NQ + q;
+        dl[v] = real(0.5) * (trn[il] - tro[il]);
+        dr[v] = real(0.5) * (trn[ir] - tro[ir]);
+    }
+}
+
+// residual form of grad_faces: normal components from u and the corrections (BR1:
+// L_s v^S; compact: the one-sided gradient keeps only the correction of face s, the
+// closed form of Eqs. aux:cmp:lr:2d), transverse components from the kept v^S
+template <typename real, int N, int DIM, int NV, int D, class ST>
+__device__ __forceinline__ void grad_faces_res(const LineGeo<real>& geo, int compact, const real* su,
+                                               const real* vS, const real* tro, const real* trn, real* out,
+                                               int q) {
+    using LL = LineLayout<N, DIM, NV>;
+    constexpr int NP = LL::NP, NQ = LL::NQ, NG = LL::NG, GST = LL::GST;
+    const OpTab<real, N>& op = c_op<real, N>;
+    const real th = geo.two_h[D];
+    real dl[NV], dr[NV];
+    line_deltas<real, NQ, NV, D, ST>(tro, trn, q, dl, dr);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+        real u[N];
+#pragma unroll
+        for (int i = 0; i < N; ++i) u[i] = su[v * ST::US + lpt<N, D>(i, q)];
+        real aL, aR;
+        if (compact) {
+            aL = th * fma(op.LM0[0], dl[v], dotc<real, N>(op.LD, u));
+            aR = th * fma(op.LMN[N], dr[v], dotc<real, N>(op.LD + N * N, u));
+        } else {
+            aL = dline<real, N>(op, 0, u, dl[v], dr[v], th);
+            aR = dline<real, N>(op, N, u, dl[v], dr[v], th);
+        }
+        out[(2 * D) * GST + v * NQ + q] = aL;
+        out[(2 * D + 1) * GST + v * NQ + q] = aR;
+    }
+#pragma unroll
+    for (int c = NV; c < NG; ++c) {
+        int v, m;
+        comp_map<NV>(D, c, v, m);
+        real gl[N];
+#pragma unroll
+        for (int i = 0; i < N; ++i) gl[i] = vS[vslot(v, m) * NP + lpt<N, D>(i, q)];
+        out[(2 * D) * GST + c * NQ + q] = dotc<real, N>(op.L, gl);
+        out[(2 * D + 1) * GST + c * NQ + q] = dotc<real, N>(op.L + N * N, gl);
+    }
+}
+
 // ---------------------------------------------------------------- kernels
 template <typename real, int N, int DIM, int NV>
 __global__ void __launch_bounds__(LineLayout<N, DIM, NV>::THREADS)
@@ -502,7 +628,7 @@ k_line_grad(const real* __restrict__ U, const real* __restrict__ Tu, real* __res
     int grp = blockIdx.x;
     if (grp >= ngroups) return;
     const LineId id = line_id<LL>(threadIdx.x);
-    real* tro = work + id.eb * (NF * LL::FST + LL::S_VS);
+    real* tro = work + id.eb * (NF * LL::FST + LL::S_VR);
     real* vS = tro + NF * LL::FST;
     pipe_start<real, LL, PL, NV, true, false>(U, Tu, nullptr, g, grp, buf0, nbr0);
     for (int b = 0; grp < ngroups; grp += gridDim.x, b ^= 1) {
@@ -514,13 +640,13 @@ k_line_grad(const real* __restrict__ U, const real* __restrict__ Tu, real* __res
         const bool live = id.ok && e < g.nelem;
         real* su = buf + id.eb * NP;
         real* trn = buf + PL::OFF_TR + id.eb * NF * LL::FST;
-        prologue<real, N, DIM, NV, ST>(geo, id, live, su, tro, trn, vS);
+        prologue_res<real, N, DIM, NV, ST>(geo, id, live, su, tro, trn, vS);
         if (live) {
             real* out = Tg + (size_t)e * NF * GST;
-            if (id.d == 0) grad_faces<real, N, DIM, NV, 0, ST>(geo, compact, vS, tro, trn, out, id.q);
+            if (id.d == 0) grad_faces_res<real, N, DIM, NV, 0, ST>(geo, compact, su, vS, tro, trn, out, id.q);
             if constexpr (DIM == 3) {
-                if (id.d == 1) grad_faces<real, N, DIM, NV, 1, ST>(geo, compact, vS, tro, trn, out, id.q);
-                if (id.d == 2) grad_faces<real, N, DIM, NV, 2, ST>(geo, compact, vS, tro, trn, out, id.q);
+                if (id.d == 1) grad_faces_res<real, N, DIM, NV, 1, ST>(geo, compact, su, vS, tro, trn, out, id.q);
+                if (id.d == 2) grad_faces_res<real, N, DIM, NV, 2, ST>(geo, compact, su, vS, tro, trn, out, id.q);
             }
         }
         __syncthreads();
@@ -620,8 +746,8 @@ k_face_flux(const real* __restrict__ Tu, const real* __restrict__ Tg, real* __re
 // interface fluxes at f = 0 and f = N come from Fh, the n-1 interior ones are evaluated here
 template <typename real, int N, int DIM, int NV, int D, class ST>
 __device__ __forceinline__ void line_flux(const LineGeo<real>& geo, const Phys<real>& P, const real* su,
-                                          const real* vS, const real* fh, int q, real (&r)[NV][N],
-                                          const float* tau_own) {
+                                          const real* vS, const real* tro, const real* trn, const real* fh,
+                                          int q, real (&r)[NV][N], const float* tau_own) {
     using LL = LineLayout<N, DIM, NV>;
     constexpr int NP = LL::NP, NQ = LL::NQ, NG = LL::NG;
     const OpTab<real, N>& op = c_op<real, N>;
@@ -633,12 +759,16 @@ __device__ __forceinline__ void line_flux(const LineGeo<real>& geo, const Phys<r
 #pragma unroll
         for (int i = 0; i < N; ++i) r[v][i] = fma(op.M[i * (N + 1) + N], FN, op.M[i * (N + 1)] * F0);
     }
-    // interior flux points: extrapolated solution and gradient (Eq. aux:v:std:2d)
-    real u[NV][N];
+    // interior flux points: extrapolated solution and gradient (Eq. aux:v:std:2d); the
+    // normal derivatives come from u and the face corrections (dline), the transverse ones
+    // from the kept v^S
+    real u[NV][N], dl[NV], dr[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v)
 #pragma unroll
         for (int i = 0; i < N; ++i) u[v][i] = su[v * ST::US + lpt<N, D>(i, q)];
+    line_deltas<real, NQ, NV, D, ST>(tro, trn, q, dl, dr);
+    const real th = geo.two_h[D];
 #pragma unroll 1
     for (int f = 1; f < N; ++f) {
         const real* Lr = op.L + f * N;
@@ -648,12 +778,14 @@ __device__ __forceinline__ void line_flux(const LineGeo<real>& geo, const Phys<r
         if constexpr (NV == 5) {
             real gf[NG];
 #pragma unroll
-            for (int c = 0; c < NG; ++c) {
+            for (int c = 0; c < NV; ++c) gf[c] = dline<real, N>(op, f, u[c], dl[c], dr[c], th);
+#pragma unroll
+            for (int c = NV; c < NG; ++c) {
                 int v, m;
                 comp_map<NV>(D, c, v, m);
                 real gl[N];
 #pragma unroll
-                for (int i = 0; i < N; ++i) gl[i] = vS[(v * DIM + m) * NP + lpt<N, D>(i, q)];
+                for (int i = 0; i < N; ++i) gl[i] = vS[vslot(v, m) * NP + lpt<N, D>(i, q)];
                 gf[c] = dotc<real, N>(Lr, gl);
             }
             real Fv[NV];
@@ -666,10 +798,7 @@ __device__ __forceinline__ void line_flux(const LineGeo<real>& geo, const Phys<r
 #pragma unroll
             for (int v = 0; v < NV; ++v) F[v] -= Fv[v];
         } else {
-            real gl[N];
-#pragma unroll
-            for (int i = 0; i < N; ++i) gl[i] = vS[D * NP + lpt<N, D>(i, q)];
-            F[0] = scalar_flux(P, uf[0], dotc<real, N>(Lr, gl));
+            F[0] = scalar_flux(P, uf[0], dline<real, N>(op, f, u[0], dl[0], dr[0], th));
         }
 #pragma unroll
         for (int v = 0; v < NV; ++v)
@@ -700,7 +829,7 @@ k_line_flux(const real* __restrict__ U, const real* __restrict__ Tu, const real*
     int grp = blockIdx.x;
     if (grp >= ngroups) return;
     const LineId id = line_id<LL>(threadIdx.x);
-    real* tro = work + id.eb * (NF * LL::FST + LL::S_VS);
+    real* tro = work + id.eb * (NF * LL::FST + LL::S_VR);
     real* vS = tro + NF * LL::FST;
     pipe_start<real, LL, PL, NV, true, true>(U, Tu, Fh, g, grp, buf0, nbr0);
     for (int b = 0; grp < ngroups; grp += gridDim.x, b ^= 1) {
@@ -713,15 +842,15 @@ k_line_flux(const real* __restrict__ U, const real* __restrict__ Tu, const real*
         real* su = buf + id.eb * NP;
         real* trn = buf + PL::OFF_TR + id.eb * NF * LL::FST;
         real* fh = buf + PL::OFF_FH + id.eb * NF * LL::FST;
-        prologue<real, N, DIM, NV, ST>(geo, id, live, su, tro, trn, vS);
+        prologue_res<real, N, DIM, NV, ST>(geo, id, live, su, tro, trn, vS);
 
         real r[NV][N];
         if (live) {
             const float* t0 = (NV == 5 && tau) ? tau + (size_t)e * 15 : nullptr;
-            if (id.d == 0) line_flux<real, N, DIM, NV, 0, ST>(geo, P, su, vS, fh, id.q, r, t0);
+            if (id.d == 0) line_flux<real, N, DIM, NV, 0, ST>(geo, P, su, vS, tro, trn, fh, id.q, r, t0);
             if constexpr (DIM == 3) {
-                if (id.d == 1) line_flux<real, N, DIM, NV, 1, ST>(geo, P, su, vS, fh, id.q, r, t0);
-                if (id.d == 2) line_flux<real, N, DIM, NV, 2, ST>(geo, P, su, vS, fh, id.q, r, t0);
+                if (id.d == 1) line_flux<real, N, DIM, NV, 1, ST>(geo, P, su, vS, tro, trn, fh, id.q, r, t0);
+                if (id.d == 2) line_flux<real, N, DIM, NV, 2, ST>(geo, P, su, vS, tro, trn, fh, id.q, r, t0);
             }
         }
         // every line has read u and v^S: the u slots now accumulate R, direction by
