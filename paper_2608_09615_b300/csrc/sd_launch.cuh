@@ -231,13 +231,15 @@ static sd_status residual_impl(sd_ctx* c, const real* U, real* R, int offset_in)
     const long long ngroups = (g.nelem + LL::EB - 1) / LL::EB;
     const size_t st = TracePipe<real, LL>::BYTES;
     const size_t sg = GradPipe<real, LL>::BYTES;
-    const size_t sf = FluxPipe<real, LL>::BYTES;
+    using FL = FluxLayout<N, DIM, NV>;
+    const size_t sf = FluxPipe<real, FL>::BYTES;
     if (!set_smem(k_line_trace<real, N, DIM, NV>, st) || !set_smem(k_line_grad<real, N, DIM, NV>, sg) ||
         !set_smem(k_line_flux<real, N, DIM, NV>, sf))
         return SD_EUNSUPPORTED;
     const int bt = persistent_grid(k_line_trace<real, N, DIM, NV>, LL::THREADS, st, ngroups, c->device);
     const int bg = persistent_grid(k_line_grad<real, N, DIM, NV>, LL::THREADS, sg, ngroups, c->device);
-    const int bf = persistent_grid(k_line_flux<real, N, DIM, NV>, LL::THREADS, sf, ngroups, c->device);
+    const int bf = persistent_grid(k_line_flux<real, N, DIM, NV>, FL::THREADS, sf, (g.nelem + FL::EB - 1) / FL::EB,
+                                   c->device);
     real* Fh = static_cast<real*>(c->Fh);
     sdi_prof_begin(c, SD_K_TRACE);
     k_line_trace<real, N, DIM, NV><<<bt, LL::THREADS, st, c->stream>>>(U, Tu, geo, g);
@@ -254,7 +256,7 @@ static sd_status residual_impl(sd_ctx* c, const real* U, real* R, int offset_in)
         Tu, Tg, Fh, geo, g, P, c->tau);
     sdi_prof_end(c, SD_K_FACE);
     sdi_prof_begin(c, SD_K_FLUX);
-    k_line_flux<real, N, DIM, NV><<<bf, LL::THREADS, sf, c->stream>>>(U, Tu, Fh, R, geo, g, P, c->tau);
+    k_line_flux<real, N, DIM, NV><<<bf, FL::THREADS, sf, c->stream>>>(U, Tu, Fh, R, geo, g, P, c->tau);
     sdi_prof_end(c, SD_K_FLUX);
     const cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) {

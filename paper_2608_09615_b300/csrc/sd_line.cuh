@@ -30,15 +30,20 @@
 
 #include "sd_kernels.cuh"
 
-// Threads per block the line kernels aim for (whole element groups of DIM warps), and the
-// register cap of k_line_flux (further limited to what one block of the layout can use).
-// 192 threads and no cap below the 143 registers the FP32 Navier-Stokes n = 5 case needs
-// without spills measured fastest among the layouts tried on B300.
+// Threads per block the line kernels aim for (whole element groups of DIM warps): 192 for
+// the trace and gradient kernels, 96 for k_line_flux, with a register cap of 136 for the
+// latter (further limited to what one block of the layout can use). For the FP32
+// Navier-Stokes n = 5 case on B300 this gives 5 resident flux blocks per SM without
+// spills; it measured fastest among the layouts tried (192 threads / 143 registers:
+// 1.24 ms per launch at 48^3, 96 / 136: 1.11 ms; 192 / 112: 1.25 ms).
 #ifndef SD_LINE_THREADS
 #define SD_LINE_THREADS 192
 #endif
+#ifndef SD_FLUX_THREADS
+#define SD_FLUX_THREADS 96
+#endif
 #ifndef SD_FLUX_MAXNREG
-#define SD_FLUX_MAXNREG 168
+#define SD_FLUX_MAXNREG 136
 #endif
 
 namespace sdk {
@@ -70,7 +75,7 @@ struct LineGeo {
 
 constexpr int round4(int x) { return (x + 3) / 4 * 4; }
 
-template <int N, int DIM, int NV>
+template <int N, int DIM, int NV, int TGT = SD_LINE_THREADS>
 struct LineLayout {
     static constexpr int NP = ipow(N, DIM);
     static constexpr int NQ = ipow(N, DIM - 1);
@@ -79,7 +84,7 @@ struct LineLayout {
     static constexpr int EPW = NQ <= 32 ? 32 / NQ : 1;            // elements per warp
     static constexpr int WPD = NQ <= 32 ? 1 : (NQ + 31) / 32;     // warps per direction
     static constexpr int UNIT = DIM * WPD * 32;                   // threads per element group
-    static constexpr int UPB = UNIT >= SD_LINE_THREADS ? 1 : SD_LINE_THREADS / UNIT;  // groups per block
+    static constexpr int UPB = UNIT >= TGT ? 1 : TGT / UNIT;      // groups per block
     static constexpr int THREADS = UPB * UNIT;
     static constexpr int EB = UPB * EPW;                          // elements per block
     // Global scratch layouts: Tu[e][f][FST] and Fh[d][e][FST] hold [v][q] in the first NV*NQ
@@ -811,11 +816,14 @@ __device__ __forceinline__ void line_flux(const LineGeo<real>& geo, const Phys<r
         for (int i = 0; i < N; ++i) r[v][i] = -geo.two_h[D] * r[v][i];
 }
 
+template <int N, int DIM, int NV>
+using FluxLayout = LineLayout<N, DIM, NV, SD_FLUX_THREADS>;
+
 template <typename real, int N, int DIM, int NV>
-__global__ void __maxnreg__((LineLayout<N, DIM, NV>::FLUX_REGS))
+__global__ void __maxnreg__((FluxLayout<N, DIM, NV>::FLUX_REGS))
 k_line_flux(const real* __restrict__ U, const real* __restrict__ Tu, const real* __restrict__ Fh,
             real* __restrict__ R, LineGeo<real> geo, Mesh g, Phys<real> P, const float* __restrict__ tau) {
-    using LL = LineLayout<N, DIM, NV>;
+    using LL = FluxLayout<N, DIM, NV>;
     using PL = FluxPipe<real, LL>;
     using ST = ResStrides<LL>;
     constexpr int NP = LL::NP, NF = LL::NF, EB = LL::EB;
