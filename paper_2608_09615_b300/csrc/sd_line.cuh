@@ -98,6 +98,8 @@ struct LineLayout {
     static constexpr int S_VS = NV * DIM * NP;
     // v^S components the residual kernels keep (vslot): 9 for Navier-Stokes, none for scalars
     static constexpr int S_VR = (NV == 5 ? 9 : 0) * NP;
+    // per-direction residual contributions R_d[v][pt] (flux kernel, in its work area)
+    static constexpr int S_RD = DIM * NV * NP;
     static constexpr int PER_GRAD = S_U + 2 * S_TR + S_VS;
     static constexpr int NBR_BYTES = ((EB * NF * 4 + 15) / 16) * 16;   // neighbour table
     static constexpr int REG_FIT = (65536 / THREADS) / 8 * 8;
@@ -273,8 +275,16 @@ template <typename real, class LL>
 using TracePipe = Pipe<LL, false, false, real, 0>;
 template <typename real, class LL>
 using GradPipe = Pipe<LL, true, false, real, LL::NF * LL::FST + LL::S_VR>;
+template <class LL>
+struct FluxWork;
 template <typename real, class LL>
-using FluxPipe = Pipe<LL, true, true, real, LL::NF * LL::FST + LL::S_VR>;
+using FluxPipe = Pipe<LL, true, true, real, FluxWork<LL>::value>;
+
+// work values per element of the flux kernel: own traces and kept v^S, later R_d
+template <class LL>
+struct FluxWork {
+    static constexpr int value = LL::NF * LL::FST + LL::S_VR > LL::S_RD ? LL::NF * LL::FST + LL::S_VR : LL::S_RD;
+};
 
 template <class LL>
 using ResStrides = Strides<LL::EB * LL::NP, LL::FST>;
@@ -325,42 +335,46 @@ __device__ __forceinline__ void stage_issue(const real* __restrict__ U, const re
     }
 }
 
-// neighbour table and copies of group grp into buf, as one committed copy group
-template <typename real, class LL, class PL, int NV, bool NB_TR, bool FH>
-__device__ __forceinline__ void stage_group(const real* __restrict__ U, const real* __restrict__ Tu,
-                                            const real* __restrict__ Fh, const Mesh& g, int grp, real* buf,
-                                            int* nbr) {
-    const int e0 = grp * LL::EB, nloc = min(LL::EB, g.nelem - e0);
-    if (NB_TR || FH) {
-        nbr_table<LL>(g, e0, nloc, nbr);
-        __syncthreads();
-    }
-    stage_issue<real, LL, PL, NV, NB_TR, FH>(U, Tu, Fh, g, e0, nloc, buf, nbr);
-    cp_async_commit();
-}
-
-// before the first group of the block: with two copies, start loading it
+// Pipeline steps. The neighbour table of a group is computed one iteration ahead, in the
+// tail of the previous group (pipe_tail, before that group's last barrier), so issuing a
+// group's copies needs no barrier of its own. With two copies the tables alternate
+// (nbr0 / nbr1 for even / odd iterations); with one, nbr0 is used throughout.
 template <typename real, class LL, class PL, int NV, bool NB_TR, bool FH>
 __device__ __forceinline__ void pipe_start(const real* __restrict__ U, const real* __restrict__ Tu,
-                                           const real* __restrict__ Fh, const Mesh& g, int grp, real* buf,
-                                           int* nbr) {
-    if constexpr (PL::NBUF == 2) stage_group<real, LL, PL, NV, NB_TR, FH>(U, Tu, Fh, g, grp, buf, nbr);
+                                           const real* __restrict__ Fh, const Mesh& g, int grp, int ngroups,
+                                           real* buf0, int* nbr0, int* nbr1) {
+    if (NB_TR || FH) {
+        nbr_table<LL>(g, grp * LL::EB, min(LL::EB, g.nelem - grp * LL::EB), nbr0);
+        const int gn = grp + gridDim.x;
+        if (PL::NBUF == 2 && gn < ngroups) nbr_table<LL>(g, gn * LL::EB, min(LL::EB, g.nelem - gn * LL::EB), nbr1);
+        __syncthreads();
+    }
+    if constexpr (PL::NBUF == 2) {
+        stage_issue<real, LL, PL, NV, NB_TR, FH>(U, Tu, Fh, g, grp * LL::EB, min(LL::EB, g.nelem - grp * LL::EB),
+                                                 buf0, nbr0);
+        cp_async_commit();
+    }
 }
 
-// at the top of each group: with two copies, start loading the next group (if any) into
-// the other copy; with one, load this group. Then wait for this group's copies, make them
-// visible to the block and remove the reference offsets.
+// at the top of iteration b (0, 1, 0, ...) for group grp: with two copies, start loading
+// the next group (if any) into the other copy; with one, load this group. Then wait for
+// this group's copies, make them visible to the block and remove the reference offsets.
 template <typename real, class LL, class PL, int NV, bool NB_TR, bool FH>
 __device__ __forceinline__ void pipe_next(const real* __restrict__ U, const real* __restrict__ Tu,
-                                          const real* __restrict__ Fh, const Mesh& g, int grp, int ngroups,
-                                          real* buf, int* nbr, real* nbuf, int* nnbr, real off0, real off4) {
+                                          const real* __restrict__ Fh, const Mesh& g, int grp, int ngroups, int b,
+                                          real* buf0, real* buf1, int* nbr0, int* nbr1, real off0, real off4) {
+    real* buf = b ? buf1 : buf0;
     if constexpr (PL::NBUF == 2) {
         const int gn = grp + gridDim.x;
-        if (gn < ngroups) stage_group<real, LL, PL, NV, NB_TR, FH>(U, Tu, Fh, g, gn, nbuf, nnbr);
-        else cp_async_commit();
+        if (gn < ngroups)
+            stage_issue<real, LL, PL, NV, NB_TR, FH>(U, Tu, Fh, g, gn * LL::EB, min(LL::EB, g.nelem - gn * LL::EB),
+                                                     b ? buf0 : buf1, b ? nbr0 : nbr1);
+        cp_async_commit();
         cp_async_wait_group<1>();
     } else {
-        stage_group<real, LL, PL, NV, NB_TR, FH>(U, Tu, Fh, g, grp, buf, nbr);
+        stage_issue<real, LL, PL, NV, NB_TR, FH>(U, Tu, Fh, g, grp * LL::EB, min(LL::EB, g.nelem - grp * LL::EB),
+                                                 buf, nbr0);
+        cp_async_commit();
         cp_async_wait_group<0>();
     }
     __syncthreads();
@@ -373,6 +387,18 @@ __device__ __forceinline__ void pipe_next(const real* __restrict__ U, const real
             u4[k] -= off4;
         }
         __syncthreads();
+    }
+}
+
+// tail of iteration b for group grp, before the iteration's last barrier: the neighbour
+// table of the group whose copies are issued next (two copies: grp + 2 grid into this
+// group's table; one copy: grp + grid into nbr0)
+template <class LL, class PL, bool NB>
+__device__ __forceinline__ void pipe_tail(const Mesh& g, int grp, int ngroups, int b, int* nbr0, int* nbr1) {
+    if constexpr (NB) {
+        const int ga = grp + (PL::NBUF == 2 ? 2 : 1) * gridDim.x;
+        if (ga < ngroups)
+            nbr_table<LL>(g, ga * LL::EB, min(LL::EB, g.nelem - ga * LL::EB), (PL::NBUF == 2 && b) ? nbr1 : nbr0);
     }
 }
 
@@ -595,12 +621,12 @@ k_line_trace(const real* __restrict__ U, real* __restrict__ Tu, LineGeo<real> ge
     int grp = blockIdx.x;
     if (grp >= ngroups) return;
     const LineId id = line_id<LL>(threadIdx.x);
-    pipe_start<real, LL, PL, NV, false, false>(U, nullptr, nullptr, g, grp, buf0, nullptr);
+    pipe_start<real, LL, PL, NV, false, false>(U, nullptr, nullptr, g, grp, ngroups, buf0, nullptr, nullptr);
     for (int b = 0; grp < ngroups; grp += gridDim.x, b ^= 1) {
         real* buf = b ? buf1 : buf0;
         const int e0 = grp * LL::EB;
-        pipe_next<real, LL, PL, NV, false, false>(U, nullptr, nullptr, g, grp, ngroups, buf, nullptr,
-                                                  b ? buf0 : buf1, nullptr, geo.off0, geo.off4);
+        pipe_next<real, LL, PL, NV, false, false>(U, nullptr, nullptr, g, grp, ngroups, b, buf0, buf1, nullptr,
+                                                  nullptr, geo.off0, geo.off4);
         const int e = e0 + id.eb;
         if (id.ok && e < g.nelem) {
             const real* su = buf + id.eb * NP;
@@ -635,12 +661,12 @@ k_line_grad(const real* __restrict__ U, const real* __restrict__ Tu, real* __res
     const LineId id = line_id<LL>(threadIdx.x);
     real* tro = work + id.eb * (NF * LL::FST + LL::S_VR);
     real* vS = tro + NF * LL::FST;
-    pipe_start<real, LL, PL, NV, true, false>(U, Tu, nullptr, g, grp, buf0, nbr0);
+    pipe_start<real, LL, PL, NV, true, false>(U, Tu, nullptr, g, grp, ngroups, buf0, nbr0, nbr1);
     for (int b = 0; grp < ngroups; grp += gridDim.x, b ^= 1) {
         real* buf = b ? buf1 : buf0;
         const int e0 = grp * LL::EB;
-        pipe_next<real, LL, PL, NV, true, false>(U, Tu, nullptr, g, grp, ngroups, buf, b ? nbr1 : nbr0,
-                                                 b ? buf0 : buf1, b ? nbr0 : nbr1, geo.off0, geo.off4);
+        pipe_next<real, LL, PL, NV, true, false>(U, Tu, nullptr, g, grp, ngroups, b, buf0, buf1, nbr0, nbr1,
+                                                 geo.off0, geo.off4);
         const int e = e0 + id.eb;
         const bool live = id.ok && e < g.nelem;
         real* su = buf + id.eb * NP;
@@ -654,6 +680,7 @@ k_line_grad(const real* __restrict__ U, const real* __restrict__ Tu, real* __res
                 if (id.d == 2) grad_faces_res<real, N, DIM, NV, 2, ST>(geo, compact, su, vS, tro, trn, out, id.q);
             }
         }
+        pipe_tail<LL, PL, true>(g, grp, ngroups, b, nbr0, nbr1);
         __syncthreads();
     }
 }
@@ -837,14 +864,15 @@ k_line_flux(const real* __restrict__ U, const real* __restrict__ Tu, const real*
     int grp = blockIdx.x;
     if (grp >= ngroups) return;
     const LineId id = line_id<LL>(threadIdx.x);
-    real* tro = work + id.eb * (NF * LL::FST + LL::S_VR);
+    constexpr int WPE = FluxWork<LL>::value;                   // work values per element
+    real* tro = work + id.eb * WPE;
     real* vS = tro + NF * LL::FST;
-    pipe_start<real, LL, PL, NV, true, true>(U, Tu, Fh, g, grp, buf0, nbr0);
+    pipe_start<real, LL, PL, NV, true, true>(U, Tu, Fh, g, grp, ngroups, buf0, nbr0, nbr1);
     for (int b = 0; grp < ngroups; grp += gridDim.x, b ^= 1) {
         real* buf = b ? buf1 : buf0;
         const int e0 = grp * EB, nloc = min(EB, g.nelem - e0);
-        pipe_next<real, LL, PL, NV, true, true>(U, Tu, Fh, g, grp, ngroups, buf, b ? nbr1 : nbr0,
-                                                b ? buf0 : buf1, b ? nbr0 : nbr1, geo.off0, geo.off4);
+        pipe_next<real, LL, PL, NV, true, true>(U, Tu, Fh, g, grp, ngroups, b, buf0, buf1, nbr0, nbr1,
+                                                geo.off0, geo.off4);
         const int e = e0 + id.eb;
         const bool live = id.ok && e < g.nelem;
         real* su = buf + id.eb * NP;
@@ -861,35 +889,37 @@ k_line_flux(const real* __restrict__ U, const real* __restrict__ Tu, const real*
                 if (id.d == 2) line_flux<real, N, DIM, NV, 2, ST>(geo, P, su, vS, tro, trn, fh, id.q, r, t0);
             }
         }
-        // every line has read u and v^S: the u slots now accumulate R, direction by
-        // direction in the fixed order x, y, z (deterministic sums)
+        // every line has read u, the traces and v^S: the work area now takes the three
+        // directions' contributions R_d[v][pt], which are added in the fixed order x, y, z
+        // (deterministic sums) while R is written
         __syncthreads();
-#pragma unroll 1
-        for (int dd = 0; dd < DIM; ++dd) {
-            if (live && id.d == dd) {
+        if (live) {
+            real* rd = tro + id.d * NV * NP;
 #pragma unroll
-                for (int v = 0; v < NV; ++v)
+            for (int v = 0; v < NV; ++v)
 #pragma unroll
-                    for (int i = 0; i < N; ++i) {
-                        int pt;
-                        if (dd == 0) pt = lpt<N, 0>(i, id.q);
-                        else if (dd == 1) pt = lpt<N, (DIM == 3 ? 1 : 0)>(i, id.q);
-                        else pt = lpt<N, (DIM == 3 ? 2 : 0)>(i, id.q);
-                        real* dst = su + v * ST::US + pt;
-                        *dst = (dd == 0) ? r[v][i] : *dst + r[v][i];
-                    }
+                for (int i = 0; i < N; ++i) {
+                    int pt;
+                    if (id.d == 0) pt = lpt<N, 0>(i, id.q);
+                    else if (id.d == 1) pt = lpt<N, (DIM == 3 ? 1 : 0)>(i, id.q);
+                    else pt = lpt<N, (DIM == 3 ? 2 : 0)>(i, id.q);
+                    rd[v * NP + pt] = r[v][i];
+                }
+        }
+        pipe_tail<LL, PL, true>(g, grp, ngroups, b, nbr0, nbr1);
+        __syncthreads();
+        for (int k = threadIdx.x; k < nloc * NV * NP; k += blockDim.x) {
+            const int eb = k / (NV * NP);
+            const int rr = k - eb * NV * NP;
+            const int v = rr / NP, pt = rr - v * NP;
+            const real* rd = work + eb * WPE + v * NP + pt;
+            real acc = rd[0];
+            if constexpr (DIM == 3) {
+                acc = acc + rd[NV * NP];
+                acc = acc + rd[2 * NV * NP];
             }
-            __syncthreads();
+            R[(size_t)v * g.nelem * NP + (size_t)(e0 + eb) * NP + pt] = acc;
         }
-        // R of the group: per variable one contiguous run in both R and the copy
-        const int span = nloc * NP;
-#pragma unroll
-        for (int v = 0; v < NV; ++v) {
-            real* dst = R + (size_t)v * g.nelem * NP + (size_t)e0 * NP;
-            const real* src = buf + v * EB * NP;
-            for (int j = threadIdx.x; j < span; j += blockDim.x) dst[j] = src[j];
-        }
-        __syncthreads();
     }
 }
 

@@ -23,36 +23,11 @@ eigenvalue must be -theta^2 (decay)."""
 import numpy as np
 import pytest
 
+from bloch_sec3 import bloch_Q, bloch_Q_ip
 from oracle.grid import Grid
 from oracle.operators import operators
 from oracle.physics import Heat
 from oracle.residual import residual
-
-
-def bloch_Q_ip(n, theta, tau):
-    """Q_IP of Sec. 3: tau (cL cL^T - cL cR^T e^{-i theta}) L + tau (cR cL^T e^{i theta} - cR cR^T) L."""
-    o = operators(n)
-    L, cL, cR = o.L, o.cL[:, None], o.cR[:, None]
-    ep, em = np.exp(1j * theta), np.exp(-1j * theta)
-    return tau * (cL @ cL.T - cL @ cR.T * em) @ L + tau * (cR @ cL.T * ep - cR @ cR.T) @ L
-
-
-def bloch_Q(n, theta, scheme, Jinv=1.0):
-    o = operators(n)
-    L, M, cL, cR = o.L, o.M, o.cL[:, None], o.cR[:, None]
-    ep, em = np.exp(1j * theta), np.exp(-1j * theta)
-    H = L + 0.5 * cL @ cR.T @ L * em - 0.5 * cL @ cL.T @ L + 0.5 * cR @ cL.T @ L * ep \
-        - 0.5 * cR @ cR.T @ L
-    if scheme == "compact":
-        WL = Jinv * M @ (H - 0.5 * cR @ cL.T @ L * ep + 0.5 * cR @ cR.T @ L)
-        WR = Jinv * M @ (H - 0.5 * cL @ cR.T @ L * em + 0.5 * cL @ cL.T @ L)
-    else:
-        WL = WR = Jinv * M @ H
-    base = L @ (Jinv * M @ H)
-    Q = base - cL @ cL.T @ base - cR @ cR.T @ base \
-        + 0.5 * cL @ cR.T @ L @ WR * em + 0.5 * cL @ cL.T @ L @ WL \
-        + 0.5 * cR @ cL.T @ L @ WL * ep + 0.5 * cR @ cR.T @ L @ WR
-    return Q
 
 
 @pytest.mark.parametrize("scheme", ["compact", "br1"])
