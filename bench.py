@@ -76,8 +76,8 @@ def residual_flops_per_element(n, nv=5, ng=9, dim=3):
 # DRAM traffic of one k_line_flux launch at 48^3 p=4 (FP32, compact), from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum; profiles/dram_residual_kernels_tgv48_p4_f32.md),
 # valid only while the kernel sources hash to the value recorded with it.
-FLUX_TRAFFIC = {"ne": 48, "bytes": 776636928 + 253750016,
-                "sources_sha256": "8ade5a60f41aedcb50b5ebfd26e47aad903b9128fc7e84b48e3c79480a3c2ad5"}
+FLUX_TRAFFIC = {"ne": 48, "bytes": 792248320 + 251945472,
+                "sources_sha256": "e9b15ed8dd8c1b86a304e8edbaf22ef401d6910cd7dd89a34ebdb93072960ca8"}
 FLUX_SOURCES = ("paper_2608_09615_b300/csrc/sd_line.cuh", "paper_2608_09615_b300/csrc/sd_kernels.cuh")
 
 
