@@ -67,8 +67,20 @@ typedef struct {
  *           sutherland != 0: mu = mu0 (e/e0)^(3/2) (1 + suth_s)/(e/e0 + suth_s),
  *           suth_s = S/T0 (0.368 for S = 110.4 K, T0 = 300 K); otherwise mu = mu0.
  *           Interfaces: Roe (Harten fix on the acoustic waves, delta = harten * c_Roe)
- *           or Rusanov, minus the viscous flux of the averaged state and gradient.
- *  All kinds: eta_ip >= 0 adds the interior-penalty term to the interface gradient. */
+ *           or Rusanov, minus the interface viscous flux.
+ *  All kinds: eta_ip >= 0 adds the interior-penalty term to the interface gradient.
+ *  Interface viscous (diffusive) flux, Sec. 2.1 step 4: viscous_flux = SD_VISC_STATE_AVG
+ *  (option (a), the flux of the averaged state and averaged gradient; the paper's choice)
+ *  or SD_VISC_FLUX_AVG (option (b), the average of the two sides' fluxes, each from its
+ *  own trace and own interface gradient; the penalty term is added to both sides'
+ *  normal gradients). */
+typedef enum { SD_VISC_STATE_AVG = 0, SD_VISC_FLUX_AVG = 1 } sd_viscous_flux;
+/* Porous medium diffusivity m |u|^(m-1) (Sec. 4.3): SD_PME_COEF_FLUX evaluates it at the
+ * flux points from the extrapolated solution (the paper's results); SD_PME_COEF_SOLUTION
+ * evaluates it at the solution points and extrapolates it like any field (the variant the
+ * paper mentions); at an interface option (a) uses the average of the two sides'
+ * extrapolated values, option (b) each side's own. Ignored for the other kinds. */
+typedef enum { SD_PME_COEF_FLUX = 0, SD_PME_COEF_SOLUTION = 1 } sd_pme_coef;
 typedef struct {
     sd_physics_kind kind;
     double nu;
@@ -80,6 +92,8 @@ typedef struct {
     double harten;
     double eta_ip;      /* interior penalty (Sec. 3): the interface average of the normal
                            gradient gains eta_ip (p+1)^2 / h_d (u_R - u_L); 0 = off */
+    sd_viscous_flux viscous_flux;
+    sd_pme_coef pme_coef;
 } sd_physics;
 
 /* Volume diagnostics (Sec. 4.4), FP64, Gauss quadrature over every element.

@@ -40,21 +40,39 @@ class Heat:
         # Sec. 2.1 step 4, option (a): G(u_hat, v_hat)
         return self.flux(uhat, vhat, m)
 
+    def interface_flux_b(self, uL, uR, vL, vR, m):
+        # Sec. 2.1 step 4, option (b): (G(u_L, v_L) + G(u_R, v_R)) / 2
+        return 0.5 * (self.flux(uL, vL, m) + self.flux(uR, vR, m))
+
 
 class PorousMedium:
-    """u_t = lap(u^m) = div(m u^(m-1) grad u) (Eq. pme)."""
+    """u_t = lap(u^m) = div(m u^(m-1) grad u) (Eq. pme).
+
+    coef: where the nonlinear diffusivity m |u|^(m-1) is evaluated (Sec. 4.3): "flux" at
+    the flux points from the extrapolated solution (the paper's results), "solution" at
+    the solution points and then extrapolated to the flux points like any other field
+    (the variant the paper mentions; the residual handles it, see oracle/residual.py)."""
 
     nvar = 1
     kind = "pme"
 
-    def __init__(self, m=2.0):
+    def __init__(self, m=2.0, coef="flux"):
+        if coef not in ("flux", "solution"):
+            raise ValueError(coef)
         self.m = float(m)
+        self.coef_at_solution_points = coef == "solution"
+
+    def coef(self, u):
+        return self.m * np.abs(u) ** (self.m - 1.0)
 
     def flux(self, u, grad, m):
-        return -self.m * np.abs(u) ** (self.m - 1.0) * grad[m]
+        return -self.coef(u) * grad[m]
 
     def interface_flux(self, uL, uR, uhat, vhat, m):
         return self.flux(uhat, vhat, m)
+
+    def interface_flux_b(self, uL, uR, vL, vR, m):
+        return 0.5 * (self.flux(uL, vL, m) + self.flux(uR, vR, m))
 
 
 @dataclass
@@ -210,6 +228,11 @@ class NavierStokes:
         # Sec. 4.4: Roe (or Rusanov) inviscid flux minus the centred viscous flux
         # evaluated on the average solution and the average gradient.
         return self.riemann(uL, uR, m) - self.viscous_flux(uhat, vhat, m)
+
+    def interface_flux_b(self, uL, uR, vL, vR, m):
+        # Sec. 2.1 step 4, option (b) for the viscous part: the average of the two
+        # sides' viscous fluxes, each from its own trace and own interface gradient
+        return self.riemann(uL, uR, m) - 0.5 * (self.viscous_flux(uL, vL, m) + self.viscous_flux(uR, vR, m))
 
 
 def make_physics(kind, **kw):

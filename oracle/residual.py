@@ -36,7 +36,7 @@ def along(A, X, axis):
     return np.moveaxis(Y, 0, axis)
 
 
-def residual(U, grid: Grid, scheme, phys, return_parts=False, tau=None, eta_ip=0.0):
+def residual(U, grid: Grid, scheme, phys, return_parts=False, tau=None, eta_ip=0.0, viscous="a"):
     """du/dt at the solution points.
 
     U: array of shape grid.shape(phys.nvar), any float/complex dtype (promoted to
@@ -49,9 +49,15 @@ def residual(U, grid: Grid, scheme, phys, return_parts=False, tau=None, eta_ip=0
        the d-component of the gradient on a face normal to d gains tau_IP (u_R - u_L),
        tau_IP = eta_ip (p+1)^2 / h_d (the element size; the paper's 1/h = |S| / J with the
        integrated surface and Jacobian gives 1/h_d on Cartesian grids).
+    viscous: the interface viscous flux of Sec. 2.1 step 4: "a" = G(u_hat, v_hat) with the
+       averaged state and gradient; "b" = (G(u_L, v_L) + G(u_R, v_R)) / 2, each side's trace
+       and own interface gradient (the interior penalty term, when on, is added to both
+       sides' normal gradients).
     """
     if scheme not in ("br1", "compact"):
         raise ValueError(scheme)
+    if viscous not in ("a", "b"):
+        raise ValueError(viscous)
     U = np.asarray(U)
     if np.iscomplexobj(U):
         U = U.astype(np.complex128)
@@ -142,16 +148,27 @@ def residual(U, grid: Grid, scheme, phys, return_parts=False, tau=None, eta_ip=0
     # continuous auxiliary variable at the flux points of each family.
     vFC = []
     vhatL_all, vhatR_all = [], []
+    # option (b): the two sides' own interface gradients (with the penalty term) at the
+    # left interface (sideL_*: element e-1, sideR_*: element e) and at the right one
+    sideL_l, sideR_l, sideL_r, sideR_r = [], [], [], []
     for d in range(dim):
         ea, pa = grid.elem_axis(d), grid.pt_axis(d)
         row, vl_row, vr_row = [], [], []
+        sl_l, sr_l, sl_r, sr_r = [], [], [], []
         for m in range(dim):
             vl = 0.5 * (np.roll(faceR[d][m], 1, axis=ea) + faceL[d][m])
             vr = 0.5 * (faceR[d][m] + np.roll(faceL[d][m], -1, axis=ea))
+            pen_l = pen_r = 0.0
             if eta_ip and m == d:
                 tip = eta_ip * (grid.n ** 2) / grid.h[d]
-                vl = vl + tip * (traceL[d] - np.roll(traceR[d], 1, axis=ea))
-                vr = vr + tip * (np.roll(traceL[d], -1, axis=ea) - traceR[d])
+                pen_l = tip * (traceL[d] - np.roll(traceR[d], 1, axis=ea))
+                pen_r = tip * (np.roll(traceL[d], -1, axis=ea) - traceR[d])
+                vl = vl + pen_l
+                vr = vr + pen_r
+            sl_l.append(np.roll(faceR[d][m], 1, axis=ea) + pen_l)
+            sr_l.append(faceL[d][m] + pen_l)
+            sl_r.append(faceR[d][m] + pen_r)
+            sr_r.append(np.roll(faceL[d][m], -1, axis=ea) + pen_r)
             a = vF[d][m].copy()
             a[_ix(nd, pa, 0)] += vl
             a[_ix(nd, pa, n)] += vr
@@ -161,10 +178,21 @@ def residual(U, grid: Grid, scheme, phys, return_parts=False, tau=None, eta_ip=0
         vFC.append(row)
         vhatL_all.append(vl_row)
         vhatR_all.append(vr_row)
+        sideL_l.append(sl_l)
+        sideR_l.append(sr_l)
+        sideL_r.append(sl_r)
+        sideR_r.append(sr_r)
 
     # Fluxes at all flux points (Eq. above c:aux:v:2d's use: G^{Fd,C} = [S . F]^{Fd}).
     # Interior flux points use the physical flux; interface points use the common
     # flux of the physics (for NS: Riemann solver minus the centred viscous flux).
+    # nonlinear diffusivity evaluated at the solution points and extrapolated (PME
+    # variant of Sec. 4.3): a^{Fd} = L_d a^S, two-valued at interfaces like any trace
+    aF = None
+    if getattr(phys, "coef_at_solution_points", False):
+        aS = phys.coef(U)
+        aF = [along(L, aS, grid.pt_axis(d)) for d in range(dim)]
+
     G = []
     for d in range(dim):
         ea, pa = grid.elem_axis(d), grid.pt_axis(d)
@@ -172,16 +200,36 @@ def residual(U, grid: Grid, scheme, phys, return_parts=False, tau=None, eta_ip=0
         for m in range(dim):
             if S[d, m] == 0.0:
                 continue
-            Fm = phys.flux(uFC[d], vFC[d], m)
+            if aF is not None:
+                Fm = -aF[d] * vFC[d][m]
+            else:
+                Fm = phys.flux(uFC[d], vFC[d], m)
             # left interface of each element: left state = neighbour's right trace
             vl = [vhatL_all[d][k] for k in range(dim)]
             vr = [vhatR_all[d][k] for k in range(dim)]
             if dim < 3 and phys.nvar == 5:
                 raise ValueError("Navier-Stokes needs dim = 3")
-            FL = phys.interface_flux(np.roll(traceR[d], 1, axis=ea), traceL[d],
-                                     uhatL[d], vl, m)
-            FR = phys.interface_flux(traceR[d], np.roll(traceL[d], -1, axis=ea),
-                                     uhatR[d], vr, m)
+            if aF is not None:
+                # the two sides' extrapolated diffusivities at each interface
+                atl = aF[d][_ix(nd, pa, 0)]                   # a_e(-1)
+                atr = aF[d][_ix(nd, pa, n)]                   # a_e(+1)
+                aln, arn = np.roll(atr, 1, axis=ea), np.roll(atl, -1, axis=ea)
+                if viscous == "a":
+                    FL = -0.5 * (aln + atl) * vl[m]
+                    FR = -0.5 * (atr + arn) * vr[m]
+                else:
+                    FL = -0.5 * (aln * sideL_l[d][m] + atl * sideR_l[d][m])
+                    FR = -0.5 * (atr * sideL_r[d][m] + arn * sideR_r[d][m])
+            elif viscous == "a":
+                FL = phys.interface_flux(np.roll(traceR[d], 1, axis=ea), traceL[d],
+                                         uhatL[d], vl, m)
+                FR = phys.interface_flux(traceR[d], np.roll(traceL[d], -1, axis=ea),
+                                         uhatR[d], vr, m)
+            else:
+                FL = phys.interface_flux_b(np.roll(traceR[d], 1, axis=ea), traceL[d],
+                                           sideL_l[d], sideR_l[d], m)
+                FR = phys.interface_flux_b(traceR[d], np.roll(traceL[d], -1, axis=ea),
+                                           sideL_r[d], sideR_r[d], m)
             Fm[_ix(nd, pa, 0)] = FL
             Fm[_ix(nd, pa, n)] = FR
             if tau is not None:

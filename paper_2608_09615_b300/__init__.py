@@ -22,6 +22,8 @@ SD_OK, SD_EINVAL, SD_ENOMEM, SD_ECUDA, SD_EUNSUPPORTED, SD_ENONFINITE, SD_ETIMEO
 SCHEMES = {"br1": 0, "compact": 1}
 KINDS = {"heat": 0, "pme": 1, "ns": 2}
 RIEMANN = {"roe": 0, "rusanov": 1}
+VISCOUS_FLUX = {"a": 0, "b": 1}
+PME_COEF = {"flux": 0, "solution": 1}
 PRECISIONS = {"f64": 0, "f32": 1}
 RK = {"rk4": 0, "ssprk54": 1, "lsrk54": 2}
 
@@ -42,7 +44,8 @@ class _Physics(ctypes.Structure):
                 ("gamma", ctypes.c_double), ("Pr", ctypes.c_double), ("Re", ctypes.c_double),
                 ("Ma", ctypes.c_double), ("rho0", ctypes.c_double), ("u0", ctypes.c_double),
                 ("L", ctypes.c_double), ("sutherland", ctypes.c_int), ("suth_s", ctypes.c_double),
-                ("riemann", ctypes.c_int), ("harten", ctypes.c_double), ("eta_ip", ctypes.c_double)]
+                ("riemann", ctypes.c_int), ("harten", ctypes.c_double), ("eta_ip", ctypes.c_double),
+                ("viscous_flux", ctypes.c_int), ("pme_coef", ctypes.c_int)]
 
 
 class _Diag(ctypes.Structure):
@@ -167,11 +170,14 @@ class Physics:
     riemann: str = "roe"
     harten: float = 0.1
     eta_ip: float = 0.0
+    viscous_flux: str = "a"         # interface viscous flux, Sec. 2.1 step 4: option "a" or "b"
+    pme_coef: str = "flux"          # porous-medium diffusivity at the "flux" or "solution" points
 
     def to_c(self):
         return _Physics(KINDS[self.kind], self.nu, self.m_pme, self.gamma, self.Pr, self.Re,
                         self.Ma, self.rho0, self.u0, self.L, int(bool(self.sutherland)),
-                        self.suth_s, RIEMANN[self.riemann], self.harten, self.eta_ip)
+                        self.suth_s, RIEMANN[self.riemann], self.harten, self.eta_ip,
+                        VISCOUS_FLUX[self.viscous_flux], PME_COEF[self.pme_coef])
 
 
 def _stream_handle(stream):

@@ -296,6 +296,14 @@ extern "C" sd_status sd_init(const sd_mesh* mesh, int p, sd_scheme scheme, const
     }
     if (phys->kind == SD_PME && !(phys->m_pme >= 1.0)) { sdi_set_error("m_pme must be >= 1"); return SD_EINVAL; }
     if (!(phys->eta_ip >= 0.0)) { sdi_set_error("eta_ip must be >= 0"); return SD_EINVAL; }
+    if (phys->viscous_flux != SD_VISC_STATE_AVG && phys->viscous_flux != SD_VISC_FLUX_AVG) {
+        sdi_set_error("bad viscous_flux");
+        return SD_EINVAL;
+    }
+    if (phys->pme_coef != SD_PME_COEF_FLUX && phys->pme_coef != SD_PME_COEF_SOLUTION) {
+        sdi_set_error("bad pme_coef");
+        return SD_EINVAL;
+    }
     long long nelem = 1;
     for (int d = 0; d < mesh->dim; ++d) {
         if (mesh->ne[d] < 1) { sdi_set_error("ne[%d] must be >= 1", d); return SD_EINVAL; }
@@ -329,7 +337,9 @@ extern "C" sd_status sd_init(const sd_mesh* mesh, int p, sd_scheme scheme, const
     c->npts = (size_t)c->nelem * np;
     c->nstate = c->npts * c->nvar;
     // face blocks padded to a multiple of 4 values (16-byte aligned, copied in 16-byte pieces)
-    const size_t fst = ((size_t)c->nvar * nq + 3) / 4 * 4, gst = ((size_t)c->ngrad * nq + 3) / 4 * 4;
+    // (scalar trace blocks also hold the traces of the porous-medium diffusivity)
+    const size_t fst = ((size_t)c->nvar * nq + (c->nvar == 1 ? nq : 0) + 3) / 4 * 4;
+    const size_t gst = ((size_t)c->ngrad * nq + 3) / 4 * 4;
     c->ntu = (size_t)c->nelem * 2 * c->dim * fst;
     c->ntg = (size_t)c->nelem * 2 * c->dim * gst;
     c->nfh = (size_t)c->nelem * c->dim * fst;

@@ -42,6 +42,8 @@ struct Phys {
     int kind;                // 0 heat, 1 porous medium, 2 Navier-Stokes
     int sutherland;
     int riemann;             // 0 Roe, 1 Rusanov
+    int vflux;               // interface viscous flux: 0 option (a), 1 option (b) (Sec. 2.1)
+    int pme_sol;             // porous medium diffusivity at the solution points (Sec. 4.3 variant)
     real nu, m_pme;
     real gamma, gm1, gamma_Pr, mu0, p0, rhoE0, inv_e0, suth_s, suth_1ps, harten;
     real rho0, H0;           // reference offsets: rho0, rhoE0 + p0
@@ -240,11 +242,16 @@ __device__ __forceinline__ void ns_riemann(const real* UL, const real* UR, int d
     F[4] -= w1 * (Ht - qn * c) + w2 * real(0.5) * q2 + w5 * (Ht + qn * c) + ws * utdvt;
 }
 
-// scalar diffusion flux (heat: -nu v_d; PME: -m |u|^(m-1) v_d, Eq. pme)
+// scalar diffusivity (heat: nu; PME: m |u|^(m-1), Eq. pme) and flux -coef v_d
+template <typename real>
+__device__ __forceinline__ real scalar_coef(const Phys<real>& P, real u) {
+    if (P.kind == 1) return P.m_pme * pow(fabs(u), P.m_pme - real(1));
+    return P.nu;
+}
+
 template <typename real>
 __device__ __forceinline__ real scalar_flux(const Phys<real>& P, real u, real g) {
-    if (P.kind == 1) return -P.m_pme * pow(fabs(u), P.m_pme - real(1)) * g;
-    return -P.nu * g;
+    return -scalar_coef(P, u) * g;
 }
 
 // ------------------------------------------------------------------ element staging

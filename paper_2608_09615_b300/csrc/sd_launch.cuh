@@ -33,6 +33,8 @@ static Phys<real> make_phys(const sd_ctx* c) {
     P.kind = (int)s.kind;
     P.sutherland = s.sutherland ? 1 : 0;
     P.riemann = (int)s.riemann;
+    P.vflux = (int)s.viscous_flux;
+    P.pme_sol = (s.kind == SD_PME && s.pme_coef == SD_PME_COEF_SOLUTION) ? 1 : 0;
     P.nu = (real)s.nu;
     P.m_pme = (real)s.m_pme;
     const double gamma = s.gamma;
@@ -242,7 +244,7 @@ static sd_status residual_impl(sd_ctx* c, const real* U, real* R, int offset_in)
                                    c->device);
     real* Fh = static_cast<real*>(c->Fh);
     sdi_prof_begin(c, SD_K_TRACE);
-    k_line_trace<real, N, DIM, NV><<<bt, LL::THREADS, st, c->stream>>>(U, Tu, geo, g);
+    k_line_trace<real, N, DIM, NV><<<bt, LL::THREADS, st, c->stream>>>(U, Tu, geo, g, P);
     sdi_prof_end(c, SD_K_TRACE);
     if (c->closure_on && NV == 5) {
         const sd_status cs = closure_stage<real, N>(c, U, offset_in);
@@ -304,7 +306,7 @@ static sd_status closure_data_dispatch(sd_ctx* c, const real* U, float* X, doubl
         const int btr = persistent_grid(k_line_trace<real, NN, 3, 5>, LL::THREADS, stb,          \
                                         (g.nelem + LL::EB - 1) / LL::EB, c->device);            \
         k_line_trace<real, NN, 3, 5><<<btr, LL::THREADS, stb, c->stream>>>(                      \
-            U, static_cast<real*>(c->Tu), geo, g);                                               \
+            U, static_cast<real*>(c->Tu), geo, g, make_phys<real>(c));                           \
         if (X) st = features_impl<real, NN>(c, U, X, offset_in);                                 \
         if (st == SD_OK && means) st = fluxmean_impl<real, NN>(c, U, means, offset_in);          \
         return st;                                                                               \

@@ -88,9 +88,10 @@ struct LineLayout {
     static constexpr int THREADS = UPB * UNIT;
     static constexpr int EB = UPB * EPW;                          // elements per block
     // Global scratch layouts: Tu[e][f][FST] and Fh[d][e][FST] hold [v][q] in the first NV*NQ
-    // values of each block, Tg[e][f][GST] holds [c][q]; blocks are padded to a multiple of
+    // values of each block (scalars: then the diffusivity traces [q], see FST), Tg[e][f][GST] holds [c][q]; blocks are padded to a multiple of
     // 4 values so that each starts on a 16-byte boundary and is copied in 16-byte pieces.
-    static constexpr int FST = round4(NV * NQ);
+    // (scalar blocks also hold the face traces of the porous-medium diffusivity at [NQ, 2 NQ))
+    static constexpr int FST = round4(NV * NQ + (NV == 1 ? NQ : 0));
     static constexpr int GST = round4(NG * NQ);
     // per-element sizes of the contiguous element staging of the closure kernels
     static constexpr int S_U = NV * NP;
@@ -418,6 +419,18 @@ __device__ __forceinline__ void line_traces(const real* su, int q, real* outL, r
     }
 }
 
+// face traces of the porous-medium diffusivity m |u|^(m-1) evaluated at the solution
+// points of line q (Sec. 4.3 variant), for the interface flux
+template <typename real, int N, int D, class ST>
+__device__ __forceinline__ void coef_traces(const Phys<real>& P, const real* su, int q, real* outL, real* outR) {
+    const OpTab<real, N>& op = c_op<real, N>;
+    real a[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) a[i] = scalar_coef(P, su[lpt<N, D>(i, q)]);
+    *outL = dotc<real, N>(op.L, a);
+    *outR = dotc<real, N>(op.L + N * N, a);
+}
+
 // v^S along D for every variable of line q (Eq. w:e in Cartesian form):
 // v_D = (2/h_D) (D u + M[:,0] delta_L + M[:,N] delta_R)
 template <typename real, int N, int DIM, int NV, int D, class ST>
@@ -609,7 +622,7 @@ __device__ __forceinline__ void grad_faces_res(const LineGeo<real>& geo, int com
 // ---------------------------------------------------------------- kernels
 template <typename real, int N, int DIM, int NV>
 __global__ void __launch_bounds__(LineLayout<N, DIM, NV>::THREADS)
-k_line_trace(const real* __restrict__ U, real* __restrict__ Tu, LineGeo<real> geo, Mesh g) {
+k_line_trace(const real* __restrict__ U, real* __restrict__ Tu, LineGeo<real> geo, Mesh g, Phys<real> P) {
     using LL = LineLayout<N, DIM, NV>;
     using PL = TracePipe<real, LL>;
     using ST = ResStrides<LL>;
@@ -635,6 +648,16 @@ k_line_trace(const real* __restrict__ U, real* __restrict__ Tu, LineGeo<real> ge
             if constexpr (DIM == 3) {
                 if (id.d == 1) line_traces<real, N, NQ, NV, 1, ST>(su, id.q, out + 2 * FST, out + 3 * FST, NQ);
                 if (id.d == 2) line_traces<real, N, NQ, NV, 2, ST>(su, id.q, out + 4 * FST, out + 5 * FST, NQ);
+            }
+            if constexpr (NV == 1) {
+                if (P.pme_sol) {
+                    real* o = out + NQ;
+                    if (id.d == 0) coef_traces<real, N, 0, ST>(P, su, id.q, o, o + FST);
+                    if constexpr (DIM == 3) {
+                        if (id.d == 1) coef_traces<real, N, 1, ST>(P, su, id.q, o + 2 * FST, o + 3 * FST);
+                        if (id.d == 2) coef_traces<real, N, 2, ST>(P, su, id.q, o + 4 * FST, o + 5 * FST);
+                    }
+                }
             }
         }
         __syncthreads();
@@ -692,19 +715,62 @@ k_line_grad(const real* __restrict__ U, const real* __restrict__ Tu, real* __res
 template <typename real, int NV, int NG, int D>
 __device__ __forceinline__ void interface_flux(const LineGeo<real>& geo, const Phys<real>& P, const real* UL,
                                                const real* UR, const real* gL, const real* gR,
-                                               const float* tauL, const float* tauR, real* F) {
-    real Uh[NV], vh[NG];
-#pragma unroll
-    for (int v = 0; v < NV; ++v) Uh[v] = real(0.5) * (UL[v] + UR[v]);
-#pragma unroll
-    for (int c = 0; c < NG; ++c) {
-        vh[c] = real(0.5) * (gL[c] + gR[c]);
-        // interior penalty on the normal derivative: tau_IP (u_R - u_L)
-        if (c < NV && geo.tip[D] != real(0)) vh[c] = fma(geo.tip[D], UR[c] - UL[c], vh[c]);
+                                               const float* tauL, const float* tauR, real* F, real aL = real(0),
+                                               real aR = real(0)) {
+    if constexpr (NV == 1) {
+        // scalar: -c v with the diffusivity c of the averaged state (option (a)) or of each
+        // side (option (b)); with the diffusivity taken at the solution points, aL and aR
+        // are the two sides' extrapolated values
+        real g = real(0.5) * (gL[0] + gR[0]);
+        real a = gL[0], b = gR[0];
+        if (geo.tip[D] != real(0)) {
+            g = fma(geo.tip[D], UR[0] - UL[0], g);
+            a = fma(geo.tip[D], UR[0] - UL[0], a);
+            b = fma(geo.tip[D], UR[0] - UL[0], b);
+        }
+        const bool sol = P.kind == 1 && P.pme_sol;
+        if (P.vflux == 0) {
+            const real c = sol ? real(0.5) * (aL + aR) : scalar_coef(P, real(0.5) * (UL[0] + UR[0]));
+            F[0] = -c * g;
+        } else {
+            const real cl = sol ? aL : scalar_coef(P, UL[0]);
+            const real cr = sol ? aR : scalar_coef(P, UR[0]);
+            F[0] = real(0.5) * (-cl * a + -cr * b);
+        }
+        return;
     }
-    if constexpr (NV == 5) {
-        real Fv[NV];
+    real Fv[NV];
+    if (P.vflux == 0) {
+        // option (a): the flux of the averaged state and the averaged gradient
+        real Uh[NV], vh[NG];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) Uh[v] = real(0.5) * (UL[v] + UR[v]);
+#pragma unroll
+        for (int c = 0; c < NG; ++c) {
+            vh[c] = real(0.5) * (gL[c] + gR[c]);
+            // interior penalty on the normal derivative: tau_IP (u_R - u_L)
+            if (c < NV && geo.tip[D] != real(0)) vh[c] = fma(geo.tip[D], UR[c] - UL[c], vh[c]);
+        }
         ns_viscous(Uh, vh, D, P, Fv);
+    } else {
+        // option (b): the average of the two sides' fluxes, each from its own trace and
+        // interface gradient (the penalty term on both sides' normal derivatives)
+        real a[NG], b[NG], FL[NV], FR[NV];
+#pragma unroll
+        for (int c = 0; c < NG; ++c) {
+            a[c] = gL[c];
+            b[c] = gR[c];
+            if (c < NV && geo.tip[D] != real(0)) {
+                a[c] = fma(geo.tip[D], UR[c] - UL[c], a[c]);
+                b[c] = fma(geo.tip[D], UR[c] - UL[c], b[c]);
+            }
+        }
+        ns_viscous(UL, a, D, P, FL);
+        ns_viscous(UR, b, D, P, FR);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) Fv[v] = real(0.5) * (FL[v] + FR[v]);
+    }
+    {
         ns_riemann(UL, UR, D, P, F);
         if (tauL) {
             // extra per-element flux: centred average of the two elements at the interface
@@ -713,8 +779,6 @@ __device__ __forceinline__ void interface_flux(const LineGeo<real>& geo, const P
         }
 #pragma unroll
         for (int v = 0; v < NV; ++v) F[v] -= Fv[v];
-    } else {
-        F[0] = scalar_flux(P, Uh[0], vh[0]);
     }
 }
 
@@ -746,7 +810,12 @@ __device__ __forceinline__ void face_point(const real* __restrict__ Tu, const re
         tauL = tau + (size_t)e * 15;
         tauR = tau + (size_t)en * 15;
     }
-    interface_flux<real, NV, NG, D>(geo, P, UL, UR, gL, gR, tauL, tauR, F);
+    real aL = real(0), aR = real(0);
+    if (NV == 1 && P.pme_sol) {
+        aL = tl[NQ];
+        aR = tr[NQ];
+    }
+    interface_flux<real, NV, NG, D>(geo, P, UL, UR, gL, gR, tauL, tauR, F, aL, aR);
     real* out = Fh + ((size_t)D * g.nelem + e) * FST + q;
 #pragma unroll
     for (int v = 0; v < NV; ++v) out[v * NQ] = F[v];
@@ -830,7 +899,16 @@ __device__ __forceinline__ void line_flux(const LineGeo<real>& geo, const Phys<r
 #pragma unroll
             for (int v = 0; v < NV; ++v) F[v] -= Fv[v];
         } else {
-            F[0] = scalar_flux(P, uf[0], dline<real, N>(op, f, u[0], dl[0], dr[0], th));
+            const real gfn = dline<real, N>(op, f, u[0], dl[0], dr[0], th);
+            if (P.kind == 1 && P.pme_sol) {
+                // diffusivity from the solution points, extrapolated to the flux point
+                real a[N];
+#pragma unroll
+                for (int i = 0; i < N; ++i) a[i] = scalar_coef(P, u[0][i]);
+                F[0] = -dotc<real, N>(Lr, a) * gfn;
+            } else {
+                F[0] = scalar_flux(P, uf[0], gfn);
+            }
         }
 #pragma unroll
         for (int v = 0; v < NV; ++v)

@@ -347,3 +347,52 @@ def test_interior_penalty_fp64_parity(scheme, eta):
     Ro = oracle_residual(U, gg, scheme, NavierStokes(prm), eta_ip=eta).astype(np.float64)
     Rg = gpu_residual(U, 3, ne, (0.0,) * 3, (TWO_PI,) * 3, p, scheme, phys, "f64")
     assert rel_err(Rg, Ro).max() <= 1e-12
+
+
+# ------------------------------------------------------------------ interface viscous flux option (b)
+@pytest.mark.parametrize("scheme", ["br1", "compact"])
+@pytest.mark.parametrize("eta", [0.0, 0.3])
+def test_viscous_flux_option_b_fp64_parity(scheme, eta):
+    # Sec. 2.1 step 4 option (b): the average of the two sides' viscous fluxes
+    prm, phys = ns_phys(Re=200.0)
+    phys.eta_ip = eta
+    phys.viscous_flux = "b"
+    ne, p = (3, 3, 2), 3
+    U = inputs.random_state(ne, p, seed=31)
+    gg = Grid(3, ne, (0.0,) * 3, (TWO_PI,) * 3, p, dtype=np.longdouble)
+    Ro = oracle_residual(U, gg, scheme, NavierStokes(prm), eta_ip=eta, viscous="b").astype(np.float64)
+    Rg = gpu_residual(U, 3, ne, (0.0,) * 3, (TWO_PI,) * 3, p, scheme, phys, "f64")
+    assert rel_err(Rg, Ro).max() <= 1e-12
+    # porous medium, 1D
+    U1 = 1.0 + 0.3 * inputs.random_scalar(1, (11,), 4, seed=32)
+    gg = Grid(1, (11,), (0.0,), (1.0,), 4, dtype=np.longdouble)
+    Ro = oracle_residual(U1, gg, scheme, PorousMedium(2.0), eta_ip=eta, viscous="b").astype(np.float64)
+    Rg = gpu_residual(U1, 1, (11,), (0.0,), (1.0,), 4, scheme,
+                      sd.Physics(kind="pme", m_pme=2.0, eta_ip=eta, viscous_flux="b"), "f64")
+    assert rel_err(Rg, Ro).max() <= 1e-12
+
+
+@pytest.mark.parametrize("scheme", ["br1", "compact"])
+@pytest.mark.parametrize("viscous", ["a", "b"])
+@pytest.mark.parametrize("eta", [0.0, 0.3])
+def test_pme_solution_point_diffusivity_fp64_parity(scheme, viscous, eta):
+    # Sec. 4.3 variant: m |u|^(m-1) at the solution points, extrapolated
+    for m, ne, p in ((3.0, (13,), 4), (2.0, (8,), 2)):
+        U = 1.0 + 0.4 * inputs.random_scalar(1, ne, p, seed=41)
+        gg = Grid(1, ne, (0.0,), (1.0,), p, dtype=np.longdouble)
+        Ro = oracle_residual(U, gg, scheme, PorousMedium(m, coef="solution"), eta_ip=eta,
+                             viscous=viscous).astype(np.float64)
+        Rg = gpu_residual(U, 1, ne, (0.0,), (1.0,), p, scheme,
+                          sd.Physics(kind="pme", m_pme=m, eta_ip=eta, viscous_flux=viscous,
+                                     pme_coef="solution"), "f64")
+        assert rel_err(Rg, Ro).max() <= 1e-12
+    # 3D scalar grid (the layout path of 3D scalar blocks)
+    ne, p = (3, 4, 2), 3
+    U = 1.0 + 0.4 * inputs.random_scalar(3, ne, p, seed=42)
+    gg = Grid(3, ne, (0.0,) * 3, (1.0,) * 3, p, dtype=np.longdouble)
+    Ro = oracle_residual(U, gg, scheme, PorousMedium(3.0, coef="solution"), eta_ip=eta,
+                         viscous=viscous).astype(np.float64)
+    Rg = gpu_residual(U, 3, ne, (0.0,) * 3, (1.0,) * 3, p, scheme,
+                      sd.Physics(kind="pme", m_pme=3.0, eta_ip=eta, viscous_flux=viscous, pme_coef="solution"),
+                      "f64")
+    assert rel_err(Rg, Ro).max() <= 1e-12
