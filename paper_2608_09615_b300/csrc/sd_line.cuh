@@ -275,16 +275,16 @@ struct Pipe {
 template <typename real, class LL>
 using TracePipe = Pipe<LL, false, false, real, 0>;
 template <typename real, class LL>
-using GradPipe = Pipe<LL, true, false, real, LL::NF * LL::FST + LL::S_VR>;
+using GradPipe = Pipe<LL, true, false, real, LL::S_VR>;
 template <class LL>
 struct FluxWork;
 template <typename real, class LL>
 using FluxPipe = Pipe<LL, true, true, real, FluxWork<LL>::value>;
 
-// work values per element of the flux kernel: own traces and kept v^S, later R_d
+// work values per element of the flux kernel: the kept v^S, later R_d
 template <class LL>
 struct FluxWork {
-    static constexpr int value = LL::NF * LL::FST + LL::S_VR > LL::S_RD ? LL::NF * LL::FST + LL::S_VR : LL::S_RD;
+    static constexpr int value = LL::S_VR > LL::S_RD ? LL::S_VR : LL::S_RD;
 };
 
 template <class LL>
@@ -518,91 +518,79 @@ __device__ __forceinline__ void grad_faces(const LineGeo<real>& geo, int compact
     }
 }
 
-// residual form of v^S along D: only the three components other lines need (vslot)
-template <typename real, int N, int DIM, int D, class ST>
-__device__ __forceinline__ void line_vs_res(const LineGeo<real>& geo, const real* su, const real* tro,
-                                            const real* trn, real* vS, int q) {
+// Residual kernels, per line (direction D, face point q): the line's u, its own face
+// traces and the corrections delta stay in registers; the only shared-memory results are
+// the kept v^S components, which the lines of the other directions read after a barrier.
+//
+// line_load: u of every variable, the own traces (L_0 u, L_n u, the same fma sequence as
+// k_line_trace), delta_L = (trace_nb - trace_own)/2 at face 2D, delta_R at face 2D+1
+// (Eq. c:flux), and (Navier-Stokes) v^S along D of rho and of the two momentum
+// components across D (Eq. w:e; vslot)
+template <typename real, int N, int DIM, int NV, int D, class ST>
+__device__ __forceinline__ void line_load(const LineGeo<real>& geo, const real* su, const real* trn, real* vS,
+                                          int q, real (&u)[NV][N], real (&dl)[NV], real (&dr)[NV]) {
     constexpr int NP = ipow(N, DIM), NQ = ipow(N, DIM - 1);
     const OpTab<real, N>& op = c_op<real, N>;
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        const int v = k == 0 ? 0 : 1 + (D + k) % 3;
-        real u[N];
+    for (int v = 0; v < NV; ++v) {
 #pragma unroll
-        for (int i = 0; i < N; ++i) u[i] = su[v * ST::US + lpt<N, D>(i, q)];
-        const int il = (2 * D) * ST::FS + v * NQ + q, ir = (2 * D + 1) * ST::FS + v * NQ + q;
-        const real dl = real(0.5) * (trn[il] - tro[il]);
-        const real dr = real(0.5) * (trn[ir] - tro[ir]);
+        for (int i = 0; i < N; ++i) u[v][i] = su[v * ST::US + lpt<N, D>(i, q)];
+        const real tl = dotc<real, N>(op.L, u[v]);
+        const real tr = dotc<real, N>(op.L + N * N, u[v]);
+        dl[v] = real(0.5) * (trn[(2 * D) * ST::FS + v * NQ + q] - tl);
+        dr[v] = real(0.5) * (trn[(2 * D + 1) * ST::FS + v * NQ + q] - tr);
+    }
+    if constexpr (NV == 5) {
 #pragma unroll
-        for (int i = 0; i < N; ++i) {
-            real acc = dotc<real, N>(op.D + i * N, u);
-            acc = fma(op.M[i * (N + 1)], dl, acc);
-            acc = fma(op.M[i * (N + 1) + N], dr, acc);
-            vS[vslot(v, D) * NP + lpt<N, D>(i, q)] = geo.two_h[D] * acc;
+        for (int k = 0; k < 3; ++k) {
+            const int v = k == 0 ? 0 : 1 + (D + k) % 3;
+#pragma unroll
+            for (int i = 0; i < N; ++i) {
+                real acc = dotc<real, N>(op.D + i * N, u[v]);
+                acc = fma(op.M[i * (N + 1)], dl[v], acc);
+                acc = fma(op.M[i * (N + 1) + N], dr[v], acc);
+                vS[vslot(v, D) * NP + lpt<N, D>(i, q)] = geo.two_h[D] * acc;
+            }
         }
     }
 }
 
-// prologue of the residual gradient and flux kernels: own traces, then the kept v^S
+// line_load for the warp's direction, then (Navier-Stokes) the barrier after which every
+// kept v^S component is visible
 template <typename real, int N, int DIM, int NV, class ST>
 __device__ __forceinline__ void prologue_res(const LineGeo<real>& geo, const LineId& id, bool live,
-                                             real* su, real* tro, real* trn, real* vS) {
-    constexpr int NQ = ipow(N, DIM - 1), FS = ST::FS;
+                                             const real* su, const real* trn, real* vS, real (&u)[NV][N],
+                                             real (&dl)[NV], real (&dr)[NV]) {
     if (live) {
-        real* o = tro + id.q;
-        if (id.d == 0) line_traces<real, N, NQ, NV, 0, ST>(su, id.q, o, o + FS, NQ);
+        if (id.d == 0) line_load<real, N, DIM, NV, 0, ST>(geo, su, trn, vS, id.q, u, dl, dr);
         if constexpr (DIM == 3) {
-            if (id.d == 1) line_traces<real, N, NQ, NV, 1, ST>(su, id.q, o + 2 * FS, o + 3 * FS, NQ);
-            if (id.d == 2) line_traces<real, N, NQ, NV, 2, ST>(su, id.q, o + 4 * FS, o + 5 * FS, NQ);
+            if (id.d == 1) line_load<real, N, DIM, NV, 1, ST>(geo, su, trn, vS, id.q, u, dl, dr);
+            if (id.d == 2) line_load<real, N, DIM, NV, 2, ST>(geo, su, trn, vS, id.q, u, dl, dr);
         }
     }
-    __syncthreads();
-    if constexpr (NV == 5) {
-        if (live) {
-            if (id.d == 0) line_vs_res<real, N, DIM, 0, ST>(geo, su, tro, trn, vS, id.q);
-            if (id.d == 1) line_vs_res<real, N, DIM, 1, ST>(geo, su, tro, trn, vS, id.q);
-            if (id.d == 2) line_vs_res<real, N, DIM, 2, ST>(geo, su, tro, trn, vS, id.q);
-        }
-        __syncthreads();
-    }
-}
-
-// face corrections delta_L, delta_R of every variable of line q (Eq. c:flux)
-template <typename real, int NQ, int NV, int D, class ST>
-__device__ __forceinline__ void line_deltas(const real* tro, const real* trn, int q, real* dl, real* dr) {
-#pragma unroll
-    for (int v = 0; v < NV; ++v) {
-        const int il = (2 * D) * ST::FS + v * NQ + q, ir = (2 * D + 1) * ST::FS + v * NQ + q;
-        dl[v] = real(0.5) * (trn[il] - tro[il]);
-        dr[v] = real(0.5) * (trn[ir] - tro[ir]);
-    }
+    if constexpr (NV == 5) __syncthreads();
 }
 
 // residual form of grad_faces: normal components from u and the corrections (BR1:
 // L_s v^S; compact: the one-sided gradient keeps only the correction of face s, the
 // closed form of Eqs. aux:cmp:lr:2d), transverse components from the kept v^S
-template <typename real, int N, int DIM, int NV, int D, class ST>
-__device__ __forceinline__ void grad_faces_res(const LineGeo<real>& geo, int compact, const real* su,
-                                               const real* vS, const real* tro, const real* trn, real* out,
-                                               int q) {
+template <typename real, int N, int DIM, int NV, int D>
+__device__ __forceinline__ void grad_faces_res(const LineGeo<real>& geo, int compact, const real (&u)[NV][N],
+                                               const real (&dl)[NV], const real (&dr)[NV], const real* vS,
+                                               real* out, int q) {
     using LL = LineLayout<N, DIM, NV>;
     constexpr int NP = LL::NP, NQ = LL::NQ, NG = LL::NG, GST = LL::GST;
     const OpTab<real, N>& op = c_op<real, N>;
     const real th = geo.two_h[D];
-    real dl[NV], dr[NV];
-    line_deltas<real, NQ, NV, D, ST>(tro, trn, q, dl, dr);
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
-        real u[N];
-#pragma unroll
-        for (int i = 0; i < N; ++i) u[i] = su[v * ST::US + lpt<N, D>(i, q)];
         real aL, aR;
         if (compact) {
-            aL = th * fma(op.LM0[0], dl[v], dotc<real, N>(op.LD, u));
-            aR = th * fma(op.LMN[N], dr[v], dotc<real, N>(op.LD + N * N, u));
+            aL = th * fma(op.LM0[0], dl[v], dotc<real, N>(op.LD, u[v]));
+            aR = th * fma(op.LMN[N], dr[v], dotc<real, N>(op.LD + N * N, u[v]));
         } else {
-            aL = dline<real, N>(op, 0, u, dl[v], dr[v], th);
-            aR = dline<real, N>(op, N, u, dl[v], dr[v], th);
+            aL = dline<real, N>(op, 0, u[v], dl[v], dr[v], th);
+            aR = dline<real, N>(op, N, u[v], dl[v], dr[v], th);
         }
         out[(2 * D) * GST + v * NQ + q] = aL;
         out[(2 * D + 1) * GST + v * NQ + q] = aR;
@@ -682,8 +670,7 @@ k_line_grad(const real* __restrict__ U, const real* __restrict__ Tu, real* __res
     int grp = blockIdx.x;
     if (grp >= ngroups) return;
     const LineId id = line_id<LL>(threadIdx.x);
-    real* tro = work + id.eb * (NF * LL::FST + LL::S_VR);
-    real* vS = tro + NF * LL::FST;
+    real* vS = work + id.eb * LL::S_VR;
     pipe_start<real, LL, PL, NV, true, false>(U, Tu, nullptr, g, grp, ngroups, buf0, nbr0, nbr1);
     for (int b = 0; grp < ngroups; grp += gridDim.x, b ^= 1) {
         real* buf = b ? buf1 : buf0;
@@ -692,15 +679,16 @@ k_line_grad(const real* __restrict__ U, const real* __restrict__ Tu, real* __res
                                                  geo.off0, geo.off4);
         const int e = e0 + id.eb;
         const bool live = id.ok && e < g.nelem;
-        real* su = buf + id.eb * NP;
-        real* trn = buf + PL::OFF_TR + id.eb * NF * LL::FST;
-        prologue_res<real, N, DIM, NV, ST>(geo, id, live, su, tro, trn, vS);
+        const real* su = buf + id.eb * NP;
+        const real* trn = buf + PL::OFF_TR + id.eb * NF * LL::FST;
+        real u[NV][N], dl[NV], dr[NV];
+        prologue_res<real, N, DIM, NV, ST>(geo, id, live, su, trn, vS, u, dl, dr);
         if (live) {
             real* out = Tg + (size_t)e * NF * GST;
-            if (id.d == 0) grad_faces_res<real, N, DIM, NV, 0, ST>(geo, compact, su, vS, tro, trn, out, id.q);
+            if (id.d == 0) grad_faces_res<real, N, DIM, NV, 0>(geo, compact, u, dl, dr, vS, out, id.q);
             if constexpr (DIM == 3) {
-                if (id.d == 1) grad_faces_res<real, N, DIM, NV, 1, ST>(geo, compact, su, vS, tro, trn, out, id.q);
-                if (id.d == 2) grad_faces_res<real, N, DIM, NV, 2, ST>(geo, compact, su, vS, tro, trn, out, id.q);
+                if (id.d == 1) grad_faces_res<real, N, DIM, NV, 1>(geo, compact, u, dl, dr, vS, out, id.q);
+                if (id.d == 2) grad_faces_res<real, N, DIM, NV, 2>(geo, compact, u, dl, dr, vS, out, id.q);
             }
         }
         pipe_tail<LL, PL, true>(g, grp, ngroups, b, nbr0, nbr1);
@@ -846,9 +834,9 @@ k_face_flux(const real* __restrict__ Tu, const real* __restrict__ Tg, real* __re
 // fluxes along D at the n+1 flux points of line q and their divergence on the line: the
 // interface fluxes at f = 0 and f = N come from Fh, the n-1 interior ones are evaluated here
 template <typename real, int N, int DIM, int NV, int D, class ST>
-__device__ __forceinline__ void line_flux(const LineGeo<real>& geo, const Phys<real>& P, const real* su,
-                                          const real* vS, const real* tro, const real* trn, const real* fh,
-                                          int q, real (&r)[NV][N], const float* tau_own) {
+__device__ __forceinline__ void line_flux(const LineGeo<real>& geo, const Phys<real>& P, const real (&u)[NV][N],
+                                          const real (&dl)[NV], const real (&dr)[NV], const real* vS,
+                                          const real* fh, int q, real (&r)[NV][N], const float* tau_own) {
     using LL = LineLayout<N, DIM, NV>;
     constexpr int NP = LL::NP, NQ = LL::NQ, NG = LL::NG;
     const OpTab<real, N>& op = c_op<real, N>;
@@ -863,12 +851,6 @@ __device__ __forceinline__ void line_flux(const LineGeo<real>& geo, const Phys<r
     // interior flux points: extrapolated solution and gradient (Eq. aux:v:std:2d); the
     // normal derivatives come from u and the face corrections (dline), the transverse ones
     // from the kept v^S
-    real u[NV][N], dl[NV], dr[NV];
-#pragma unroll
-    for (int v = 0; v < NV; ++v)
-#pragma unroll
-        for (int i = 0; i < N; ++i) u[v][i] = su[v * ST::US + lpt<N, D>(i, q)];
-    line_deltas<real, NQ, NV, D, ST>(tro, trn, q, dl, dr);
     const real th = geo.two_h[D];
 #pragma unroll 1
     for (int f = 1; f < N; ++f) {
@@ -943,8 +925,7 @@ k_line_flux(const real* __restrict__ U, const real* __restrict__ Tu, const real*
     if (grp >= ngroups) return;
     const LineId id = line_id<LL>(threadIdx.x);
     constexpr int WPE = FluxWork<LL>::value;                   // work values per element
-    real* tro = work + id.eb * WPE;
-    real* vS = tro + NF * LL::FST;
+    real* vS = work + id.eb * WPE;
     pipe_start<real, LL, PL, NV, true, true>(U, Tu, Fh, g, grp, ngroups, buf0, nbr0, nbr1);
     for (int b = 0; grp < ngroups; grp += gridDim.x, b ^= 1) {
         real* buf = b ? buf1 : buf0;
@@ -953,26 +934,27 @@ k_line_flux(const real* __restrict__ U, const real* __restrict__ Tu, const real*
                                                 geo.off0, geo.off4);
         const int e = e0 + id.eb;
         const bool live = id.ok && e < g.nelem;
-        real* su = buf + id.eb * NP;
-        real* trn = buf + PL::OFF_TR + id.eb * NF * LL::FST;
-        real* fh = buf + PL::OFF_FH + id.eb * NF * LL::FST;
-        prologue_res<real, N, DIM, NV, ST>(geo, id, live, su, tro, trn, vS);
+        const real* su = buf + id.eb * NP;
+        const real* trn = buf + PL::OFF_TR + id.eb * NF * LL::FST;
+        const real* fh = buf + PL::OFF_FH + id.eb * NF * LL::FST;
+        real u[NV][N], dl[NV], dr[NV];
+        prologue_res<real, N, DIM, NV, ST>(geo, id, live, su, trn, vS, u, dl, dr);
 
         real r[NV][N];
         if (live) {
             const float* t0 = (NV == 5 && tau) ? tau + (size_t)e * 15 : nullptr;
-            if (id.d == 0) line_flux<real, N, DIM, NV, 0, ST>(geo, P, su, vS, tro, trn, fh, id.q, r, t0);
+            if (id.d == 0) line_flux<real, N, DIM, NV, 0, ST>(geo, P, u, dl, dr, vS, fh, id.q, r, t0);
             if constexpr (DIM == 3) {
-                if (id.d == 1) line_flux<real, N, DIM, NV, 1, ST>(geo, P, su, vS, tro, trn, fh, id.q, r, t0);
-                if (id.d == 2) line_flux<real, N, DIM, NV, 2, ST>(geo, P, su, vS, tro, trn, fh, id.q, r, t0);
+                if (id.d == 1) line_flux<real, N, DIM, NV, 1, ST>(geo, P, u, dl, dr, vS, fh, id.q, r, t0);
+                if (id.d == 2) line_flux<real, N, DIM, NV, 2, ST>(geo, P, u, dl, dr, vS, fh, id.q, r, t0);
             }
         }
-        // every line has read u, the traces and v^S: the work area now takes the three
-        // directions' contributions R_d[v][pt], which are added in the fixed order x, y, z
+        // every line has read v^S: the work area now takes the three directions'
+        // contributions R_d[v][pt], which are added in the fixed order x, y, z
         // (deterministic sums) while R is written
         __syncthreads();
         if (live) {
-            real* rd = tro + id.d * NV * NP;
+            real* rd = vS + id.d * NV * NP;
 #pragma unroll
             for (int v = 0; v < NV; ++v)
 #pragma unroll
