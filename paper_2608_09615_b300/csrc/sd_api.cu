@@ -258,6 +258,13 @@ static void free_closure(sd_ctx* c) {
 
 static void free_all(sd_ctx* c) {
     free_closure(c);
+    if (c->s_h2d) cudaStreamDestroy(c->s_h2d);
+    if (c->s_d2h) cudaStreamDestroy(c->s_d2h);
+    if (c->ev_start) cudaEventDestroy(c->ev_start);
+    for (int k = 0; k < SDI_MAX_SLABS; ++k) {
+        if (c->ev_in[k]) cudaEventDestroy(c->ev_in[k]);
+        if (c->ev_out[k]) cudaEventDestroy(c->ev_out[k]);
+    }
     if (c->cl_tmode) cudaFree(c->cl_tmode);
     void* ptrs[] = {c->Tu, c->Tg, c->Fh, c->S, c->K, c->rA, c->rB, c->rC, c->rX, c->dW,
                     c->partial, c->dsum, c->hU, c->hR};
@@ -391,6 +398,15 @@ extern "C" sd_status sd_init(const sd_mesh* mesh, int p, sd_scheme scheme, const
     alloc((void**)&c->dsum, sdk::NDIAG * sizeof(double));
     alloc(&c->hU, S * c->esize);
     alloc(&c->hR, S * c->esize);
+    if (ok && c->dim == 3) {
+        // streams and events of the slab-pipelined host-buffer residual
+        ok = cudaStreamCreateWithFlags(&c->s_h2d, cudaStreamNonBlocking) == cudaSuccess &&
+             cudaStreamCreateWithFlags(&c->s_d2h, cudaStreamNonBlocking) == cudaSuccess &&
+             cudaEventCreateWithFlags(&c->ev_start, cudaEventDisableTiming) == cudaSuccess;
+        for (int k = 0; ok && k < SDI_MAX_SLABS; ++k)
+            ok = cudaEventCreateWithFlags(&c->ev_in[k], cudaEventDisableTiming) == cudaSuccess &&
+                 cudaEventCreateWithFlags(&c->ev_out[k], cudaEventDisableTiming) == cudaSuccess;
+    }
     if (!ok) {
         cudaGetLastError();
         sdi_set_error("device allocation of the context scratch failed");
@@ -483,8 +499,84 @@ extern "C" sd_status sd_residual(sd_ctx* c, const void* U, void* R) {
     return residual_any(c, U, R);
 }
 
+static sd_status residual_phase_any(sd_ctx* c, int phase, int e0, int e1) {
+    if (c->prec == SD_F32)
+        return sdi_residual_phase_f32(c, (const float*)c->hU, (float*)c->hR, phase, e0, e1, c->stream);
+    return sdi_residual_phase_f64(c, (const double*)c->hU, (double*)c->hR, phase, e0, e1, c->stream);
+}
+
+// Host-buffer residual in z-slabs: the copies of U run on their own stream, slab by slab,
+// and each residual phase of a slab starts as soon as the slabs it reads are in (its own
+// and its z neighbours'); R goes back slab by slab on a third stream as each slab's flux
+// phase ends. Phases of one slab: trace <- copy in; grad <- trace of slabs k-1, k, k+1;
+// face <- grad of k, k+1 (+z faces); flux <- face of k-1, k. The slabs are copied in the
+// order S-1, 0, 1, ..., S-2, so slab 0's periodic neighbour arrives first.
+static sd_status residual_host_slabs(sd_ctx* c, const void* U_host, void* R_host) {
+    const int S = std::min(c->ne[2], SDI_MAX_SLABS);
+    const int layer = c->ne[0] * c->ne[1];
+    const size_t ppe = c->npts / c->nelem;
+    auto first = [&](int k) { return (int)((long long)k * c->ne[2] / S) * layer; };
+    auto copy_slab = [&](int k, bool in) -> cudaError_t {
+        const size_t e0 = first(k), e1 = first(k + 1);
+        const size_t bytes = (e1 - e0) * ppe * c->esize;
+        for (int v = 0; v < c->nvar; ++v) {
+            const size_t off = ((size_t)v * c->nelem + e0) * ppe * c->esize;
+            const cudaError_t e = in ? cudaMemcpyAsync((char*)c->hU + off, (const char*)U_host + off, bytes,
+                                                       cudaMemcpyHostToDevice, c->s_h2d)
+                                     : cudaMemcpyAsync((char*)R_host + off, (const char*)c->hR + off, bytes,
+                                                       cudaMemcpyDeviceToHost, c->s_d2h);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    };
+    // the copies start after everything already queued on the context stream
+    CK(cudaEventRecord(c->ev_start, c->stream));
+    CK(cudaStreamWaitEvent(c->s_h2d, c->ev_start, 0));
+    for (int a = 0; a < S; ++a) {
+        const int k = (a + S - 1) % S;
+        CK(copy_slab(k, true));
+        CK(cudaEventRecord(c->ev_in[k], c->s_h2d));
+    }
+    bool tr[SDI_MAX_SLABS] = {false}, gr[SDI_MAX_SLABS] = {false}, fa[SDI_MAX_SLABS] = {false},
+         fl[SDI_MAX_SLABS] = {false};
+    auto m = [&](int k) { return (k + S) % S; };
+    sd_status st;
+    for (int a = 0; a < S; ++a) {
+        const int k = (a + S - 1) % S;
+        CK(cudaStreamWaitEvent(c->stream, c->ev_in[k], 0));
+        if ((st = residual_phase_any(c, SDI_PH_TRACE, first(k), first(k + 1))) != SD_OK) return st;
+        tr[k] = true;
+        for (bool progress = true; progress;) {
+            progress = false;
+            for (int j = 0; j < S; ++j) {
+                if (!gr[j] && tr[m(j - 1)] && tr[j] && tr[m(j + 1)]) {
+                    if ((st = residual_phase_any(c, SDI_PH_GRAD, first(j), first(j + 1))) != SD_OK) return st;
+                    gr[j] = progress = true;
+                }
+                if (!fa[j] && gr[j] && gr[m(j + 1)]) {
+                    if ((st = residual_phase_any(c, SDI_PH_FACE, first(j), first(j + 1))) != SD_OK) return st;
+                    fa[j] = progress = true;
+                }
+                if (!fl[j] && fa[j] && fa[m(j - 1)]) {
+                    if ((st = residual_phase_any(c, SDI_PH_FLUX, first(j), first(j + 1))) != SD_OK) return st;
+                    fl[j] = progress = true;
+                    CK(cudaEventRecord(c->ev_out[j], c->stream));
+                    CK(cudaStreamWaitEvent(c->s_d2h, c->ev_out[j], 0));
+                    CK(copy_slab(j, false));
+                }
+            }
+        }
+    }
+    for (int j = 0; j < S; ++j)
+        if (!fl[j]) { sdi_set_error("slab schedule incomplete"); return SD_ECUDA; }
+    CK(cudaStreamSynchronize(c->s_d2h));
+    CK(cudaStreamSynchronize(c->stream));
+    return SD_OK;
+}
+
 extern "C" sd_status sd_residual_host(sd_ctx* c, const void* U_host, void* R_host) {
     if (!c || !U_host || !R_host) { sdi_set_error("null argument"); return SD_EINVAL; }
+    if (c->s_h2d && !c->closure_on && c->ne[2] >= 4) return residual_host_slabs(c, U_host, R_host);
     const size_t bytes = c->nstate * c->esize;
     CK(cudaMemcpyAsync(c->hU, U_host, bytes, cudaMemcpyHostToDevice, c->stream));
     const sd_status st = residual_any(c, c->hU, c->hR);

@@ -6,6 +6,11 @@ sd_status sdi_residual_f64(sd_ctx* c, const double* U, double* R, int offset_in)
     return sdk::residual_dispatch<double>(c, U, R, offset_in);
 }
 
+sd_status sdi_residual_phase_f64(sd_ctx* c, const double* U, double* R, int phase, int e_begin, int e_end,
+                                 cudaStream_t stream) {
+    return sdk::phase_dispatch<double>(c, U, R, 0, phase, e_begin, e_end, stream);
+}
+
 sd_status sdi_upload_f64(const sd_ctx* c) { return sdk::upload_dispatch<double>(c); }
 
 sd_status sdi_closure_data_f64(sd_ctx* c, const double* U, float* X, double* means) {

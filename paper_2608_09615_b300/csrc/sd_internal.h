@@ -8,6 +8,8 @@
 
 #define SD_MAX_N 9
 
+#define SDI_MAX_SLABS 16   // slabs of the pipelined host-buffer residual
+
 struct sd_ctx {
     // problem
     int dim;
@@ -53,6 +55,10 @@ struct sd_ctx {
     int diag_blocks;
     void* hU;                // device staging of the host-buffer residual path
     void* hR;
+    // host-buffer path in slabs (3D): copy streams and per-slab events, created with the
+    // context; null when the path is not used
+    cudaStream_t s_h2d, s_d2h;
+    cudaEvent_t ev_in[SDI_MAX_SLABS], ev_out[SDI_MAX_SLABS], ev_start;
     // extra per-element flux added by the residual ([nelem][15] FP32, tau[e][3 v + d]),
     // caller-owned or the closure's own buffer; NULL: none
     const float* tau;
@@ -86,6 +92,12 @@ void sdi_prof_end(sd_ctx* c, int k);
 // offset_in != 0: U already has the reference offsets removed (Runge-Kutta stage copies)
 sd_status sdi_residual_f32(sd_ctx* c, const float* U, float* R, int offset_in);
 sd_status sdi_residual_f64(sd_ctx* c, const double* U, double* R, int offset_in);
+// one phase of the residual over elements [e_begin, e_end) on `stream` (host pipeline)
+enum { SDI_PH_TRACE = 0, SDI_PH_GRAD = 1, SDI_PH_FACE = 2, SDI_PH_FLUX = 3 };
+sd_status sdi_residual_phase_f32(sd_ctx* c, const float* U, float* R, int phase, int e_begin, int e_end,
+                                 cudaStream_t stream);
+sd_status sdi_residual_phase_f64(sd_ctx* c, const double* U, double* R, int phase, int e_begin, int e_end,
+                                 cudaStream_t stream);
 sd_status sdi_upload_f32(const sd_ctx* c);
 sd_status sdi_upload_f64(const sd_ctx* c);
 // closure data of a state: features X [nelem][64] and/or flux means [nelem][15] (either NULL)

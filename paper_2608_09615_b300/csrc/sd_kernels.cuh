@@ -52,6 +52,7 @@ struct Phys {
 struct Mesh {
     int ne[3];
     int nelem;
+    int e_begin, e_end;      // elements [e_begin, e_end) processed by a residual launch
 };
 
 // ------------------------------------------------------------------ index helpers

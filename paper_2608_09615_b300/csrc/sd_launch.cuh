@@ -125,10 +125,12 @@ static sd_status upload_dispatch(const sd_ctx* c) {
     }
 }
 
-inline Mesh make_mesh(const sd_ctx* c) {
+inline Mesh make_mesh(const sd_ctx* c, int e_begin = 0, int e_end = -1) {
     Mesh g;
     for (int d = 0; d < 3; ++d) g.ne[d] = c->ne[d];
     g.nelem = c->nelem;
+    g.e_begin = e_begin;
+    g.e_end = e_end < 0 ? c->nelem : e_end;
     return g;
 }
 
@@ -221,51 +223,97 @@ static sd_status closure_stage(sd_ctx* c, const real* U, int offset_in) {
     return sdi_closure_network(c);
 }
 
+// One phase of the residual (SDI_PH_TRACE, _GRAD, _FACE, _FLUX) over the elements
+// [e_begin, e_end) on `stream`. Each phase reads what the earlier phases wrote for the
+// elements it touches (its own and their face neighbours).
 template <typename real, int N, int DIM, int NV>
-static sd_status residual_impl(sd_ctx* c, const real* U, real* R, int offset_in) {
+static sd_status residual_phase(sd_ctx* c, const real* U, real* R, int offset_in, int phase, int e_begin,
+                                int e_end, cudaStream_t stream) {
     using LL = LineLayout<N, DIM, NV>;
+    using FL = FluxLayout<N, DIM, NV>;
     const LineGeo<real> geo = make_geo<real>(c, offset_in);
-    const Mesh g = make_mesh(c);
+    const Mesh g = make_mesh(c, e_begin, e_end);
     const Phys<real> P = make_phys<real>(c);
-    const int compact = c->scheme == SD_COMPACT ? 1 : 0;
+    const long long ne = e_end - e_begin;
+    if (ne <= 0) return SD_OK;
     real* Tu = static_cast<real*>(c->Tu);
     real* Tg = static_cast<real*>(c->Tg);
-    const long long ngroups = (g.nelem + LL::EB - 1) / LL::EB;
-    const size_t st = TracePipe<real, LL>::BYTES;
-    const size_t sg = GradPipe<real, LL>::BYTES;
-    using FL = FluxLayout<N, DIM, NV>;
-    const size_t sf = FluxPipe<real, FL>::BYTES;
-    if (!set_smem(k_line_trace<real, N, DIM, NV>, st) || !set_smem(k_line_grad<real, N, DIM, NV>, sg) ||
-        !set_smem(k_line_flux<real, N, DIM, NV>, sf))
-        return SD_EUNSUPPORTED;
-    const int bt = persistent_grid(k_line_trace<real, N, DIM, NV>, LL::THREADS, st, ngroups, c->device);
-    const int bg = persistent_grid(k_line_grad<real, N, DIM, NV>, LL::THREADS, sg, ngroups, c->device);
-    const int bf = persistent_grid(k_line_flux<real, N, DIM, NV>, FL::THREADS, sf, (g.nelem + FL::EB - 1) / FL::EB,
-                                   c->device);
     real* Fh = static_cast<real*>(c->Fh);
-    sdi_prof_begin(c, SD_K_TRACE);
-    k_line_trace<real, N, DIM, NV><<<bt, LL::THREADS, st, c->stream>>>(U, Tu, geo, g, P);
-    sdi_prof_end(c, SD_K_TRACE);
-    if (c->closure_on && NV == 5) {
-        const sd_status cs = closure_stage<real, N>(c, U, offset_in);
-        if (cs != SD_OK) return cs;
+    if (phase == SDI_PH_TRACE) {
+        const size_t st = TracePipe<real, LL>::BYTES;
+        if (!set_smem(k_line_trace<real, N, DIM, NV>, st)) return SD_EUNSUPPORTED;
+        const int bt = persistent_grid(k_line_trace<real, N, DIM, NV>, LL::THREADS, st, (ne + LL::EB - 1) / LL::EB,
+                                       c->device);
+        sdi_prof_begin(c, SD_K_TRACE);
+        k_line_trace<real, N, DIM, NV><<<bt, LL::THREADS, st, stream>>>(U, Tu, geo, g, P);
+        sdi_prof_end(c, SD_K_TRACE);
+    } else if (phase == SDI_PH_GRAD) {
+        const size_t sg = GradPipe<real, LL>::BYTES;
+        if (!set_smem(k_line_grad<real, N, DIM, NV>, sg)) return SD_EUNSUPPORTED;
+        const int bg = persistent_grid(k_line_grad<real, N, DIM, NV>, LL::THREADS, sg, (ne + LL::EB - 1) / LL::EB,
+                                       c->device);
+        sdi_prof_begin(c, SD_K_GRAD);
+        k_line_grad<real, N, DIM, NV><<<bg, LL::THREADS, sg, stream>>>(U, Tu, Tg, geo, g,
+                                                                       c->scheme == SD_COMPACT ? 1 : 0);
+        sdi_prof_end(c, SD_K_GRAD);
+    } else if (phase == SDI_PH_FACE) {
+        sdi_prof_begin(c, SD_K_FACE);
+        k_face_flux<real, N, DIM, NV><<<trace_blocks(ne * DIM * LL::NQ), 256, 0, stream>>>(Tu, Tg, Fh, geo, g, P,
+                                                                                          c->tau);
+        sdi_prof_end(c, SD_K_FACE);
+    } else {
+        const size_t sf = FluxPipe<real, FL>::BYTES;
+        if (!set_smem(k_line_flux<real, N, DIM, NV>, sf)) return SD_EUNSUPPORTED;
+        const int bf = persistent_grid(k_line_flux<real, N, DIM, NV>, FL::THREADS, sf, (ne + FL::EB - 1) / FL::EB,
+                                       c->device);
+        sdi_prof_begin(c, SD_K_FLUX);
+        k_line_flux<real, N, DIM, NV><<<bf, FL::THREADS, sf, stream>>>(U, Tu, Fh, R, geo, g, P, c->tau);
+        sdi_prof_end(c, SD_K_FLUX);
     }
-    sdi_prof_begin(c, SD_K_GRAD);
-    k_line_grad<real, N, DIM, NV><<<bg, LL::THREADS, sg, c->stream>>>(U, Tu, Tg, geo, g, compact);
-    sdi_prof_end(c, SD_K_GRAD);
-    sdi_prof_begin(c, SD_K_FACE);
-    k_face_flux<real, N, DIM, NV><<<trace_blocks((long long)g.nelem * DIM * LL::NQ), 256, 0, c->stream>>>(
-        Tu, Tg, Fh, geo, g, P, c->tau);
-    sdi_prof_end(c, SD_K_FACE);
-    sdi_prof_begin(c, SD_K_FLUX);
-    k_line_flux<real, N, DIM, NV><<<bf, FL::THREADS, sf, c->stream>>>(U, Tu, Fh, R, geo, g, P, c->tau);
-    sdi_prof_end(c, SD_K_FLUX);
     const cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) {
         sdi_set_error("residual launch failed: %s", cudaGetErrorString(err));
         return SD_ECUDA;
     }
     return SD_OK;
+}
+
+template <typename real, int N, int DIM, int NV>
+static sd_status residual_impl(sd_ctx* c, const real* U, real* R, int offset_in) {
+    const int ne = c->nelem;
+    sd_status s = residual_phase<real, N, DIM, NV>(c, U, R, offset_in, SDI_PH_TRACE, 0, ne, c->stream);
+    if (s != SD_OK) return s;
+    if (c->closure_on && NV == 5) {
+        s = closure_stage<real, N>(c, U, offset_in);
+        if (s != SD_OK) return s;
+    }
+    for (int ph : {SDI_PH_GRAD, SDI_PH_FACE, SDI_PH_FLUX})
+        if ((s = residual_phase<real, N, DIM, NV>(c, U, R, offset_in, ph, 0, ne, c->stream)) != SD_OK) return s;
+    return SD_OK;
+}
+
+template <typename real, int N>
+static sd_status phase_n(sd_ctx* c, const real* U, real* R, int offset_in, int phase, int eb, int ee,
+                         cudaStream_t st) {
+    if (c->nvar == 5) return residual_phase<real, N, 3, 5>(c, U, R, offset_in, phase, eb, ee, st);
+    if (c->dim == 1) return residual_phase<real, N, 1, 1>(c, U, R, offset_in, phase, eb, ee, st);
+    return residual_phase<real, N, 3, 1>(c, U, R, offset_in, phase, eb, ee, st);
+}
+
+template <typename real>
+static sd_status phase_dispatch(sd_ctx* c, const real* U, real* R, int offset_in, int phase, int eb, int ee,
+                                cudaStream_t st) {
+    switch (c->n) {
+        case 2: return phase_n<real, 2>(c, U, R, offset_in, phase, eb, ee, st);
+        case 3: return phase_n<real, 3>(c, U, R, offset_in, phase, eb, ee, st);
+        case 4: return phase_n<real, 4>(c, U, R, offset_in, phase, eb, ee, st);
+        case 5: return phase_n<real, 5>(c, U, R, offset_in, phase, eb, ee, st);
+        case 6: return phase_n<real, 6>(c, U, R, offset_in, phase, eb, ee, st);
+        case 7: return phase_n<real, 7>(c, U, R, offset_in, phase, eb, ee, st);
+        case 8: return phase_n<real, 8>(c, U, R, offset_in, phase, eb, ee, st);
+        case 9: return phase_n<real, 9>(c, U, R, offset_in, phase, eb, ee, st);
+        default: return SD_EUNSUPPORTED;
+    }
 }
 
 template <typename real, int N>

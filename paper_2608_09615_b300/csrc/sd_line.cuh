@@ -118,6 +118,20 @@ struct Strides {
     static constexpr int FS = FS_;
 };
 
+// element groups of a launch: EB consecutive elements each, over [e_begin, e_end)
+template <int EB>
+__device__ __forceinline__ int num_groups(const Mesh& g) {
+    return (g.e_end - g.e_begin + EB - 1) / EB;
+}
+template <int EB>
+__device__ __forceinline__ int grp_first(const Mesh& g, int grp) {
+    return g.e_begin + grp * EB;
+}
+template <int EB>
+__device__ __forceinline__ int grp_count(const Mesh& g, int grp) {
+    return min(EB, g.e_end - (g.e_begin + grp * EB));
+}
+
 struct LineId {
     int d;      // direction of this warp
     int eb;     // element slot in the block
@@ -345,13 +359,13 @@ __device__ __forceinline__ void pipe_start(const real* __restrict__ U, const rea
                                            const real* __restrict__ Fh, const Mesh& g, int grp, int ngroups,
                                            real* buf0, int* nbr0, int* nbr1) {
     if (NB_TR || FH) {
-        nbr_table<LL>(g, grp * LL::EB, min(LL::EB, g.nelem - grp * LL::EB), nbr0);
+        nbr_table<LL>(g, grp_first<LL::EB>(g, grp), grp_count<LL::EB>(g, grp), nbr0);
         const int gn = grp + gridDim.x;
-        if (PL::NBUF == 2 && gn < ngroups) nbr_table<LL>(g, gn * LL::EB, min(LL::EB, g.nelem - gn * LL::EB), nbr1);
+        if (PL::NBUF == 2 && gn < ngroups) nbr_table<LL>(g, grp_first<LL::EB>(g, gn), grp_count<LL::EB>(g, gn), nbr1);
         __syncthreads();
     }
     if constexpr (PL::NBUF == 2) {
-        stage_issue<real, LL, PL, NV, NB_TR, FH>(U, Tu, Fh, g, grp * LL::EB, min(LL::EB, g.nelem - grp * LL::EB),
+        stage_issue<real, LL, PL, NV, NB_TR, FH>(U, Tu, Fh, g, grp_first<LL::EB>(g, grp), grp_count<LL::EB>(g, grp),
                                                  buf0, nbr0);
         cp_async_commit();
     }
@@ -368,19 +382,19 @@ __device__ __forceinline__ void pipe_next(const real* __restrict__ U, const real
     if constexpr (PL::NBUF == 2) {
         const int gn = grp + gridDim.x;
         if (gn < ngroups)
-            stage_issue<real, LL, PL, NV, NB_TR, FH>(U, Tu, Fh, g, gn * LL::EB, min(LL::EB, g.nelem - gn * LL::EB),
+            stage_issue<real, LL, PL, NV, NB_TR, FH>(U, Tu, Fh, g, grp_first<LL::EB>(g, gn), grp_count<LL::EB>(g, gn),
                                                      b ? buf0 : buf1, b ? nbr0 : nbr1);
         cp_async_commit();
         cp_async_wait_group<1>();
     } else {
-        stage_issue<real, LL, PL, NV, NB_TR, FH>(U, Tu, Fh, g, grp * LL::EB, min(LL::EB, g.nelem - grp * LL::EB),
+        stage_issue<real, LL, PL, NV, NB_TR, FH>(U, Tu, Fh, g, grp_first<LL::EB>(g, grp), grp_count<LL::EB>(g, grp),
                                                  buf, nbr0);
         cp_async_commit();
         cp_async_wait_group<0>();
     }
     __syncthreads();
     if (NV == 5 && (off0 != real(0) || off4 != real(0))) {
-        const int span = min(LL::EB, g.nelem - grp * LL::EB) * LL::NP;
+        const int span = grp_count<LL::EB>(g, grp) * LL::NP;
         real* u0 = buf;
         real* u4 = buf + 4 * LL::EB * LL::NP;
         for (int k = threadIdx.x; k < span; k += blockDim.x) {
@@ -399,7 +413,7 @@ __device__ __forceinline__ void pipe_tail(const Mesh& g, int grp, int ngroups, i
     if constexpr (NB) {
         const int ga = grp + (PL::NBUF == 2 ? 2 : 1) * gridDim.x;
         if (ga < ngroups)
-            nbr_table<LL>(g, ga * LL::EB, min(LL::EB, g.nelem - ga * LL::EB), (PL::NBUF == 2 && b) ? nbr1 : nbr0);
+            nbr_table<LL>(g, grp_first<LL::EB>(g, ga), grp_count<LL::EB>(g, ga), (PL::NBUF == 2 && b) ? nbr1 : nbr0);
     }
 }
 
@@ -618,18 +632,18 @@ k_line_trace(const real* __restrict__ U, real* __restrict__ Tu, LineGeo<real> ge
     extern __shared__ __align__(16) unsigned char smem_raw[];
     real* buf0 = reinterpret_cast<real*>(smem_raw + 2 * LL::NBR_BYTES);
     real* buf1 = buf0 + (PL::NBUF - 1) * PL::LOAD;
-    const int ngroups = (g.nelem + LL::EB - 1) / LL::EB;
+    const int ngroups = num_groups<LL::EB>(g);
     int grp = blockIdx.x;
     if (grp >= ngroups) return;
     const LineId id = line_id<LL>(threadIdx.x);
     pipe_start<real, LL, PL, NV, false, false>(U, nullptr, nullptr, g, grp, ngroups, buf0, nullptr, nullptr);
     for (int b = 0; grp < ngroups; grp += gridDim.x, b ^= 1) {
         real* buf = b ? buf1 : buf0;
-        const int e0 = grp * LL::EB;
+        const int e0 = grp_first<LL::EB>(g, grp);
         pipe_next<real, LL, PL, NV, false, false>(U, nullptr, nullptr, g, grp, ngroups, b, buf0, buf1, nullptr,
                                                   nullptr, geo.off0, geo.off4);
         const int e = e0 + id.eb;
-        if (id.ok && e < g.nelem) {
+        if (id.ok && e < g.e_end) {
             const real* su = buf + id.eb * NP;
             real* out = Tu + (size_t)e * NF * FST + id.q;
             if (id.d == 0) line_traces<real, N, NQ, NV, 0, ST>(su, id.q, out, out + FST, NQ);
@@ -666,7 +680,7 @@ k_line_grad(const real* __restrict__ U, const real* __restrict__ Tu, real* __res
     real* buf0 = reinterpret_cast<real*>(smem_raw + 2 * LL::NBR_BYTES);
     real* buf1 = buf0 + (PL::NBUF - 1) * PL::LOAD;
     real* work = buf0 + PL::NBUF * PL::LOAD;
-    const int ngroups = (g.nelem + LL::EB - 1) / LL::EB;
+    const int ngroups = num_groups<LL::EB>(g);
     int grp = blockIdx.x;
     if (grp >= ngroups) return;
     const LineId id = line_id<LL>(threadIdx.x);
@@ -674,11 +688,11 @@ k_line_grad(const real* __restrict__ U, const real* __restrict__ Tu, real* __res
     pipe_start<real, LL, PL, NV, true, false>(U, Tu, nullptr, g, grp, ngroups, buf0, nbr0, nbr1);
     for (int b = 0; grp < ngroups; grp += gridDim.x, b ^= 1) {
         real* buf = b ? buf1 : buf0;
-        const int e0 = grp * LL::EB;
+        const int e0 = grp_first<LL::EB>(g, grp);
         pipe_next<real, LL, PL, NV, true, false>(U, Tu, nullptr, g, grp, ngroups, b, buf0, buf1, nbr0, nbr1,
                                                  geo.off0, geo.off4);
         const int e = e0 + id.eb;
-        const bool live = id.ok && e < g.nelem;
+        const bool live = id.ok && e < g.e_end;
         const real* su = buf + id.eb * NP;
         const real* trn = buf + PL::OFF_TR + id.eb * NF * LL::FST;
         real u[NV][N], dl[NV], dr[NV];
@@ -816,13 +830,14 @@ __global__ void __launch_bounds__(256)
 k_face_flux(const real* __restrict__ Tu, const real* __restrict__ Tg, real* __restrict__ Fh,
             LineGeo<real> geo, Mesh g, Phys<real> P, const float* __restrict__ tau) {
     constexpr int NQ = ipow(N, DIM - 1);
-    const long long per_d = (long long)g.nelem * NQ;
+    const long long per_d = (long long)(g.e_end - g.e_begin) * NQ;
     const long long total = per_d * DIM;
     for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
          idx += (long long)gridDim.x * blockDim.x) {
         const int d = (int)(idx / per_d);
         const long long r = idx - d * per_d;
-        const int e = (int)(r / NQ), q = (int)(r - (long long)e * NQ);
+        const int el = (int)(r / NQ), q = (int)(r - (long long)el * NQ);
+        const int e = g.e_begin + el;
         if (d == 0) face_point<real, N, DIM, NV, 0>(Tu, Tg, Fh, geo, g, P, tau, e, q);
         if constexpr (DIM == 3) {
             if (d == 1) face_point<real, N, DIM, NV, 1>(Tu, Tg, Fh, geo, g, P, tau, e, q);
@@ -920,7 +935,7 @@ k_line_flux(const real* __restrict__ U, const real* __restrict__ Tu, const real*
     real* buf0 = reinterpret_cast<real*>(smem_raw + 2 * LL::NBR_BYTES);
     real* buf1 = buf0 + (PL::NBUF - 1) * PL::LOAD;
     real* work = buf0 + PL::NBUF * PL::LOAD;
-    const int ngroups = (g.nelem + EB - 1) / EB;
+    const int ngroups = num_groups<EB>(g);
     int grp = blockIdx.x;
     if (grp >= ngroups) return;
     const LineId id = line_id<LL>(threadIdx.x);
@@ -929,11 +944,11 @@ k_line_flux(const real* __restrict__ U, const real* __restrict__ Tu, const real*
     pipe_start<real, LL, PL, NV, true, true>(U, Tu, Fh, g, grp, ngroups, buf0, nbr0, nbr1);
     for (int b = 0; grp < ngroups; grp += gridDim.x, b ^= 1) {
         real* buf = b ? buf1 : buf0;
-        const int e0 = grp * EB, nloc = min(EB, g.nelem - e0);
+        const int e0 = grp_first<EB>(g, grp), nloc = grp_count<EB>(g, grp);
         pipe_next<real, LL, PL, NV, true, true>(U, Tu, Fh, g, grp, ngroups, b, buf0, buf1, nbr0, nbr1,
                                                 geo.off0, geo.off4);
         const int e = e0 + id.eb;
-        const bool live = id.ok && e < g.nelem;
+        const bool live = id.ok && e < g.e_end;
         const real* su = buf + id.eb * NP;
         const real* trn = buf + PL::OFF_TR + id.eb * NF * LL::FST;
         const real* fh = buf + PL::OFF_FH + id.eb * NF * LL::FST;

@@ -150,16 +150,23 @@ def test_fp32_error_tgv_report(capsys):
 
 
 # ------------------------------------------------------------------ host path, RK, diagnostics
-def test_host_path_equals_device_path():
+@pytest.mark.parametrize("ne,precision,scheme", [((4, 3, 2), "f32", "compact"),     # one pass
+                                                   ((4, 3, 7), "f32", "compact"),     # 7 z-slabs
+                                                   ((3, 5, 20), "f32", "br1"),        # 16 uneven slabs
+                                                   ((3, 2, 9), "f64", "compact")])
+def test_host_path_equals_device_path(ne, precision, scheme):
+    # sd_residual_host: whole-grid copies for thin grids, the slab pipeline (copies on
+    # their own streams, phases per z-slab) otherwise; bitwise the device residual
     prm, phys = ns_phys()
-    ne, p = (4, 3, 2), 3
-    ctx = sd.SD(3, ne, (0,) * 3, (TWO_PI,) * 3, p, "compact", phys, "f32")
-    U = torch.from_numpy(inputs.tgv_3d(ne, p, perturb_seed=1)).float()
+    p = 3
+    ctx = sd.SD(3, ne, (0,) * 3, (TWO_PI,) * 3, p, scheme, phys, precision)
+    U = torch.from_numpy(inputs.tgv_3d(ne, p, perturb_seed=1)).to(ctx.dtype)
     Rd = ctx.residual(U.cuda()).cpu()
     Uh = U.pin_memory()
-    Rh = torch.empty_like(Uh).pin_memory()
-    ctx.residual_host(Uh, Rh)
-    assert torch.equal(Rd, Rh)
+    Rh = torch.full_like(Uh, float("nan")).pin_memory()
+    for _ in range(2):
+        ctx.residual_host(Uh, Rh)
+        assert torch.equal(Rd, Rh)
     ctx.close()
 
 
