@@ -19,7 +19,7 @@ import time
 import numpy as np
 
 from . import MLP, SD, Physics, closure_targets, colstats, filter_project, filter_matrix, standardise
-from . import inputs
+from . import inputs, tgv
 
 
 def init_params(seed, widths=(64, 128, 128, 15)):
@@ -33,40 +33,14 @@ def init_params(seed, widths=(64, 128, 128, 15)):
 
 
 def stable_dt(ne, p, Ma=0.1, cfl=0.2):
-    """Acoustic time step of the periodic [0, 2 pi]^3 grid with u0 = 1:
-    cfl h / ((p + 1)(|u| + c)) with |u| + c ~ 1 + 1/Ma."""
-    h = 2 * math.pi / ne
-    return cfl * h / ((p + 1) * (1.0 + 1.0 / Ma))
+    """Acoustic time step of the periodic [0, 2 pi]^3 grid with u0 = 1 (tgv.time_step)."""
+    return tgv.time_step(ne, p, Ma, cfl=cfl)
 
 
-def run_tgv(ne, p, Re, t_end, every, dt=None, precision="f32", scheme="compact", closure=None,
-            on_sample=None):
-    """SSPRK(5,4) Taylor-Green run on the GPU; returns the diagnostics every `every` time
-    units (and calls on_sample(t, U) there)."""
-    import torch
-    dt = dt or stable_dt(ne, p)
-    steps_per = max(1, int(round(every / dt)))
-    dt = every / steps_per
-    ctx = SD(3, (ne,) * 3, (0.0,) * 3, (2 * math.pi,) * 3, p, scheme, Physics(kind="ns", Re=Re), precision)
-    if closure is not None:
-        ctx.closure_enable(*closure)
-    U = torch.from_numpy(inputs.tgv_3d((ne,) * 3, p)).cuda()
-    t = 0.0
-    rec = [ctx.diagnostics(U, t, raise_nonfinite=False)]
-    if on_sample:
-        on_sample(t, U)
-    for _ in range(int(round(t_end / every))):
-        for _ in range(steps_per):
-            ctx.rk_step(U, t, dt, "ssprk54")
-            t += dt
-        d = ctx.diagnostics(U, t, raise_nonfinite=False)
-        rec.append(d)
-        if on_sample:
-            on_sample(t, U)
-        if d["nonfinite"]:
-            break
-    ctx.close()
-    return rec
+def run_tgv(ne, p, Re, t_end, every, precision="f32", scheme="compact", closure=None, on_sample=None):
+    """SSPRK(5,4) Taylor-Green run on the GPU (tgv.run); returns the diagnostics every
+    `every` time units (and calls on_sample(t, U) there)."""
+    return tgv.run(ne, p, Re, scheme, t_end, every, precision, closure=closure, on_sample=on_sample)["diag"]
 
 
 def training_data(fine_ne, coarse_ne, Re_list, t_end, every, pf=4, pc=3):
@@ -117,8 +91,7 @@ def train(X, T, steps=2000, lr=2e-3, seed=0, log_every=0):
 
 
 def dissipation(rec, every):
-    ke = np.array([d["ke"] / d["volume"] for d in rec])
-    return -(ke[2:] - ke[:-2]) / (2 * every)
+    return tgv.dissipation(rec, every)
 
 
 def evaluate(net, stats, coarse_ne, Re, t_end, every, reference, pc=3):
