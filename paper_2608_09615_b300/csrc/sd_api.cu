@@ -267,7 +267,7 @@ static void free_all(sd_ctx* c) {
     }
     if (c->cl_tmode) cudaFree(c->cl_tmode);
     void* ptrs[] = {c->Tu, c->Tg, c->Fh, c->S, c->K, c->rA, c->rB, c->rC, c->rX, c->dW,
-                    c->partial, c->dsum, c->hU, c->hR};
+                    c->partial, c->partial2, c->dsum, c->hU, c->hR};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c->Tu64 && (void*)c->Tu64 != c->Tu) cudaFree(c->Tu64);
@@ -396,6 +396,7 @@ extern "C" sd_status sd_init(const sd_mesh* mesh, int p, sd_scheme scheme, const
     c->diag_blocks = (c->nelem + epb - 1) / epb;
     alloc((void**)&c->partial, (size_t)c->diag_blocks * sdk::NDIAG * sizeof(double));
     alloc((void**)&c->dsum, sdk::NDIAG * sizeof(double));
+    alloc((void**)&c->partial2, sdk::DIAG_L1 * sdk::NDIAG * sizeof(double));
     alloc(&c->hU, S * c->esize);
     alloc(&c->hR, S * c->esize);
     if (ok && c->dim == 3) {
@@ -811,6 +812,28 @@ extern "C" sd_status sd_rk_step(sd_ctx* c, double* U64, double t, double dt, sd_
 
 // ------------------------------------------------------------------ diagnostics
 namespace sdk {
+// two-level reduction of the block partials, in a fixed order (deterministic): block j of
+// the first level sums partials [j chunk, (j + 1) chunk); one block then sums those
+
+__global__ void k_diag_reduce(const double* __restrict__ partial, int nblocks, int chunk,
+                              double* __restrict__ out) {
+    __shared__ double red[NDIAG][256];
+    const int b0 = blockIdx.x * chunk, b1 = min(nblocks, b0 + chunk);
+    for (int k = 0; k < NDIAG; ++k) {
+        double s = 0.0;
+        for (int b = b0 + threadIdx.x; b < b1; b += blockDim.x) s += partial[(size_t)b * NDIAG + k];
+        red[k][threadIdx.x] = s;
+    }
+    __syncthreads();
+    for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+        if ((int)threadIdx.x < st)
+            for (int k = 0; k < NDIAG; ++k) red[k][threadIdx.x] += red[k][threadIdx.x + st];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        for (int k = 0; k < NDIAG; ++k) out[(size_t)blockIdx.x * NDIAG + k] = red[k][0];
+}
+
 __global__ void k_diag_final(const double* __restrict__ partial, int nblocks,
                              double* __restrict__ out) {
     __shared__ double red[NDIAG][256];
@@ -847,8 +870,13 @@ static sd_status diag_impl(sd_ctx* c, const double* U) {
     sdi_prof_begin(c, SD_K_OTHER);
     k_diag<N, DIM, NV><<<nb, threads, smem, c->stream>>>(U, c->Tu64, ops, g, c->dW, c->J, c->partial);
     sdi_prof_end(c, SD_K_OTHER);
+    const int chunk = (nb + DIAG_L1 - 1) / DIAG_L1;
+    const int nb1 = (nb + chunk - 1) / chunk;
     sdi_prof_begin(c, SD_K_OTHER);
-    k_diag_final<<<1, 256, 0, c->stream>>>(c->partial, nb, c->dsum);
+    k_diag_reduce<<<nb1, 256, 0, c->stream>>>(c->partial, nb, chunk, c->partial2);
+    sdi_prof_end(c, SD_K_OTHER);
+    sdi_prof_begin(c, SD_K_OTHER);
+    k_diag_final<<<1, 256, 0, c->stream>>>(c->partial2, nb1, c->dsum);
     sdi_prof_end(c, SD_K_OTHER);
     CK(cudaGetLastError());
     return SD_OK;

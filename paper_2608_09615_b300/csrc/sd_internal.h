@@ -51,6 +51,7 @@ struct sd_ctx {
     void* rX;                // FP32 contexts: the step's start state minus the offsets
     double* dW;              // Gauss weights (device, n values)
     double* partial;         // diagnostics block partials
+    double* partial2;        // second-level partials (DIAG_L1 x NDIAG)
     double* dsum;            // diagnostics totals (device)
     int diag_blocks;
     void* hU;                // device staging of the host-buffer residual path

@@ -283,26 +283,34 @@ __device__ __forceinline__ void stage_element(const real* __restrict__ U,
                                               real* tro, real* trn, real* vS) {
     using FP = Footprint<N, DIM, NV>;
     constexpr int NP = FP::NP, NQ = FP::NQ, NF = FP::NF, TPE = FP::TPE;
+    // (the diagnostics need no gradient of a scalar, and for Navier-Stokes only the
+    // derivatives of rho and of the momentum components across the derivative direction:
+    // the vorticity)
     if (valid) {
         for (int k = tid; k < NV * NP; k += TPE) {
             const int v = k / NP, pt = k - v * NP;
             su[k] = U[(size_t)v * g.nelem * NP + (size_t)e * NP + pt];
         }
-        for (int k = tid; k < NF * NV * NQ; k += TPE) {
-            const int f = k / (NV * NQ);
-            const int rem = k - f * NV * NQ;
-            const int d = f >> 1, s = f & 1;
-            const int en = neighbour(g, e, d, s);
-            // the neighbour's trace on the shared face is its face of opposite side
-            trn[k] = Tu[((size_t)en * NF + (f ^ 1)) * NV * NQ + rem];
+        if constexpr (NV == 5) {
+            for (int k = tid; k < NF * NV * NQ; k += TPE) {
+                const int f = k / (NV * NQ);
+                const int rem = k - f * NV * NQ;
+                if (rem >= 4 * NQ) continue;
+                const int d = f >> 1, s = f & 1;
+                const int en = neighbour(g, e, d, s);
+                // the neighbour's trace on the shared face is its face of opposite side
+                trn[k] = Tu[((size_t)en * NF + (f ^ 1)) * NV * NQ + rem];
+            }
         }
     }
     __syncthreads();
+    if constexpr (NV != 5) return;
     if (valid) {
         for (int k = tid; k < NF * NV * NQ; k += TPE) {
             const int f = k / (NV * NQ);
             const int rem = k - f * NV * NQ;
             const int v = rem / NQ, q = rem - v * NQ;
+            if (v >= 4) continue;
             const int d = f >> 1, s = f & 1;
             tro[k] = line_dot<real, N>(ops.L + (s ? N * N : 0), su + v * NP + pt_of<N>(d, 0, q),
                                        npow<N>(d));
@@ -315,6 +323,7 @@ __device__ __forceinline__ void stage_element(const real* __restrict__ U,
         for (int k = tid; k < NV * DIM * NP; k += TPE) {
             const int vm = k / NP, pt = k - vm * NP;
             const int v = vm / DIM, m = vm - v * DIM;
+            if (v >= 4 || (v >= 1 && v - 1 == m)) continue;
             const int lo = npow<N>(m);
             const int i = (pt / lo) % N;
             const int q = (pt % lo) + lo * (pt / (lo * N));
@@ -330,27 +339,6 @@ __device__ __forceinline__ void stage_element(const real* __restrict__ U,
     __syncthreads();
 }
 
-// The element's own interface value of gradient component c on face f (BR1: Eq. v:e at
-// the interface row; compact: the closed form described at the top of this file).
-template <typename real, int N, int DIM, int NV>
-__device__ __forceinline__ real face_grad(const Ops<real, N>& ops, int compact, int f, int c,
-                                          int q, const real* vS, const real* tro,
-                                          const real* trn) {
-    using FP = Footprint<N, DIM, NV>;
-    constexpr int NP = FP::NP, NQ = FP::NQ;
-    const int d = f >> 1, s = f & 1;
-    int v, m;
-    comp_map<NV>(d, c, v, m);
-    real val = line_dot<real, N>(ops.L + (s ? N * N : 0), vS + (v * DIM + m) * NP + pt_of<N>(d, 0, q),
-                                 npow<N>(d));
-    if (compact && m == d) {
-        const int fo = f ^ 1;    // the opposite face of the same direction
-        const real dop = real(0.5) * (trn[(fo * NV + v) * NQ + q] - tro[(fo * NV + v) * NQ + q]);
-        val = fma(-(s ? ops.corrR[d] : ops.corrL[d]), dop, val);
-    }
-    return val;
-}
-
 // ------------------------------------------------------------------ kernels
 template <typename real, int N, int DIM, int NV>
 __global__ void k_trace(const real* __restrict__ U, real* __restrict__ Tu, Ops<real, N> ops,
@@ -363,6 +351,7 @@ __global__ void k_trace(const real* __restrict__ U, real* __restrict__ Tu, Ops<r
         long long r = idx / NQ;
         const int v = (int)(r % NV);
         r /= NV;
+        if (NV == 5 && v == 4) continue;      // the diagnostics use no trace of rho E
         const int f = (int)(r % NF);
         const int e = (int)(r / NF);
         const int d = f >> 1, s = f & 1;
@@ -376,6 +365,7 @@ __global__ void k_trace(const real* __restrict__ U, real* __restrict__ Tu, Ops<r
 // Sums, per block, of the Gauss-weighted integrands of Sec. 4.4 plus conserved totals;
 // k_diag_final adds the block partials in a fixed order (deterministic).
 constexpr int NDIAG = 10;   // ke, ke_rho, enstrophy, mass, mom0..2, energy, l2sq, nonfinite
+constexpr int DIAG_L1 = 256;   // blocks of the first level of the partials' reduction
 
 template <int N, int DIM, int NV>
 __global__ void __launch_bounds__(Footprint<N, DIM, NV>::MAXT) k_diag(const double* __restrict__ U, const double* __restrict__ Tu,
@@ -415,12 +405,13 @@ __global__ void __launch_bounds__(Footprint<N, DIM, NV>::MAXT) k_diag(const doub
                 const double rho = su[pt];
                 const double vel[3] = {su[NP + pt] / rho, su[2 * NP + pt] / rho, su[3 * NP + pt] / rho};
                 const double q2 = vel[0] * vel[0] + vel[1] * vel[1] + vel[2] * vel[2];
-                double du[3][3];   // du[k][i] = d u_i / d x_k
+                double du[3][3] = {};   // du[k][i] = d u_i / d x_k, off-diagonal (the vorticity)
 #pragma unroll
                 for (int k = 0; k < 3; ++k)
 #pragma unroll
                     for (int i = 0; i < 3; ++i)
-                        du[k][i] = (vS[((1 + i) * DIM + k) * NP + pt] - vel[i] * vS[(0 * DIM + k) * NP + pt]) / rho;
+                        if (i != k)
+                            du[k][i] = (vS[((1 + i) * DIM + k) * NP + pt] - vel[i] * vS[(0 * DIM + k) * NP + pt]) / rho;
                 const double o0 = du[1][2] - du[2][1], o1 = du[2][0] - du[0][2], o2 = du[0][1] - du[1][0];
                 acc[0] += w * 0.5 * q2;
                 acc[1] += w * 0.5 * rho * q2;

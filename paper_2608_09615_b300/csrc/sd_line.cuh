@@ -470,26 +470,7 @@ __device__ __forceinline__ void line_vs(const LineGeo<real>& geo, const real* su
     }
 }
 
-// own interface gradient of component c on side s (0: face 2D, 1: face 2D+1) from the
-// loaded line g[] (BR1: Eq. v:e at the interface row; compact: minus (2/h) alpha (beta)
-// times the opposite-face correction on the d-component)
-template <typename real, int N, int NQ, int NV, int D, class ST>
-__device__ __forceinline__ real face_value(const LineGeo<real>& geo, int compact, int c, int s,
-                                           const real* g, const real* tro, const real* trn, int q) {
-    const OpTab<real, N>& op = c_op<real, N>;
-    real a = dotc<real, N>(op.L + (s ? N * N : 0), g);
-    int v, m;
-    comp_map<NV>(D, c, v, m);
-    if (compact && m == D) {
-        const int fo = 2 * D + (1 - s);
-        const int io = fo * ST::FS + v * NQ + q;
-        const real dop = real(0.5) * (trn[io] - tro[io]);
-        a = fma(-(s ? geo.corrR[D] : geo.corrL[D]), dop, a);
-    }
-    return a;
-}
-
-// shared prologue of the gradient, flux and closure kernels: own traces, then v^S
+// prologue of the closure kernels: own traces, then v^S (all components)
 template <typename real, int N, int DIM, int NV, class ST>
 __device__ __forceinline__ void prologue(const LineGeo<real>& geo, const LineId& id, bool live,
                                          real* su, real* tro, real* trn, real* vS) {
@@ -511,25 +492,6 @@ __device__ __forceinline__ void prologue(const LineGeo<real>& geo, const LineId&
         }
     }
     __syncthreads();
-}
-
-// own interface gradients of the two faces of direction D, written to the padded global
-// blocks out[f][GST] ([c][q] within a block)
-template <typename real, int N, int DIM, int NV, int D, class ST>
-__device__ __forceinline__ void grad_faces(const LineGeo<real>& geo, int compact, const real* vS,
-                                           const real* tro, const real* trn, real* out, int q) {
-    using LL = LineLayout<N, DIM, NV>;
-    constexpr int NP = LL::NP, NQ = LL::NQ, NG = LL::NG, GST = LL::GST;
-#pragma unroll
-    for (int c = 0; c < NG; ++c) {
-        int v, m;
-        comp_map<NV>(D, c, v, m);
-        real gl[N];
-#pragma unroll
-        for (int i = 0; i < N; ++i) gl[i] = vS[(v * DIM + m) * NP + lpt<N, D>(i, q)];
-        out[(2 * D) * GST + c * NQ + q] = face_value<real, N, NQ, NV, D, ST>(geo, compact, c, 0, gl, tro, trn, q);
-        out[(2 * D + 1) * GST + c * NQ + q] = face_value<real, N, NQ, NV, D, ST>(geo, compact, c, 1, gl, tro, trn, q);
-    }
 }
 
 // Residual kernels, per line (direction D, face point q): the line's u, its own face
@@ -585,7 +547,8 @@ __device__ __forceinline__ void prologue_res(const LineGeo<real>& geo, const Lin
     if constexpr (NV == 5) __syncthreads();
 }
 
-// residual form of grad_faces: normal components from u and the corrections (BR1:
+// own interface gradients of the two faces of direction D (written to the padded global
+// blocks out[f][GST], [c][q] within a block): normal components from u and the corrections (BR1:
 // L_s v^S; compact: the one-sided gradient keeps only the correction of face s, the
 // closed form of Eqs. aux:cmp:lr:2d), transverse components from the kept v^S
 template <typename real, int N, int DIM, int NV, int D>
