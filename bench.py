@@ -434,10 +434,11 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
             "config": {"workload": "TGV Re=1600 Ma=0.1 Pr=0.71, %dx%dx%d hex p=4 (%d DOF, 5 vars), "
-                                   "%s scheme, Roe + Sutherland, FP32 residual, FP64 SSPRK(5,4), "
+                                   "%s scheme, Roe + Sutherland, FP32 residual, SSPRK(5,4) with FP64 state, "
                                    "dt=%g" % (ne + (npts, args.scheme, DT)),
-                       "step": "one SSPRK(5,4) step = 5 residuals + FP64 stage updates; "
-                               "diagnostics once per timed window",
+                       "step": "one SSPRK(5,4) step = 5 residuals + 5 stage updates (FP32 stage "
+                               "increments, FP64 state update once per step); FP64 diagnostics once "
+                               "per timed window",
                        "l2": "inputs larger than L2 (FP32 state %.0f MB, FP64 state %.0f MB)"
                              % (5 * npts * 4 / 1e6, 5 * npts * 8 / 1e6),
                        "parallelism": "replicas" if world > 1 else "single GPU"},
