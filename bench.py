@@ -76,8 +76,8 @@ def residual_flops_per_element(n, nv=5, ng=9, dim=3):
 # DRAM traffic of one k_line_flux launch at 48^3 p=4 (FP32, compact), from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum; profiles/dram_residual_kernels_tgv48_p4_f32.md),
 # valid only while the kernel sources hash to the value recorded with it.
-FLUX_TRAFFIC = {"ne": 48, "bytes": 796176640 + 252943616,
-                "sources_sha256": "e1205fbe4807d5e4ef10fde0171102698ca060b08ea490a341de8ea6e5572a20"}
+FLUX_TRAFFIC = {"ne": 48, "bytes": 796335360 + 253035264,
+                "sources_sha256": "a09622cb15fb1beebb215fe8cf6072c867da72f71ace0f77318838e6163d44fe"}
 FLUX_SOURCES = ("paper_2608_09615_b300/csrc/sd_line.cuh", "paper_2608_09615_b300/csrc/sd_kernels.cuh")
 
 
