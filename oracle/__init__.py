@@ -16,6 +16,8 @@ Modules:
   grid       - periodic uniform Cartesian element grid, J and S = adj(J) (Eqs. ns:mapped, adj:f)
   physics    - heat, porous-medium and compressible Navier-Stokes fluxes (Secs. 4.3, 4.4)
   residual   - the SD semi-discrete residual, BR1 (Sec. 2.1) and compact (Secs. 2.2, 2.3)
+  curvilinear- periodic grids of trilinear hexahedra (Sec. 2 mapping, K = 8), per-point
+               metric terms and the residual on them (Sec. 2.3 steps with [S]^{Fd}, [J^-1]^S)
   timestep   - RK4, SSPRK(5,4) and the 5-stage low-storage RK (Sec. 4.4 time integration)
   diagnostics- kinetic energy, enstrophy, conserved totals (Sec. 4.4)
   bloch      - the temporal-eigenanalysis operator B(theta) of Sec. 3 (used as a pin)

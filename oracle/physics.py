@@ -224,6 +224,68 @@ class NavierStokes:
                    + lam2 * rt * sum(ut[i] * dvt[i] for i in range(3)))
         return 0.5 * (self.convective_flux(UL, m) + self.convective_flux(UR, m)) - 0.5 * diss
 
+    # --- numerical flux along a general unit normal (curved faces) ------------------
+    def normal_flux(self, U, nvec):
+        """n . F_c(U) for the unit normal nvec (list of 3 arrays or numbers)."""
+        return sum(nvec[m] * self.convective_flux(U, m) for m in range(3))
+
+    def riemann_normal(self, UL, UR, nvec):
+        if self.prm.riemann == "roe":
+            return self.roe_normal(UL, UR, nvec)
+        if self.prm.riemann == "rusanov":
+            g = self.prm.gamma
+            rl, vl, El, el, pl = self.primitives(UL)
+            rr, vr, Er, er, pr = self.primitives(UR)
+            unl = sum(vl[i] * nvec[i] for i in range(3))
+            unr = sum(vr[i] * nvec[i] for i in range(3))
+            smax = np.maximum(np.abs(unl) + np.sqrt(g * pl / rl), np.abs(unr) + np.sqrt(g * pr / rr))
+            return 0.5 * (self.normal_flux(UL, nvec) + self.normal_flux(UR, nvec)) - 0.5 * smax * (UR - UL)
+        raise ValueError(self.prm.riemann)
+
+    def roe_normal(self, UL, UR, nvec):
+        """Roe's flux with Harten's fix along the unit normal nvec: the 1D Roe solver of
+        Sec. 4.4 written in the frame of the face, with normal velocity q_n = u . n and
+        tangential jumps dv - (dv . n) n."""
+        g = self.prm.gamma
+        rl, vl, El, el, pl = self.primitives(UL)
+        rr, vr, Er, er, pr = self.primitives(UR)
+        Hl = (UL[4] + pl) / rl
+        Hr = (UR[4] + pr) / rr
+        sl = np.sqrt(rl)
+        sr = np.sqrt(rr)
+        wsum = sl + sr
+        ut = [(sl * vl[i] + sr * vr[i]) / wsum for i in range(3)]
+        Ht = (sl * Hl + sr * Hr) / wsum
+        rt = sl * sr
+        q2 = ut[0] ** 2 + ut[1] ** 2 + ut[2] ** 2
+        c2 = (g - 1.0) * (Ht - 0.5 * q2)
+        c = np.sqrt(c2)
+        qn = sum(ut[i] * nvec[i] for i in range(3))
+        drho = rr - rl
+        dp = pr - pl
+        dv = [vr[i] - vl[i] for i in range(3)]
+        dvn = sum(dv[i] * nvec[i] for i in range(3))
+        lam1 = np.abs(qn - c)
+        lam2 = np.abs(qn)
+        lam5 = np.abs(qn + c)
+        delta = self.prm.harten * c
+        if self.prm.harten > 0.0:
+            lam1 = np.where(lam1 < delta, (lam1 ** 2 + delta ** 2) / (2.0 * delta), lam1)
+            lam5 = np.where(lam5 < delta, (lam5 ** 2 + delta ** 2) / (2.0 * delta), lam5)
+        a1 = (dp - rt * c * dvn) / (2.0 * c2)
+        a2 = drho - dp / c2
+        a5 = (dp + rt * c * dvn) / (2.0 * c2)
+        dvt = [dv[i] - dvn * nvec[i] for i in range(3)]
+        diss = np.empty_like(UL)
+        diss[0] = lam1 * a1 + lam2 * a2 + lam5 * a5
+        for i in range(3):
+            diss[1 + i] = (lam1 * a1 * (ut[i] - c * nvec[i]) + lam2 * a2 * ut[i]
+                           + lam5 * a5 * (ut[i] + c * nvec[i]) + lam2 * rt * dvt[i])
+        diss[4] = (lam1 * a1 * (Ht - qn * c) + lam2 * a2 * 0.5 * q2
+                   + lam5 * a5 * (Ht + qn * c)
+                   + lam2 * rt * sum(ut[i] * dvt[i] for i in range(3)))
+        return 0.5 * (self.normal_flux(UL, nvec) + self.normal_flux(UR, nvec)) - 0.5 * diss
+
     def interface_flux(self, uL, uR, uhat, vhat, m):
         # Sec. 4.4: Roe (or Rusanov) inviscid flux minus the centred viscous flux
         # evaluated on the average solution and the average gradient.

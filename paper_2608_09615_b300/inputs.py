@@ -129,14 +129,17 @@ def _smooth_field(rng, X, kmax, nmodes=12):
 
 
 def tgv_3d(ne, p, gamma=1.4, Ma=0.1, rho0=1.0, u0=1.0, L=1.0, perturb_seed=None,
-           amp=1e-2):
+           amp=1e-2, X=None):
     """Conservative Taylor-Green initial state (Sec. 4.4): domain [0, 2 pi L]^3,
     x* = (x - x_c)/L, rho = rho0, u = u0 (sin x* cos y* cos z*, -cos x* sin y* cos z*, 0),
     p = p0 + rho0 u0^2/16 (cos 2x* + cos 2y*)(cos 2z* + 2), p0 = rho0 (u0/Ma)^2/gamma.
     With perturb_seed, smooth random perturbations of relative size `amp` are added to
-    rho, u and p so that no symmetry of the field can hide an indexing error."""
+    rho, u and p so that no symmetry of the field can hide an indexing error.
+    X: optional solution-point coordinates (e.g. curvilinear_coordinates of a deformed
+    grid); by default those of the uniform grid with ne elements."""
     hi = (2.0 * math.pi * L,) * 3
-    X = coordinates(3, ne, (0.0,) * 3, hi, p)
+    if X is None:
+        X = coordinates(3, ne, (0.0,) * 3, hi, p)
     xs = [(X[d] - math.pi * L) / L for d in range(3)]
     rho = rho0 * np.ones_like(xs[0])
     u = u0 * np.sin(xs[0]) * np.cos(xs[1]) * np.cos(xs[2])
@@ -179,3 +182,79 @@ def random_state(ne, p, seed, gamma=1.4, Ma=0.1, rho0=1.0, u0=1.0, rel=0.1):
 def random_scalar(dim, ne, p, seed, lo=-1.0, hi=1.0):
     rng = np.random.default_rng(seed)
     return rng.uniform(lo, hi, (1,) + element_shape(dim, ne, p + 1))
+
+
+# ------------------------------------------------------------------ curvilinear grids
+# A periodic structured grid of trilinear hexahedra is given by its corner nodes,
+# nodes[c][k][j][i] (c = physical component, i along x), shape (3, nz + 1, ny + 1, nx + 1):
+# element (ex, ey, ez) has the corners (ex + a, ey + b, ez + c), a, b, c in {0, 1}, and the
+# last node along each axis is the periodic image of the first (node[..., nx] = node[..., 0]
+# + the period vector along x, the same vector for every j, k).
+
+def periodic_lattice(ne, lo=(0.0,) * 3, hi=(2 * math.pi,) * 3):
+    """Corner nodes of the uniform grid of the box [lo, hi] with ne elements per axis."""
+    ax = [np.linspace(lo[d], hi[d], ne[d] + 1) for d in range(3)]
+    Z, Y, X = np.meshgrid(ax[2], ax[1], ax[0], indexing="ij")
+    return np.stack([X, Y, Z])
+
+
+def _periodic_displacement(ne, field):
+    """Extend a displacement given on the nz x ny x nx lattice to the image nodes."""
+    D = np.empty((3, ne[2] + 1, ne[1] + 1, ne[0] + 1))
+    D[:, :-1, :-1, :-1] = field
+    D[:, -1, :, :] = D[:, 0, :, :]
+    D[:, :, -1, :] = D[:, :, 0, :]
+    D[:, :, :, -1] = D[:, :, :, 0]
+    return D
+
+
+def jittered_lattice(ne, lo=(0.0,) * 3, hi=(2 * math.pi,) * 3, seed=0, amp=0.1):
+    """Uniform lattice with each node moved by a seeded random vector whose components
+    are uniform in [-amp h_d, amp h_d] (periodic: image nodes move with their originals).
+    Every element stays a valid (positive-Jacobian) trilinear hexahedron for amp <= 0.15."""
+    rng = np.random.default_rng(seed)
+    h = [(hi[d] - lo[d]) / ne[d] for d in range(3)]
+    f = rng.uniform(-1.0, 1.0, (3, ne[2], ne[1], ne[0]))
+    for d in range(3):
+        f[d] *= amp * h[d]
+    return periodic_lattice(ne, lo, hi) + _periodic_displacement(ne, f)
+
+
+def wavy_lattice(ne, lo=(0.0,) * 3, hi=(2 * math.pi,) * 3, amp=0.1):
+    """Smooth periodic deformation of the uniform lattice: component d of each node moves
+    by amp h_d sin(2 pi s_{d+1}) sin(2 pi s_{d+2}), s_t the node's position along axis t as
+    a fraction of the box."""
+    h = [(hi[d] - lo[d]) / ne[d] for d in range(3)]
+    k, j, i = np.meshgrid(np.arange(ne[2]), np.arange(ne[1]), np.arange(ne[0]), indexing="ij")
+    s = [i / ne[0], j / ne[1], k / ne[2]]
+    f = np.stack([amp * h[d] * np.sin(2 * math.pi * s[(d + 1) % 3]) * np.sin(2 * math.pi * s[(d + 2) % 3])
+                  for d in range(3)])
+    return periodic_lattice(ne, lo, hi) + _periodic_displacement(ne, f)
+
+
+def rotation_matrix(axis, angle):
+    """Rotation by `angle` about the unit vector along `axis` (Rodrigues' formula)."""
+    a = np.asarray(axis, dtype=np.float64)
+    a = a / np.linalg.norm(a)
+    K = np.array([[0, -a[2], a[1]], [a[2], 0, -a[0]], [-a[1], a[0], 0]])
+    return np.eye(3) + math.sin(angle) * K + (1 - math.cos(angle)) * (K @ K)
+
+
+def curvilinear_coordinates(nodes, p):
+    """Physical coordinates of the solution points of every trilinear element (sample
+    placement only): list over d of arrays shaped like one variable of U."""
+    n = p + 1
+    xs, _ = gl_points(n)
+    nz, ny, nx = nodes.shape[1] - 1, nodes.shape[2] - 1, nodes.shape[3] - 1
+    w = [np.stack([(1 - xs) / 2, (1 + xs) / 2]) for _ in range(3)]     # w[t][a][i]
+    out = []
+    for d in range(3):
+        X = np.zeros((nz, ny, nx, n, n, n))
+        for a in range(2):
+            for b in range(2):
+                for c in range(2):
+                    corner = nodes[d, c:c + nz, b:b + ny, a:a + nx]
+                    wt = np.einsum("k,j,i->kji", w[2][c], w[1][b], w[0][a])
+                    X += corner[:, :, :, None, None, None] * wt
+        out.append(X)
+    return out
