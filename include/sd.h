@@ -119,6 +119,31 @@ typedef struct sd_ctx sd_ctx;
 sd_status sd_init(const sd_mesh* mesh, int p, sd_scheme scheme, const sd_physics* phys,
                   sd_precision prec, void* stream, sd_ctx** out);
 
+/* Create a context on a periodic grid of curved (trilinear) hexahedra: the element map of
+ * Sec. 2 with K = 8 corner nodes, the transformed equations Eqs. ns:mapped / adj:f and the
+ * steps of Sec. 2.3 with the metric terms taken point by point (row d of S = adj(dx/dxi)
+ * at the flux points of family d, J^-1 at the solution points).
+ *   mesh: dim must be 3; ne gives the element counts; lo / hi are ignored.
+ *   nodes: host array of 3 * (ne[2]+1) * (ne[1]+1) * (ne[0]+1) doubles, read only during
+ *     the call: nodes[((c*(nz+1) + k)*(ny+1) + j)*(nx+1) + i] is component c (x, y, z) of
+ *     corner node (i, j, k). Element (ex, ey, ez) has the corners (ex+a, ey+b, ez+c), a, b, c
+ *     in {0, 1}; xi runs along i, eta along j, zeta along k. The last node along each axis is
+ *     the periodic image of the first: node(nx, j, k) - node(0, j, k) must be the same
+ *     vector for every j, k (likewise along y and z), else SD_EINVAL.
+ *   Every element needs a positive Jacobian at its solution points, else SD_EINVAL.
+ * The other arguments are those of sd_init. State layout, sd_residual, sd_residual_host,
+ * sd_rk_step and sd_diagnostics (Gauss quadrature with weights J w_i w_j w_k; volume =
+ * the domain's) work as on a Cartesian grid. The interior penalty uses, per interface,
+ * 1/h = |A_f| / min(V_{e-}, V_{e+}) (A_f: integral of the area vector over the face,
+ * V: element volumes) along the face's unit normal (Sec. 3). Not available here
+ * (SD_EUNSUPPORTED): the learned closure and per-element fluxes, and the porous-medium
+ * diffusivity at the solution points. */
+sd_status sd_init_curvilinear(const sd_mesh* mesh, const double* nodes, int p, sd_scheme scheme,
+                              const sd_physics* phys, sd_precision prec, void* stream, sd_ctx** out);
+
+/* 1 if the context was made by sd_init_curvilinear, else 0. */
+int sd_is_curvilinear(const sd_ctx* ctx);
+
 void sd_destroy(sd_ctx* ctx);
 sd_status sd_set_stream(sd_ctx* ctx, void* stream);
 

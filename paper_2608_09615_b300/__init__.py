@@ -61,7 +61,8 @@ EXPORTS = ("sd_init", "sd_destroy", "sd_set_stream", "sd_state_size", "sd_nvar",
            "sd_mlp_param_count", "sd_mlp_cast", "sd_mlp_forward", "sd_mlp_loss", "sd_mlp_backward",
            "sd_mlp_adam", "sd_residual_f32_noalloc", "sd_set_flux_tau", "sd_closure_data",
            "sd_filter_matrix", "sd_filter_project", "sd_closure_targets", "sd_colstats",
-           "sd_standardise", "sd_unstandardise", "sd_closure_enable")
+           "sd_standardise", "sd_unstandardise", "sd_closure_enable", "sd_init_curvilinear",
+           "sd_is_curvilinear")
 KERNEL_CLASSES = ("trace", "grad", "flux_div", "other", "face")
 
 _lib_handle = None
@@ -80,6 +81,11 @@ def load_library(path=LIB_PATH):
     lib.sd_init.argtypes = [ctypes.POINTER(_Mesh), I, I, ctypes.POINTER(_Physics), I, P,
                             ctypes.POINTER(P)]
     lib.sd_init.restype = I
+    lib.sd_init_curvilinear.argtypes = [ctypes.POINTER(_Mesh), P, I, I, ctypes.POINTER(_Physics), I, P,
+                                        ctypes.POINTER(P)]
+    lib.sd_init_curvilinear.restype = I
+    lib.sd_is_curvilinear.argtypes = [P]
+    lib.sd_is_curvilinear.restype = I
     lib.sd_destroy.argtypes = [P]
     lib.sd_destroy.restype = None
     lib.sd_set_stream.argtypes = [P, P]
@@ -202,6 +208,27 @@ def sd_init(dim, ne, lo, hi, p, scheme, physics, precision, stream=None):
     return out
 
 
+def sd_init_curvilinear(nodes, p, scheme, physics, precision, stream=None):
+    """Create a context on a periodic grid of trilinear hexahedra (sd_init_curvilinear).
+    nodes: array (3, nz+1, ny+1, nx+1) of corner-node coordinates, the last node along each
+    axis being the periodic image of the first. Returns an opaque handle (c_void_p)."""
+    import numpy as np
+    lib = load_library()
+    nodes = np.ascontiguousarray(nodes, dtype=np.float64)
+    if nodes.ndim != 4 or nodes.shape[0] != 3 or min(nodes.shape[1:]) < 2:
+        raise ValueError("nodes must have shape (3, nz+1, ny+1, nx+1)")
+    ne = [nodes.shape[3] - 1, nodes.shape[2] - 1, nodes.shape[1] - 1]
+    m = _Mesh(3, (ctypes.c_int * 3)(*ne), (ctypes.c_double * 3)(0.0, 0.0, 0.0),
+              (ctypes.c_double * 3)(1.0, 1.0, 1.0))
+    ph = physics.to_c()
+    out = ctypes.c_void_p()
+    st = lib.sd_init_curvilinear(ctypes.byref(m), ctypes.c_void_p(nodes.ctypes.data), int(p), SCHEMES[scheme],
+                                 ctypes.byref(ph), PRECISIONS[precision], _stream_handle(stream),
+                                 ctypes.byref(out))
+    _check(st, "sd_init_curvilinear")
+    return out
+
+
 def sd_residual_f32_noalloc(dim, ne, lo, hi, p, scheme, physics, U, R, stream=None):
     """FP32 residual through the allocation-free entry point (no context, no device
     allocation; the library's static scratch is shared by all calls). U, R: contiguous
@@ -275,17 +302,35 @@ class SD:
     """One SD residual context (grid, p, scheme, physics, residual precision)."""
 
     def __init__(self, dim, ne, lo, hi, p, scheme="compact", physics=None, precision="f32",
-                 stream=None):
+                 stream=None, nodes=None):
+        """nodes: optional corner nodes (3, nz+1, ny+1, nx+1) of a periodic grid of
+        trilinear hexahedra (then dim must be 3, ne must match the nodes, lo / hi are
+        ignored); without it the grid is the uniform Cartesian box [lo, hi)."""
         import torch
         self.physics = physics if physics is not None else Physics()
         self.dim, self.ne, self.p, self.n = dim, tuple(ne), p, p + 1
         self.scheme, self.precision = scheme, precision
         self.dtype = torch.float32 if precision == "f32" else torch.float64
-        self._ctx = sd_init(dim, ne, lo, hi, p, scheme, self.physics, precision, stream)
+        if nodes is not None:
+            if dim != 3 or tuple(ne) != (nodes.shape[3] - 1, nodes.shape[2] - 1, nodes.shape[1] - 1):
+                raise ValueError("a curvilinear grid needs dim = 3 and ne matching the nodes")
+            self._ctx = sd_init_curvilinear(nodes, p, scheme, self.physics, precision, stream)
+        else:
+            self._ctx = sd_init(dim, ne, lo, hi, p, scheme, self.physics, precision, stream)
         lib = load_library()
         self.numel = int(lib.sd_state_size(self._ctx))
         self.nvar = int(lib.sd_nvar(self._ctx))
         self.shape = (self.nvar,) + tuple(reversed(tuple(ne))) + (self.n,) * dim
+
+    @classmethod
+    def curvilinear(cls, nodes, p, scheme="compact", physics=None, precision="f32", stream=None):
+        """Context on the periodic trilinear-hexahedron grid with corner nodes `nodes`."""
+        ne = (nodes.shape[3] - 1, nodes.shape[2] - 1, nodes.shape[1] - 1)
+        return cls(3, ne, (0.0,) * 3, (1.0,) * 3, p, scheme, physics, precision, stream, nodes=nodes)
+
+    @property
+    def curved(self):
+        return bool(load_library().sd_is_curvilinear(self._ctx))
 
     def set_stream(self, stream):
         _check(load_library().sd_set_stream(self._ctx, _stream_handle(stream)), "sd_set_stream")

@@ -267,9 +267,10 @@ static void free_all(sd_ctx* c) {
     }
     if (c->cl_tmode) cudaFree(c->cl_tmode);
     void* ptrs[] = {c->Tu, c->Tg, c->Fh, c->S, c->K, c->rA, c->rB, c->rC, c->rX, c->dW,
-                    c->partial, c->partial2, c->dsum, c->hU, c->hR};
+                    c->partial, c->partial2, c->dsum, c->hU, c->hR, c->cih, c->cvs, c->cTg, c->cgeo64};
     for (void* p : ptrs)
         if (p) cudaFree(p);
+    if (c->cgeo && c->cgeo != (void*)c->cgeo64) cudaFree(c->cgeo);
     if (c->Tu64 && (void*)c->Tu64 != c->Tu) cudaFree(c->Tu64);
 }
 
@@ -464,6 +465,38 @@ extern "C" void sd_destroy(sd_ctx* c) {
     free(c);
 }
 
+extern "C" sd_status sd_init_curvilinear(const sd_mesh* mesh, const double* nodes, int p, sd_scheme scheme,
+                                         const sd_physics* phys, sd_precision prec, void* stream, sd_ctx** out) {
+    g_err[0] = 0;
+    if (!mesh || !nodes || !phys || !out) { sdi_set_error("null argument"); return SD_EINVAL; }
+    *out = nullptr;
+    if (mesh->dim != 3) { sdi_set_error("curvilinear grids are 3D"); return SD_EUNSUPPORTED; }
+    if (phys->kind == SD_PME && phys->pme_coef == SD_PME_COEF_SOLUTION) {
+        sdi_set_error("the solution-point diffusivity variant is available on Cartesian grids only");
+        return SD_EUNSUPPORTED;
+    }
+    for (int d = 0; d < 3; ++d)
+        if (mesh->ne[d] < 1) { sdi_set_error("ne[%d] must be >= 1", d); return SD_EINVAL; }
+    // the Cartesian box fields are not used on a curved grid: give the context a unit box
+    sd_mesh m = *mesh;
+    for (int d = 0; d < 3; ++d) {
+        m.lo[d] = 0.0;
+        m.hi[d] = 1.0;
+    }
+    sd_ctx* c = nullptr;
+    sd_status s = sd_init(&m, p, scheme, phys, prec, stream, &c);
+    if (s != SD_OK) return s;
+    s = sdi_curv_setup(c, nodes);
+    if (s != SD_OK) {
+        sd_destroy(c);
+        return s;
+    }
+    *out = c;
+    return SD_OK;
+}
+
+extern "C" int sd_is_curvilinear(const sd_ctx* c) { return c ? c->curv : 0; }
+
 extern "C" sd_status sd_set_stream(sd_ctx* c, void* stream) {
     if (!c) return SD_EINVAL;
     c->stream = (cudaStream_t)stream;
@@ -490,6 +523,10 @@ static bool overlap(const void* a, const void* b, size_t bytes) {
 }
 
 static sd_status residual_any(sd_ctx* c, const void* U, void* R, int offset_in = 0) {
+    if (c->curv) {
+        if (c->prec == SD_F32) return sdi_curv_residual_f32(c, (const float*)U, (float*)R, offset_in);
+        return sdi_curv_residual_f64(c, (const double*)U, (double*)R, offset_in);
+    }
     if (c->prec == SD_F32) return sdi_residual_f32(c, (const float*)U, (float*)R, offset_in);
     return sdi_residual_f64(c, (const double*)U, (double*)R, offset_in);
 }
@@ -577,7 +614,7 @@ static sd_status residual_host_slabs(sd_ctx* c, const void* U_host, void* R_host
 
 extern "C" sd_status sd_residual_host(sd_ctx* c, const void* U_host, void* R_host) {
     if (!c || !U_host || !R_host) { sdi_set_error("null argument"); return SD_EINVAL; }
-    if (c->s_h2d && !c->closure_on && c->ne[2] >= 4) return residual_host_slabs(c, U_host, R_host);
+    if (c->s_h2d && !c->closure_on && !c->curv && c->ne[2] >= 4) return residual_host_slabs(c, U_host, R_host);
     const size_t bytes = c->nstate * c->esize;
     CK(cudaMemcpyAsync(c->hU, U_host, bytes, cudaMemcpyHostToDevice, c->stream));
     const sd_status st = residual_any(c, c->hU, c->hR);
@@ -852,6 +889,20 @@ __global__ void k_diag_final(const double* __restrict__ partial, int nblocks,
         for (int k = 0; k < NDIAG; ++k) out[k] = red[k][0];
 }
 
+// two-level deterministic reduction of the nb rows of diagnostics partial sums
+static sd_status diag_reduce(sd_ctx* c, int nb) {
+    const int chunk = (nb + DIAG_L1 - 1) / DIAG_L1;
+    const int nb1 = (nb + chunk - 1) / chunk;
+    sdi_prof_begin(c, SD_K_OTHER);
+    k_diag_reduce<<<nb1, 256, 0, c->stream>>>(c->partial, nb, chunk, c->partial2);
+    sdi_prof_end(c, SD_K_OTHER);
+    sdi_prof_begin(c, SD_K_OTHER);
+    k_diag_final<<<1, 256, 0, c->stream>>>(c->partial2, nb1, c->dsum);
+    sdi_prof_end(c, SD_K_OTHER);
+    CK(cudaGetLastError());
+    return SD_OK;
+}
+
 template <int N, int DIM, int NV>
 static sd_status diag_impl(sd_ctx* c, const double* U) {
     using FP = Footprint<N, DIM, NV>;
@@ -870,16 +921,7 @@ static sd_status diag_impl(sd_ctx* c, const double* U) {
     sdi_prof_begin(c, SD_K_OTHER);
     k_diag<N, DIM, NV><<<nb, threads, smem, c->stream>>>(U, c->Tu64, ops, g, c->dW, c->J, c->partial);
     sdi_prof_end(c, SD_K_OTHER);
-    const int chunk = (nb + DIAG_L1 - 1) / DIAG_L1;
-    const int nb1 = (nb + chunk - 1) / chunk;
-    sdi_prof_begin(c, SD_K_OTHER);
-    k_diag_reduce<<<nb1, 256, 0, c->stream>>>(c->partial, nb, chunk, c->partial2);
-    sdi_prof_end(c, SD_K_OTHER);
-    sdi_prof_begin(c, SD_K_OTHER);
-    k_diag_final<<<1, 256, 0, c->stream>>>(c->partial2, nb1, c->dsum);
-    sdi_prof_end(c, SD_K_OTHER);
-    CK(cudaGetLastError());
-    return SD_OK;
+    return diag_reduce(c, nb);
 }
 
 template <int N>
@@ -893,7 +935,10 @@ static sd_status diag_n(sd_ctx* c, const double* U) {
 extern "C" sd_status sd_diagnostics(sd_ctx* c, const double* U64, double t, sd_diag* out) {
     if (!c || !U64 || !out) { sdi_set_error("null argument"); return SD_EINVAL; }
     sd_status s;
-    switch (c->n) {
+    if (c->curv) {
+        s = sdi_curv_diag_partials(c, U64);
+        if (s == SD_OK) s = sdk::diag_reduce(c, c->diag_nb);
+    } else switch (c->n) {
         case 2: s = sdk::diag_n<2>(c, U64); break;
         case 3: s = sdk::diag_n<3>(c, U64); break;
         case 4: s = sdk::diag_n<4>(c, U64); break;
@@ -921,7 +966,7 @@ extern "C" sd_status sd_diagnostics(sd_ctx* c, const double* U64, double t, sd_d
     out->l2sq = h[8];
     double vol = 1.0;
     for (int d = 0; d < c->dim; ++d) vol *= c->hi[d] - c->lo[d];
-    out->volume = vol;
+    out->volume = c->curv ? c->curv_volume : vol;
     out->nonfinite = h[9] != 0.0 ? 1 : 0;
     if (out->nonfinite) {
         sdi_set_error("state holds %g non-finite points", h[9]);
@@ -934,12 +979,14 @@ extern "C" sd_status sd_diagnostics(sd_ctx* c, const double* U64, double t, sd_d
 extern "C" sd_status sd_set_flux_tau(sd_ctx* c, const float* tau) {
     if (!c) { sdi_set_error("null argument"); return SD_EINVAL; }
     if (c->nvar != 5 && tau) { sdi_set_error("a per-element flux needs Navier-Stokes"); return SD_EUNSUPPORTED; }
+    if (c->curv && tau) { sdi_set_error("a per-element flux is available on Cartesian grids only"); return SD_EUNSUPPORTED; }
     c->tau = tau;
     return SD_OK;
 }
 
 extern "C" sd_status sd_closure_data(sd_ctx* c, const void* U, float* X, double* means) {
     if (!c || !U || (!X && !means)) { sdi_set_error("null argument"); return SD_EINVAL; }
+    if (c->curv) { sdi_set_error("closure data are available on Cartesian grids only"); return SD_EUNSUPPORTED; }
     if (c->prec == SD_F32) return sdi_closure_data_f32(c, (const float*)U, X, means);
     return sdi_closure_data_f64(c, (const double*)U, X, means);
 }
@@ -980,6 +1027,7 @@ extern "C" sd_status sd_closure_enable(sd_ctx* c, const void* Wb, const float* P
     }
     if (!P || !mu_x || !sig_x || !mu_t || !sig_t) { sdi_set_error("null argument"); return SD_EINVAL; }
     if (c->nvar != 5) { sdi_set_error("the closure needs Navier-Stokes"); return SD_EUNSUPPORTED; }
+    if (c->curv) { sdi_set_error("the closure is available on Cartesian grids only"); return SD_EUNSUPPORTED; }
     if (!c->cl_X) {
         const size_t E = (size_t)c->nelem;
         bool ok = cudaMalloc((void**)&c->cl_X, E * 64 * sizeof(float)) == cudaSuccess &&

@@ -74,6 +74,15 @@ struct sd_ctx {
     const void* cl_Wb;       // caller-owned network: BF16 weights, FP32 parameters,
     const float* cl_P;       //   input and output standardisation
     const float *cl_mux, *cl_sgx, *cl_mut, *cl_sgt;
+    // curvilinear grids (periodic trilinear hexahedra), set up by sd_init_curvilinear
+    int curv;
+    void* cgeo;              // map coefficients c1..c7 [nelem][24] in the residual precision
+    double* cgeo64;          // the same in FP64 (diagnostics; == cgeo when prec is F64)
+    void* cih;               // interior-penalty 1/h of the -d face of each element [nelem][3]
+    void* cvs;               // v^S [nelem][nvar][3][n^3]
+    void* cTg;               // own interface gradients [nelem][6][nvar][3][n^2]
+    double curv_volume;      // volume of the periodic domain (sum of the element volumes)
+    int diag_nb;             // rows of `partial` written by the last diagnostics launch
     // profiling and launch accounting
     long long launches;
     int prof_on;
@@ -99,6 +108,11 @@ sd_status sdi_residual_phase_f32(sd_ctx* c, const float* U, float* R, int phase,
                                  cudaStream_t stream);
 sd_status sdi_residual_phase_f64(sd_ctx* c, const double* U, double* R, int phase, int e_begin, int e_end,
                                  cudaStream_t stream);
+// curvilinear grids: set-up from the corner nodes, residual, diagnostics partial sums
+sd_status sdi_curv_setup(sd_ctx* c, const double* nodes);
+sd_status sdi_curv_residual_f32(sd_ctx* c, const float* U, float* R, int offset_in);
+sd_status sdi_curv_residual_f64(sd_ctx* c, const double* U, double* R, int offset_in);
+sd_status sdi_curv_diag_partials(sd_ctx* c, const double* U64);
 sd_status sdi_upload_f32(const sd_ctx* c);
 sd_status sdi_upload_f64(const sd_ctx* c);
 // closure data of a state: features X [nelem][64] and/or flux means [nelem][15] (either NULL)
