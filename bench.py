@@ -73,6 +73,33 @@ def residual_flops_per_element(n, nv=5, ng=9, dim=3):
             "grad": trace + vs + nf * ng * nq * (sw + 2)}
 
 
+def curv_flops_per_element(n, nv=5):
+    """Algorithmic FP32 flops per element of the curved-grid NS residual kernels (FMA = 2
+    flops; a 1D sweep of length n costs 2n - 1). Metric terms from the trilinear map: one
+    row of S = 2 bilinear tangents (6 x 7 flops) and a cross product (9); J = 3 tangents,
+    a cross and a dot (77).
+    k_ctrace: the 6 face traces of every variable.
+    k_cgrad: J^-1 at the solution points; per family the row of S and u^{F,C} at its flux
+    points and the 3 nv derivative sums sum_f M (u S_m); the 6 faces' 3 nv own interface
+    gradients (compact: one coefficient sum_i L J^-1 M and one row of S per face point).
+    k_cface: the 3 faces owned by the element, per point: the row of S, unit normal, the
+    penalty, averages, Roe along the normal (~180) and the full viscous flux (~110).
+    k_cflux: J^-1; per family at the n - 1 interior flux points the extrapolated state and
+    3 nv gradient components, the row of S and S . (F_c - F_v) (~140); the divergence of all
+    n + 1 flux points; the J^-1 scaling."""
+    npnt, nq, nfp = n ** 3, n ** 2, (n + 1) * n ** 2
+    sw = 2 * n - 1
+    row, jac = 51, 78
+    trace = 6 * nv * nq * sw
+    fam_grad = nfp * row + nfp * nv * sw + 2 * nv * nq + 3 * nv * npnt * (3 * (n + 1) + 1)
+    grad = npnt * jac + 3 * fam_grad + 3 * nv * npnt + 6 * 3 * nv * nq * sw + 6 * nq * (3 * n + row) \
+        + 6 * 3 * nv * nq * 3
+    face = 3 * nq * (row + 10 + 6 * nv + 8 * nv + 180 + 110)
+    fam_flux = (n - 1) * nq * (4 * nv * sw + row + 140) + nv * npnt * (2 * (n + 1))
+    flux = npnt * jac + 3 * fam_flux + nv * npnt
+    return {"trace": trace, "grad": grad, "face": face, "flux": flux}
+
+
 # DRAM traffic of one k_line_flux launch at 48^3 p=4 (FP32, compact), from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum; profiles/dram_residual_kernels_tgv48_p4_f32.md),
 # valid only while the kernel sources hash to the value recorded with it.
@@ -237,6 +264,52 @@ def residual_rate(sd, torch, dim, ne, p, scheme, phys, precision, U, reps=10, lo
     return {"ms": ms, "dof_per_s": npts / (ms * 1e-3), "dof": npts, "finite": ok}
 
 
+def curvilinear_rate(sd, torch, ne, p, precision, fp32_peak, amp=0.15, reps=10):
+    """The Taylor-Green residual on a curved grid: the 48^3 box with every node displaced
+    by the smooth periodic field of inputs.wavy_lattice (amplitude 0.15 h). The state is
+    the perturbed Taylor-Green field sampled at the uniform-grid positions (a smooth field;
+    the time does not depend on the values). ms per sd_residual (CUDA events), per-kernel
+    times from the context's profiling events, and the ALU roofline of the dominant kernel
+    and of the whole residual against the algorithmic flops of curv_flops_per_element."""
+    nodes = inputs.wavy_lattice(ne, (0.0,) * 3, (2 * math.pi,) * 3, amp=amp)
+    ctx = sd.SD.curvilinear(nodes, p, "compact", sd.Physics(kind="ns"), precision)
+    Ug = torch.from_numpy(inputs.tgv_3d(ne, p, perturb_seed=0)).to("cuda", ctx.dtype)
+    R = torch.empty_like(Ug)
+    for _ in range(2):
+        ctx.residual(Ug, R)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        ctx.residual(Ug, R)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    ctx.profile(True)
+    for _ in range(reps):
+        ctx.residual(Ug, R)
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    ok = bool(torch.isfinite(R).all())
+    ctx.close()
+    kms = {k: prof[k][0] / max(prof[k][1], 1) for k in ("trace", "grad", "face", "flux_div")}
+    fl = curv_flops_per_element(p + 1)
+    fl["flux_div"] = fl.pop("flux")
+    nelem = int(np.prod(ne))
+    npts = nelem * (p + 1) ** 3
+    top = max(kms, key=kms.get)
+    names = {"trace": "k_ctrace", "grad": "k_cgrad", "face": "k_cface", "flux_div": "k_cflux"}
+    ach = fl[top] * nelem / (kms[top] * 1e-3) / 1e12
+    res = sum(fl.values()) * nelem / (sum(kms.values()) * 1e-3) / 1e12
+    return {"workload": "TGV Re=1600 on %dx%dx%d wavy trilinear hexahedra (node displacement %.2f h), p=%d, "
+                        "compact, %s residual" % (ne + (amp, p, precision.upper())),
+            "ms": ms, "dof_per_s": npts / (ms * 1e-3), "finite": ok,
+            "kernels_ms": kms, "flops_per_element": fl,
+            "roofline": {"bound": "alu", "kernel": names[top], "achieved": ach, "peak": fp32_peak,
+                         "unit": "TFLOP/s", "frac": ach / fp32_peak,
+                         "residual_alu_tflops": res, "residual_frac": res / fp32_peak}}
+
+
 def other_configs(sd, torch):
     """Residual rates on the other workloads the method is run on: 3D heat (32^3, p = 3
     and 4, nu = 0.01), the Taylor-Green grid with the BR1 scheme, Taylor-Green Re = 5000 on
@@ -267,7 +340,11 @@ def other_configs(sd, torch):
 
 
 def residual_only(sd, torch, args, ne, lo, hi, phys):
-    ctx = sd.SD(3, ne, lo, hi, P, args.scheme, phys, args.precision)
+    if args.wavy > 0:
+        nodes = inputs.wavy_lattice(ne, lo, hi, amp=args.wavy)
+        ctx = sd.SD.curvilinear(nodes, P, args.scheme, phys, args.precision)
+    else:
+        ctx = sd.SD(3, ne, lo, hi, P, args.scheme, phys, args.precision)
     npts = int(np.prod(ne)) * (P + 1) ** 3
     U = torch.from_numpy(inputs.tgv_3d(ne, P, perturb_seed=0)).to("cuda", ctx.dtype)
     R = torch.empty_like(U)
@@ -280,7 +357,7 @@ def residual_only(sd, torch, args, ne, lo, hi, phys):
     ctx.close()
     out = {k: {"ms_per_launch": ms / max(n, 1), "launches": n} for k, (ms, n) in prof.items() if n}
     tot = sum(v["ms_per_launch"] for v in out.values())
-    print(json.dumps({"grid": ne, "p": P, "precision": args.precision, "scheme": args.scheme,
+    print(json.dumps({"grid": ne, "p": P, "precision": args.precision, "scheme": args.scheme, "wavy": args.wavy,
                       "kernels": out, "residual_ms": tot, "dof_per_s": npts / (tot * 1e-3)}))
 
 
@@ -298,6 +375,8 @@ def main():
                     help="only evaluate K residuals (FP32 unless --precision f64) and print the "
                          "per-kernel CUDA-event times; the small command used for ncu captures")
     ap.add_argument("--precision", default="f32", choices=["f32", "f64"])
+    ap.add_argument("--wavy", type=float, default=0.0, metavar="AMP",
+                    help="with --residual-only: the curved grid whose nodes move by AMP h (wavy_lattice)")
     ap.add_argument("--no-other-configs", action="store_true",
                     help="skip the residual rates of the other workloads")
     args = ap.parse_args()
@@ -415,9 +494,10 @@ def main():
     res64_ms = e0.elapsed_time(e1) / nrep64
     ctx64.close()
 
-    others = None
+    others = curv = None
     if rank == 0 and not args.no_other_configs:
         others = other_configs(sd, torch)
+        curv = curvilinear_rate(sd, torch, ne, P, "f32", fp32_peak)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -460,6 +540,7 @@ def main():
             "residual_dof_per_s": {"f32": npts / (res32_ms * 1e-3), "f64": npts / (res64_ms * 1e-3),
                                    "f32_ms": res32_ms, "f64_ms": res64_ms},
             "other_configs_residual": others,
+            "curvilinear": curv,
             "e2e": {"value": npts / e2e_s, "unit": UNIT, "call": "sd_residual_host (FP32)",
                     "h2d_bytes_per_step": 5 * npts * 4, "d2h_bytes_per_step": 5 * npts * 4},
             "gpu_launches": launches,

@@ -47,24 +47,29 @@ struct COps {
     real xf[N + 1];
 };
 
-template <int N>
-__device__ __forceinline__ int cpow(int d) {
-    return d == 0 ? 1 : (d == 1 ? N : N * N);
-}
 
-// point index of position i along direction d on the line with face index q
-template <int N>
-__device__ __forceinline__ int cpt(int d, int i, int q) {
-    const int lo = cpow<N>(d);
+// Direction-specialised index helpers: D is a template argument wherever a loop runs over
+// one family, so strides are constants and no small array is indexed at run time.
+template <int N, int D>
+__device__ __forceinline__ int cpt(int i, int q) {
+    constexpr int lo = D == 0 ? 1 : (D == 1 ? N : N * N);
     return (q % lo) + lo * i + lo * N * (q / lo);
 }
 
-// reference coordinates (xi, eta, zeta) of flux point f of family d on line q (transverse
+// position along D and line index q of solution point pt
+template <int N, int D>
+__device__ __forceinline__ void line_of(int pt, int& i, int& q) {
+    constexpr int lo = D == 0 ? 1 : (D == 1 ? N : N * N);
+    i = (pt / lo) % N;
+    q = (pt % lo) + lo * (pt / (lo * N));
+}
+
+// reference coordinates (xi, eta, zeta) of flux point f of family D on line q (transverse
 // coordinates at the solution points; the lower transverse axis runs fastest in q)
-template <typename real, int N>
-__device__ __forceinline__ void flux_point_coords(const COps<real, N>& o, int d, int f, int q, real r[3]) {
-    const int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
-    r[d] = o.xf[f];
+template <typename real, int N, int D>
+__device__ __forceinline__ void flux_point_coords(const COps<real, N>& o, int f, int q, real r[3]) {
+    constexpr int t1 = D == 0 ? 1 : 0, t2 = D == 2 ? 1 : 2;
+    r[D] = o.xf[f];
     r[t1] = o.xs[q % N];
     r[t2] = o.xs[q / N];
 }
@@ -76,15 +81,15 @@ __device__ __forceinline__ void solution_point_coords(const COps<real, N>& o, in
     r[2] = o.xs[pt / (N * N)];
 }
 
-// tangents a[t][k] = d x_k / d xi_t of the trilinear map with coefficients c (c1..c7)
-template <typename real>
-__device__ __forceinline__ void tangents(const real* c, const real r[3], real a[3][3]) {
+// tangent a_t[k] = d x_k / d xi_t of the trilinear map with coefficients c (c1..c7)
+template <typename real, int T>
+__device__ __forceinline__ void tangent(const real* c, const real r[3], real a[3]) {
     const real x = r[0], y = r[1], z = r[2];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        a[0][k] = c[k] + c[9 + k] * y + c[15 + k] * z + c[18 + k] * (y * z);
-        a[1][k] = c[3 + k] + c[9 + k] * x + c[12 + k] * z + c[18 + k] * (x * z);
-        a[2][k] = c[6 + k] + c[12 + k] * y + c[15 + k] * x + c[18 + k] * (x * y);
+        if (T == 0) a[k] = c[k] + c[9 + k] * y + c[15 + k] * z + c[18 + k] * (y * z);
+        if (T == 1) a[k] = c[3 + k] + c[9 + k] * x + c[12 + k] * z + c[18 + k] * (x * z);
+        if (T == 2) a[k] = c[6 + k] + c[12 + k] * y + c[15 + k] * x + c[18 + k] * (x * y);
     }
 }
 
@@ -95,20 +100,23 @@ __device__ __forceinline__ void cross3(const real* u, const real* v, real* w) {
     w[2] = u[0] * v[1] - u[1] * v[0];
 }
 
-// row d of S = adj(dx/dxi) at reference point r
-template <typename real>
-__device__ __forceinline__ void metric_row(const real* c, const real r[3], int d, real S[3]) {
-    real a[3][3];
-    tangents(c, r, a);
-    cross3(a[(d + 1) % 3], a[(d + 2) % 3], S);
+// row D of S = adj(dx/dxi) at reference point r: a_{D+1} x a_{D+2}
+template <typename real, int D>
+__device__ __forceinline__ void metric_row(const real* c, const real r[3], real S[3]) {
+    real a1[3], a2[3];
+    tangent<real, (D + 1) % 3>(c, r, a1);
+    tangent<real, (D + 2) % 3>(c, r, a2);
+    cross3(a1, a2, S);
 }
 
 template <typename real>
 __device__ __forceinline__ real jacobian(const real* c, const real r[3]) {
-    real a[3][3], s[3];
-    tangents(c, r, a);
-    cross3(a[1], a[2], s);
-    return a[0][0] * s[0] + a[0][1] * s[1] + a[0][2] * s[2];
+    real a0[3], a1[3], a2[3], s[3];
+    tangent<real, 0>(c, r, a0);
+    tangent<real, 1>(c, r, a1);
+    tangent<real, 2>(c, r, a2);
+    cross3(a1, a2, s);
+    return a0[0] * s[0] + a0[1] * s[1] + a0[2] * s[2];
 }
 
 // ------------------------------------------------------------------ physics on a general area vector
@@ -226,22 +234,27 @@ __device__ __forceinline__ void cv_riemann(const real* UL, const real* UR, const
 }
 
 // ------------------------------------------------------------------ kernels
-template <int N, int NV>
+template <typename real, int N, int NV>
 struct CSizes {
     static constexpr int NP = N * N * N;
     static constexpr int NQ = N * N;
     static constexpr int NFP = (N + 1) * NQ;          // flux points of one family
-    // gradient staging: u, face corrections, J^-1, v^S, u^{Fd,C}, S_d (one family), map
-    static constexpr int G_U = 0;
+    static constexpr int OPS = (N + 1) * N + N * (N + 1) + N + (N + 1);   // L, M, xs, xf
+    static constexpr int OPS_PAD = (OPS + 3) / 4 * 4;
+    // gradient staging: operators, u, face corrections, J^-1, v^S, the flux vectors of one
+    // family (H[v][m][k] = u^{F,C} S_m, or u^{F,C} and S_m separately when H does not fit),
+    // the compact corrections of the face gradients, the map
+    static constexpr int G_U = OPS_PAD;
     static constexpr int G_DL = G_U + NV * NP;
     static constexpr int G_JI = G_DL + 6 * NV * NQ;
     static constexpr int G_VS = G_JI + NP;
-    static constexpr int G_UF = G_VS + 3 * NV * NP;
-    static constexpr int G_SF = G_UF + NV * NFP;
-    static constexpr int G_C = G_SF + 3 * NFP;
+    static constexpr int G_W = G_VS + 3 * NV * NP;
+    static constexpr bool HSTORE = (size_t)(G_W + 3 * NV * NFP + 18 * NQ + NGEO) * sizeof(real) <= 200 * 1024;
+    static constexpr int G_CR = G_W + (HSTORE ? 3 * NV * NFP : (NV + 3) * NFP);
+    static constexpr int G_C = G_CR + 18 * NQ;
     static constexpr int GRAD = G_C + NGEO;
-    // flux staging: u, v^S, G (one family), R, J^-1, map
-    static constexpr int F_U = 0;
+    // flux staging: operators, u, v^S, G (one family), R, J^-1, map
+    static constexpr int F_U = OPS_PAD;
     static constexpr int F_VS = F_U + NV * NP;
     static constexpr int F_G = F_VS + 3 * NV * NP;
     static constexpr int F_R = F_G + NV * NFP;
@@ -250,17 +263,71 @@ struct CSizes {
     static constexpr int FLUX = F_C + NGEO;
 };
 
+// periodic face neighbour of element e across its face (d, side) (no run-time indexed array)
+__device__ __forceinline__ int cneighbour(const Mesh& g, int e, int d, int side) {
+    int cx = e % g.ne[0];
+    const int r = e / g.ne[0];
+    int cy = r % g.ne[1], cz = r / g.ne[1];
+    const int s = side ? 1 : -1;
+    if (d == 0) {
+        cx += s;
+        cx = cx < 0 ? cx + g.ne[0] : (cx >= g.ne[0] ? cx - g.ne[0] : cx);
+    } else if (d == 1) {
+        cy += s;
+        cy = cy < 0 ? cy + g.ne[1] : (cy >= g.ne[1] ? cy - g.ne[1] : cy);
+    } else {
+        cz += s;
+        cz = cz < 0 ? cz + g.ne[2] : (cz >= g.ne[2] ? cz - g.ne[2] : cz);
+    }
+    return cx + g.ne[0] * (cy + g.ne[1] * cz);
+}
+
 template <typename real, int NV>
 __device__ __forceinline__ real var_offset(int v, real off0, real off4) {
     if (NV != 5) return real(0);
     return v == 0 ? off0 : (v == 4 ? off4 : real(0));
 }
 
+// copy the 1D operators to shared memory (their indices vary across a warp in the loops)
+template <typename real, int N>
+__device__ __forceinline__ void stage_ops(const COps<real, N>& o, real* s) {
+    for (int k = threadIdx.x; k < (N + 1) * N; k += blockDim.x) {
+        s[k] = o.L[k];
+        s[(N + 1) * N + k] = o.M[k];
+    }
+    for (int k = threadIdx.x; k < N; k += blockDim.x) s[2 * N * (N + 1) + k] = o.xs[k];
+    for (int k = threadIdx.x; k <= N; k += blockDim.x) s[2 * N * (N + 1) + N + k] = o.xf[k];
+}
+
+template <typename real, int N>
+struct SOps {
+    const real *L, *M, *xs, *xf;
+    __device__ __forceinline__ explicit SOps(const real* s)
+        : L(s), M(s + (N + 1) * N), xs(s + 2 * N * (N + 1)), xf(s + 2 * N * (N + 1) + N) {}
+};
+
+template <typename real, int N, int D>
+__device__ __forceinline__ void flux_point_coords(const real* xs, const real* xf, int f, int q, real r[3]) {
+    constexpr int t1 = D == 0 ? 1 : 0, t2 = D == 2 ? 1 : 2;
+    r[D] = xf[f];
+    r[t1] = xs[q % N];
+    r[t2] = xs[q / N];
+}
+
 // face traces of u: Tc[((e*6 + f)*NV + v)*NQ + q] = l(+-1) . u along d on line q
+template <typename real, int N, int D>
+__device__ __forceinline__ real trace_line(const real* base, const real* Lr, int q, real off) {
+    real acc = Lr[0] * (base[cpt<N, D>(0, q)] - off);
+#pragma unroll
+    for (int i = 1; i < N; ++i) acc = fma(Lr[i], base[cpt<N, D>(i, q)] - off, acc);
+    return acc;
+}
+
 template <typename real, int N, int NV>
-__global__ void __launch_bounds__(256) k_ctrace(const real* __restrict__ U, real* __restrict__ Tc, COps<real, N> o,
-                                                Mesh g, real off0, real off4) {
-    using CS = CSizes<N, NV>;
+__global__ void __launch_bounds__(256) k_ctrace(const real* __restrict__ U, real* __restrict__ Tc,
+                                                const __grid_constant__ COps<real, N> o, Mesh g, real off0,
+                                                real off4) {
+    using CS = CSizes<real, N, NV>;
     const long long total = (long long)g.nelem * 6 * NV * CS::NQ;
     for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
          idx += (long long)gridDim.x * blockDim.x) {
@@ -270,33 +337,100 @@ __global__ void __launch_bounds__(256) k_ctrace(const real* __restrict__ U, real
         r /= NV;
         const int f = (int)(r % 6);
         const long long e = r / 6;
-        const int d = f >> 1;
         const real* base = U + (size_t)v * g.nelem * CS::NP + (size_t)e * CS::NP;
-        const real* Lr = o.L + ((f & 1) ? N * N : 0);
-        const real off = var_offset<real, NV>(v, off0, off4);
-        real acc = Lr[0] * (base[cpt<N>(d, 0, q)] - off);
+        real Lr[N];
 #pragma unroll
-        for (int i = 1; i < N; ++i) acc = fma(Lr[i], base[cpt<N>(d, i, q)] - off, acc);
+        for (int i = 0; i < N; ++i) Lr[i] = (f & 1) ? o.L[N * N + i] : o.L[i];
+        const real off = var_offset<real, NV>(v, off0, off4);
+        real acc;
+        switch (f >> 1) {
+            case 0: acc = trace_line<real, N, 0>(base, Lr, q, off); break;
+            case 1: acc = trace_line<real, N, 1>(base, Lr, q, off); break;
+            default: acc = trace_line<real, N, 2>(base, Lr, q, off); break;
+        }
         Tc[idx] = acc;
     }
 }
 
-// Stage element e and form v^S (Sec. 2.3 step 3): on return sm + G_VS holds
-// v^S[v][m][pt] (J^-1 applied), sm + G_DL the face corrections delta = (u_nb - u_own)/2
-// [face][v][q], sm + G_JI the values of J^-1. Ends with __syncthreads.
+// One family of Sec. 2.3 step 3: the flux vectors H_m = u^{FD,C} S_Dm at the flux points of
+// family D, then v^S_m += M_D H_m at the solution points. Ends with __syncthreads.
+template <typename real, int N, int NV, int D>
+__device__ __forceinline__ void family_gradient(real* sm) {
+    using CS = CSizes<real, N, NV>;
+    constexpr int NP = CS::NP, NQ = CS::NQ, NFP = CS::NFP;
+    const SOps<real, N> op(sm);
+    const real* su = sm + CS::G_U;
+    const real* sdl = sm + CS::G_DL;
+    const real* sc = sm + CS::G_C;
+    real* svs = sm + CS::G_VS;
+    real* sw = sm + CS::G_W;
+    const int tid = threadIdx.x, T = blockDim.x;
+    for (int k = tid; k < NFP; k += T) {
+        const int f = k / NQ, q = k - f * NQ;
+        real r[3], S[3];
+        flux_point_coords<real, N, D>(op.xs, op.xf, f, q, r);
+        metric_row<real, D>(sc, r, S);
+        const real* Lr = op.L + f * N;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            real acc = Lr[0] * su[v * NP + cpt<N, D>(0, q)];
+#pragma unroll
+            for (int i = 1; i < N; ++i) acc = fma(Lr[i], su[v * NP + cpt<N, D>(i, q)], acc);
+            if (f == 0) acc += sdl[(2 * D) * NV * NQ + v * NQ + q];
+            if (f == N) acc += sdl[(2 * D + 1) * NV * NQ + v * NQ + q];
+            if constexpr (CS::HSTORE) {
+#pragma unroll
+                for (int m = 0; m < 3; ++m) sw[(v * 3 + m) * NFP + k] = acc * S[m];
+            } else {
+                sw[v * NFP + k] = acc;
+            }
+        }
+        if constexpr (!CS::HSTORE) {
+#pragma unroll
+            for (int m = 0; m < 3; ++m) sw[(NV + m) * NFP + k] = S[m];
+        }
+    }
+    __syncthreads();
+    for (int k = tid; k < 3 * NV * NP; k += T) {
+        const int vm = k / NP, pt = k - vm * NP;
+        int i, q;
+        line_of<N, D>(pt, i, q);
+        const real* Mr = op.M + i * (N + 1);
+        real acc;
+        if constexpr (CS::HSTORE) {
+            const real* h = sw + vm * NFP + q;
+            acc = Mr[0] * h[0];
+#pragma unroll
+            for (int f = 1; f <= N; ++f) acc = fma(Mr[f], h[f * NQ], acc);
+        } else {
+            const int v = vm / 3, m = vm - 3 * v;
+            const real* u = sw + v * NFP + q;
+            const real* s = sw + (NV + m) * NFP + q;
+            acc = (Mr[0] * u[0]) * s[0];
+#pragma unroll
+            for (int f = 1; f <= N; ++f) acc = fma(Mr[f] * u[f * NQ], s[f * NQ], acc);
+        }
+        svs[k] += acc;
+    }
+    __syncthreads();
+}
+
+// Stage element e and form v^S (Sec. 2.3 step 3): on return sm + G_VS holds v^S[v][m][pt]
+// (J^-1 applied), sm + G_DL the face corrections delta = (u_nb - u_own)/2 [face][v][q],
+// sm + G_JI the values of J^-1. The operators must already be staged. Ends with
+// __syncthreads.
 template <typename real, int N, int NV>
 __device__ void element_gradient(const real* __restrict__ U, const real* __restrict__ Tc,
-                                 const real* __restrict__ geo, const COps<real, N>& o, const Mesh& g, int e,
-                                 real off0, real off4, real* sm) {
-    using CS = CSizes<N, NV>;
-    constexpr int NP = CS::NP, NQ = CS::NQ, NFP = CS::NFP;
+                                 const real* __restrict__ geo, const Mesh& g, int e, real off0, real off4,
+                                 real* sm) {
+    using CS = CSizes<real, N, NV>;
+    constexpr int NP = CS::NP, NQ = CS::NQ;
+    const SOps<real, N> op(sm);
     const int tid = threadIdx.x, T = blockDim.x;
     real* su = sm + CS::G_U;
     real* sdl = sm + CS::G_DL;
     real* sji = sm + CS::G_JI;
     real* svs = sm + CS::G_VS;
-    real* suf = sm + CS::G_UF;
-    real* ssf = sm + CS::G_SF;
     real* sc = sm + CS::G_C;
     for (int k = tid; k < NGEO; k += T) sc[k] = geo[(size_t)e * NGEO + k];
     for (int k = tid; k < NV * NP; k += T) {
@@ -305,7 +439,7 @@ __device__ void element_gradient(const real* __restrict__ U, const real* __restr
     }
     for (int k = tid; k < 6 * NV * NQ; k += T) {
         const int f = k / (NV * NQ), rem = k - f * NV * NQ;
-        const int en = sdk::neighbour(g, e, f >> 1, f & 1);
+        const int en = cneighbour(g, e, f >> 1, f & 1);
         const real own = Tc[((size_t)e * 6 + f) * NV * NQ + rem];
         const real nb = Tc[((size_t)en * 6 + (f ^ 1)) * NV * NQ + rem];
         sdl[k] = real(0.5) * (nb - own);
@@ -313,88 +447,90 @@ __device__ void element_gradient(const real* __restrict__ U, const real* __restr
     for (int k = tid; k < 3 * NV * NP; k += T) svs[k] = real(0);
     __syncthreads();
     for (int pt = tid; pt < NP; pt += T) {
-        real r[3];
-        solution_point_coords(o, pt, r);
+        const real r[3] = {op.xs[pt % N], op.xs[(pt / N) % N], op.xs[pt / (N * N)]};
         sji[pt] = real(1) / jacobian(sc, r);
     }
-    for (int d = 0; d < 3; ++d) {
-        // u^{Fd,C} and row d of S at the flux points of family d
-        for (int k = tid; k < NFP; k += T) {
-            const int f = k / NQ, q = k - f * NQ;
-            real r[3], S[3];
-            flux_point_coords(o, d, f, q, r);
-            metric_row(sc, r, d, S);
-#pragma unroll
-            for (int m = 0; m < 3; ++m) ssf[m * NFP + k] = S[m];
-            const real* Lr = o.L + f * N;
-#pragma unroll
-            for (int v = 0; v < NV; ++v) {
-                real acc = Lr[0] * su[v * NP + cpt<N>(d, 0, q)];
-#pragma unroll
-                for (int i = 1; i < N; ++i) acc = fma(Lr[i], su[v * NP + cpt<N>(d, i, q)], acc);
-                if (f == 0) acc += sdl[(2 * d) * NV * NQ + v * NQ + q];
-                if (f == N) acc += sdl[(2 * d + 1) * NV * NQ + v * NQ + q];
-                suf[v * NFP + k] = acc;
-            }
-        }
-        __syncthreads();
-        // sum over the family: M_d (u^{Fd,C} S_dm)
-        for (int k = tid; k < 3 * NV * NP; k += T) {
-            const int vm = k / NP, pt = k - vm * NP;
-            const int v = vm / 3, m = vm - 3 * v;
-            const int lo = cpow<N>(d);
-            const int i = (pt / lo) % N;
-            const int q = (pt % lo) + lo * (pt / (lo * N));
-            const real* Mr = o.M + i * (N + 1);
-            real acc = real(0);
-#pragma unroll
-            for (int f = 0; f <= N; ++f) acc = fma(Mr[f], suf[v * NFP + f * NQ + q] * ssf[m * NFP + f * NQ + q], acc);
-            svs[k] += acc;
-        }
-        __syncthreads();
-    }
+    family_gradient<real, N, NV, 0>(sm);
+    family_gradient<real, N, NV, 1>(sm);
+    family_gradient<real, N, NV, 2>(sm);
     for (int k = tid; k < 3 * NV * NP; k += T) svs[k] *= sji[k % NP];
     __syncthreads();
+}
+
+// compact scheme, face point q of face 2D + s: the one-sided gradient removes the derivative
+// of the opposite face's correction, extrapolated to this face (Eqs. aux:v:cmp:l-t):
+//   L_s (J^-1 M[:, opp]) delta_opp S_Dm(opp);  cr[m] = (L_s J^-1 M[:, opp]) S_Dm(opp)
+template <typename real, int N, int NV, int D>
+__device__ __forceinline__ void face_correction(const real* sm, int s, int q, real* cr) {
+    using CS = CSizes<real, N, NV>;
+    const SOps<real, N> op(sm);
+    const real* sji = sm + CS::G_JI;
+    const real* sc = sm + CS::G_C;
+    const int fo = s ? 0 : N;
+    const real* Lr = op.L + (s ? N * N : 0);
+    real kap = real(0);
+#pragma unroll
+    for (int i = 0; i < N; ++i) kap = fma(Lr[i] * sji[cpt<N, D>(i, q)], op.M[i * (N + 1) + fo], kap);
+    real r[3], S[3];
+    flux_point_coords<real, N, D>(op.xs, op.xf, fo, q, r);
+    metric_row<real, D>(sc, r, S);
+#pragma unroll
+    for (int m = 0; m < 3; ++m) cr[m] = kap * S[m];
+}
+
+template <typename real, int N, int D>
+__device__ __forceinline__ real face_extrapolate(const real* vs, const real* Lr, int q) {
+    real val = Lr[0] * vs[cpt<N, D>(0, q)];
+#pragma unroll
+    for (int i = 1; i < N; ++i) val = fma(Lr[i], vs[cpt<N, D>(i, q)], val);
+    return val;
 }
 
 template <typename real, int N, int NV>
 __global__ void __launch_bounds__(CURV_THREADS) k_cgrad(const real* __restrict__ U, const real* __restrict__ Tc,
                                                         const real* __restrict__ geo, real* __restrict__ VS,
-                                                        real* __restrict__ Tg, COps<real, N> o, Mesh g, real off0,
-                                                        real off4, int compact) {
-    using CS = CSizes<N, NV>;
+                                                        real* __restrict__ Tg, const __grid_constant__ COps<real, N> o,
+                                                        Mesh g, real off0, real off4, int compact) {
+    using CS = CSizes<real, N, NV>;
     constexpr int NP = CS::NP, NQ = CS::NQ;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     real* sm = reinterpret_cast<real*>(smem_raw);
     const int tid = threadIdx.x, T = blockDim.x;
+    stage_ops(o, sm);
+    __syncthreads();
+    const SOps<real, N> op(sm);
     for (int e = blockIdx.x; e < g.nelem; e += gridDim.x) {
-        element_gradient<real, N, NV>(U, Tc, geo, o, g, e, off0, off4, sm);
+        element_gradient<real, N, NV>(U, Tc, geo, g, e, off0, off4, sm);
         const real* svs = sm + CS::G_VS;
         const real* sdl = sm + CS::G_DL;
-        const real* sji = sm + CS::G_JI;
-        const real* sc = sm + CS::G_C;
+        real* scr = sm + CS::G_CR;
         for (int k = tid; k < 3 * NV * NP; k += T) VS[(size_t)e * 3 * NV * NP + k] = svs[k];
+        if (compact) {
+            for (int k = tid; k < 6 * NQ; k += T) {
+                const int f = k / NQ, q = k - f * NQ;
+                switch (f >> 1) {
+                    case 0: face_correction<real, N, NV, 0>(sm, f & 1, q, scr + 3 * k); break;
+                    case 1: face_correction<real, N, NV, 1>(sm, f & 1, q, scr + 3 * k); break;
+                    default: face_correction<real, N, NV, 2>(sm, f & 1, q, scr + 3 * k); break;
+                }
+            }
+            __syncthreads();
+        }
         for (int k = tid; k < 6 * 3 * NV * NQ; k += T) {
             const int f = k / (3 * NV * NQ), rem = k - f * 3 * NV * NQ;
             const int vm = rem / NQ, q = rem - vm * NQ;
             const int d = f >> 1, s = f & 1;
-            const real* Lr = o.L + (s ? N * N : 0);
+            const real* Lr = op.L + (s ? N * N : 0);
             const real* vs = svs + vm * NP;
-            real val = Lr[0] * vs[cpt<N>(d, 0, q)];
-#pragma unroll
-            for (int i = 1; i < N; ++i) val = fma(Lr[i], vs[cpt<N>(d, i, q)], val);
+            real val;
+            switch (d) {
+                case 0: val = face_extrapolate<real, N, 0>(vs, Lr, q); break;
+                case 1: val = face_extrapolate<real, N, 1>(vs, Lr, q); break;
+                default: val = face_extrapolate<real, N, 2>(vs, Lr, q); break;
+            }
             if (compact) {
-                // remove the opposite face's correction from the d-flux (Eqs. aux:v:cmp:l-t):
-                // L_s (J^-1 M[:, opp]) delta_opp S_dm(opp)
-                const int fo = s ? 0 : N;
                 const int v = vm / 3, m = vm - 3 * v;
-                real kap = real(0);
-#pragma unroll
-                for (int i = 0; i < N; ++i) kap = fma(Lr[i] * sji[cpt<N>(d, i, q)], o.M[i * (N + 1) + fo], kap);
-                real r[3], S[3];
-                flux_point_coords(o, d, fo, q, r);
-                metric_row(sc, r, d, S);
-                val -= kap * sdl[(2 * d + (s ? 0 : 1)) * NV * NQ + v * NQ + q] * S[m];
+                val -= scr[3 * (f * NQ + q) + m] * sdl[(2 * d + (s ? 0 : 1)) * NV * NQ + v * NQ + q];
             }
             Tg[((size_t)e * 6 + f) * 3 * NV * NQ + rem] = val;
         }
@@ -402,111 +538,191 @@ __global__ void __launch_bounds__(CURV_THREADS) k_cgrad(const real* __restrict__
     }
 }
 
-// one common flux per interface point (the -d face of element e): Fh[((d*nelem + e)*NV + v)*NQ + q]
+// one common flux per interface point (the -D face of element e): Fh[((D*nelem + e)*NV + v)*NQ + q]
+template <typename real, int N, int NV, int D>
+__device__ __forceinline__ void face_point(const real* __restrict__ Tc, const real* __restrict__ Tg,
+                                           const real* __restrict__ geo, const real* __restrict__ ih,
+                                           real* __restrict__ Fh, const COps<real, N>& o, const Mesh& g,
+                                           const Phys<real>& P, real eta_n2, int e, int q) {
+    using CS = CSizes<real, N, NV>;
+    constexpr int NQ = CS::NQ;
+    const int el = cneighbour(g, e, D, 0);
+    const real* tl = Tc + ((size_t)el * 6 + 2 * D + 1) * NV * NQ + q;
+    const real* tr = Tc + ((size_t)e * 6 + 2 * D) * NV * NQ + q;
+    const real* gl = Tg + ((size_t)el * 6 + 2 * D + 1) * 3 * NV * NQ + q;
+    const real* gr = Tg + ((size_t)e * 6 + 2 * D) * 3 * NV * NQ + q;
+    real uL[NV], uR[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+        uL[v] = tl[v * NQ];
+        uR[v] = tr[v * NQ];
+    }
+    real c[21];
+#pragma unroll
+    for (int k = 0; k < 21; ++k) c[k] = geo[(size_t)e * NGEO + k];
+    real rr[3], S[3];
+    flux_point_coords<real, N, D>(o.xs, o.xf, 0, q, rr);
+    metric_row<real, D>(c, rr, S);
+    const real area = sqrt(S[0] * S[0] + S[1] * S[1] + S[2] * S[2]);
+    const real ia = real(1) / area;
+    const real nv[3] = {S[0] * ia, S[1] * ia, S[2] * ia};
+    const real tau = eta_n2 > real(0) ? eta_n2 * ih[(size_t)e * 3 + D] : real(0);
+    // own-side gradients with the penalty tau (u_R - u_L) n added (Sec. 3, IP)
+    real vl[NV * 3], vr[NV * 3];
+#pragma unroll
+    for (int v = 0; v < NV; ++v)
+#pragma unroll
+        for (int m = 0; m < 3; ++m) {
+            const real pen = tau * (uR[v] - uL[v]) * nv[m];
+            vl[v * 3 + m] = gl[(v * 3 + m) * NQ] + pen;
+            vr[v * 3 + m] = gr[(v * 3 + m) * NQ] + pen;
+        }
+    real G[NV];
+    if constexpr (NV == 5) {
+        cv_riemann(uL, uR, nv, P, G);
+#pragma unroll
+        for (int k = 0; k < 5; ++k) G[k] *= area;
+        if (P.vflux == 0) {
+            real uh[5], vh[15], Gv[5];
+#pragma unroll
+            for (int k = 0; k < 5; ++k) uh[k] = real(0.5) * (uL[k] + uR[k]);
+#pragma unroll
+            for (int k = 0; k < 15; ++k) vh[k] = real(0.5) * (vl[k] + vr[k]);
+            cv_viscous(uh, vh, S, P, Gv);
+#pragma unroll
+            for (int k = 0; k < 5; ++k) G[k] -= Gv[k];
+        } else {
+            real Ga[5], Gb[5];
+            cv_viscous(uL, vl, S, P, Ga);
+            cv_viscous(uR, vr, S, P, Gb);
+#pragma unroll
+            for (int k = 0; k < 5; ++k) G[k] -= real(0.5) * (Ga[k] + Gb[k]);
+        }
+    } else {
+        if (P.vflux == 0) {
+            const real uh = real(0.5) * (uL[0] + uR[0]);
+            real s = real(0);
+#pragma unroll
+            for (int m = 0; m < 3; ++m) s += S[m] * (real(0.5) * (vl[m] + vr[m]));
+            G[0] = -sdk::scalar_coef(P, uh) * s;
+        } else {
+            real sa = real(0), sb = real(0);
+#pragma unroll
+            for (int m = 0; m < 3; ++m) {
+                sa += S[m] * vl[m];
+                sb += S[m] * vr[m];
+            }
+            G[0] = real(0.5) * (-sdk::scalar_coef(P, uL[0]) * sa - sdk::scalar_coef(P, uR[0]) * sb);
+        }
+    }
+#pragma unroll
+    for (int v = 0; v < NV; ++v) Fh[(((size_t)D * g.nelem + e) * NV + v) * NQ + q] = G[v];
+}
+
 template <typename real, int N, int NV>
 __global__ void __launch_bounds__(256) k_cface(const real* __restrict__ Tc, const real* __restrict__ Tg,
                                                const real* __restrict__ geo, const real* __restrict__ ih,
-                                               real* __restrict__ Fh, COps<real, N> o, Mesh g, Phys<real> P,
-                                               real eta_n2) {
-    using CS = CSizes<N, NV>;
-    constexpr int NQ = CS::NQ;
+                                               real* __restrict__ Fh, const __grid_constant__ COps<real, N> o,
+                                               Mesh g, Phys<real> P, real eta_n2) {
+    constexpr int NQ = N * N;
     const long long total = 3LL * g.nelem * NQ;
     for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
          idx += (long long)gridDim.x * blockDim.x) {
         const int q = (int)(idx % NQ);
         const long long r = idx / NQ;
         const int e = (int)(r % g.nelem);
-        const int d = (int)(r / g.nelem);
-        const int el = sdk::neighbour(g, e, d, 0);
-        const real* tl = Tc + ((size_t)el * 6 + 2 * d + 1) * NV * NQ + q;
-        const real* tr = Tc + ((size_t)e * 6 + 2 * d) * NV * NQ + q;
-        const real* gl = Tg + ((size_t)el * 6 + 2 * d + 1) * 3 * NV * NQ + q;
-        const real* gr = Tg + ((size_t)e * 6 + 2 * d) * 3 * NV * NQ + q;
-        real uL[NV], uR[NV];
-#pragma unroll
-        for (int v = 0; v < NV; ++v) {
-            uL[v] = tl[v * NQ];
-            uR[v] = tr[v * NQ];
+        switch ((int)(r / g.nelem)) {
+            case 0: face_point<real, N, NV, 0>(Tc, Tg, geo, ih, Fh, o, g, P, eta_n2, e, q); break;
+            case 1: face_point<real, N, NV, 1>(Tc, Tg, geo, ih, Fh, o, g, P, eta_n2, e, q); break;
+            default: face_point<real, N, NV, 2>(Tc, Tg, geo, ih, Fh, o, g, P, eta_n2, e, q); break;
         }
-        real c[21];
-#pragma unroll
-        for (int k = 0; k < 21; ++k) c[k] = geo[(size_t)e * NGEO + k];
-        real rr[3], S[3];
-        flux_point_coords(o, d, 0, q, rr);
-        metric_row(c, rr, d, S);
-        const real area = sqrt(S[0] * S[0] + S[1] * S[1] + S[2] * S[2]);
-        const real ia = real(1) / area;
-        const real nv[3] = {S[0] * ia, S[1] * ia, S[2] * ia};
-        const real tau = eta_n2 > real(0) ? eta_n2 * ih[(size_t)e * 3 + d] : real(0);
-        // own-side gradients with the penalty tau (u_R - u_L) n added (Sec. 3, IP)
-        real vl[NV * 3], vr[NV * 3];
-#pragma unroll
-        for (int v = 0; v < NV; ++v)
-#pragma unroll
-            for (int m = 0; m < 3; ++m) {
-                const real pen = tau * (uR[v] - uL[v]) * nv[m];
-                vl[v * 3 + m] = gl[(v * 3 + m) * NQ] + pen;
-                vr[v * 3 + m] = gr[(v * 3 + m) * NQ] + pen;
-            }
-        real G[NV];
-        if constexpr (NV == 5) {
-            cv_riemann(uL, uR, nv, P, G);
-#pragma unroll
-            for (int k = 0; k < 5; ++k) G[k] *= area;
-            if (P.vflux == 0) {
-                real uh[5], vh[15], Gv[5];
-#pragma unroll
-                for (int k = 0; k < 5; ++k) uh[k] = real(0.5) * (uL[k] + uR[k]);
-#pragma unroll
-                for (int k = 0; k < 15; ++k) vh[k] = real(0.5) * (vl[k] + vr[k]);
-                cv_viscous(uh, vh, S, P, Gv);
-#pragma unroll
-                for (int k = 0; k < 5; ++k) G[k] -= Gv[k];
-            } else {
-                real Ga[5], Gb[5];
-                cv_viscous(uL, vl, S, P, Ga);
-                cv_viscous(uR, vr, S, P, Gb);
-#pragma unroll
-                for (int k = 0; k < 5; ++k) G[k] -= real(0.5) * (Ga[k] + Gb[k]);
-            }
-        } else {
-            if (P.vflux == 0) {
-                const real uh = real(0.5) * (uL[0] + uR[0]);
-                real s = real(0);
-#pragma unroll
-                for (int m = 0; m < 3; ++m) s += S[m] * (real(0.5) * (vl[m] + vr[m]));
-                G[0] = -sdk::scalar_coef(P, uh) * s;
-            } else {
-                real sa = real(0), sb = real(0);
-#pragma unroll
-                for (int m = 0; m < 3; ++m) {
-                    sa += S[m] * vl[m];
-                    sb += S[m] * vr[m];
-                }
-                G[0] = real(0.5) * (-sdk::scalar_coef(P, uL[0]) * sa - sdk::scalar_coef(P, uR[0]) * sb);
-            }
-        }
-#pragma unroll
-        for (int v = 0; v < NV; ++v) Fh[(((size_t)d * g.nelem + e) * NV + v) * NQ + q] = G[v];
     }
 }
 
-template <typename real, int N, int NV>
-__global__ void __launch_bounds__(CURV_THREADS) k_cflux(const real* __restrict__ U, const real* __restrict__ VS,
-                                                        const real* __restrict__ Fh, const real* __restrict__ geo,
-                                                        real* __restrict__ R, COps<real, N> o, Mesh g,
-                                                        Phys<real> P, real off0, real off4) {
-    using CS = CSizes<N, NV>;
+// One family of Sec. 2.3 steps 4-5: G = S_D . F at the interior flux points (the stored
+// interface fluxes at the ends), then R -= M_D G. Ends with __syncthreads.
+template <typename real, int N, int NV, int D>
+__device__ __forceinline__ void family_flux(real* sm, const real* __restrict__ Fh, const Mesh& g, int e,
+                                            const Phys<real>& P) {
+    using CS = CSizes<real, N, NV>;
     constexpr int NP = CS::NP, NQ = CS::NQ, NFP = CS::NFP;
+    const SOps<real, N> op(sm);
+    const real* su = sm + CS::F_U;
+    const real* svs = sm + CS::F_VS;
+    const real* sc = sm + CS::F_C;
+    real* sG = sm + CS::F_G;
+    real* sR = sm + CS::F_R;
+    const int tid = threadIdx.x, T = blockDim.x;
+    for (int k = tid; k < NFP; k += T) {
+        const int f = k / NQ, q = k - f * NQ;
+        if (f == 0 || f == N) {
+            const int ee = f == 0 ? e : cneighbour(g, e, D, 1);
+#pragma unroll
+            for (int v = 0; v < NV; ++v) sG[v * NFP + k] = Fh[(((size_t)D * g.nelem + ee) * NV + v) * NQ + q];
+            continue;
+        }
+        const real* Lr = op.L + f * N;
+        real uF[NV], vF[3 * NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            real acc = Lr[0] * su[v * NP + cpt<N, D>(0, q)];
+#pragma unroll
+            for (int i = 1; i < N; ++i) acc = fma(Lr[i], su[v * NP + cpt<N, D>(i, q)], acc);
+            uF[v] = acc;
+        }
+#pragma unroll
+        for (int vm = 0; vm < 3 * NV; ++vm) {
+            real acc = Lr[0] * svs[vm * NP + cpt<N, D>(0, q)];
+#pragma unroll
+            for (int i = 1; i < N; ++i) acc = fma(Lr[i], svs[vm * NP + cpt<N, D>(i, q)], acc);
+            vF[vm] = acc;
+        }
+        real r[3], S[3];
+        flux_point_coords<real, N, D>(op.xs, op.xf, f, q, r);
+        metric_row<real, D>(sc, r, S);
+        if constexpr (NV == 5) {
+            real Gc[5], Gv[5];
+            cv_convective(uF, S, P, Gc);
+            cv_viscous(uF, vF, S, P, Gv);
+#pragma unroll
+            for (int v = 0; v < 5; ++v) sG[v * NFP + k] = Gc[v] - Gv[v];
+        } else {
+            sG[k] = -sdk::scalar_coef(P, uF[0]) * (S[0] * vF[0] + S[1] * vF[1] + S[2] * vF[2]);
+        }
+    }
+    __syncthreads();
+    for (int k = tid; k < NV * NP; k += T) {
+        const int v = k / NP, pt = k - v * NP;
+        int i, q;
+        line_of<N, D>(pt, i, q);
+        const real* Mr = op.M + i * (N + 1);
+        const real* gq = sG + v * NFP + q;
+        real acc = Mr[0] * gq[0];
+#pragma unroll
+        for (int f = 1; f <= N; ++f) acc = fma(Mr[f], gq[f * NQ], acc);
+        sR[k] -= acc;
+    }
+    __syncthreads();
+}
+
+template <typename real, int N, int NV>
+__global__ void __launch_bounds__(CURV_THREADS, sizeof(real) == 4 ? 3 : 1) k_cflux(const real* __restrict__ U, const real* __restrict__ VS,
+                                                        const real* __restrict__ Fh, const real* __restrict__ geo,
+                                                        real* __restrict__ R, const __grid_constant__ COps<real, N> o,
+                                                        Mesh g, Phys<real> P, real off0, real off4) {
+    using CS = CSizes<real, N, NV>;
+    constexpr int NP = CS::NP;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     real* sm = reinterpret_cast<real*>(smem_raw);
     real* su = sm + CS::F_U;
     real* svs = sm + CS::F_VS;
-    real* sG = sm + CS::F_G;
     real* sR = sm + CS::F_R;
     real* sji = sm + CS::F_JI;
     real* sc = sm + CS::F_C;
     const int tid = threadIdx.x, T = blockDim.x;
+    stage_ops(o, sm);
+    __syncthreads();
+    const SOps<real, N> op(sm);
     for (int e = blockIdx.x; e < g.nelem; e += gridDim.x) {
         for (int k = tid; k < NGEO; k += T) sc[k] = geo[(size_t)e * NGEO + k];
         for (int k = tid; k < NV * NP; k += T) {
@@ -517,62 +733,12 @@ __global__ void __launch_bounds__(CURV_THREADS) k_cflux(const real* __restrict__
         for (int k = tid; k < 3 * NV * NP; k += T) svs[k] = VS[(size_t)e * 3 * NV * NP + k];
         __syncthreads();
         for (int pt = tid; pt < NP; pt += T) {
-            real r[3];
-            solution_point_coords(o, pt, r);
+            const real r[3] = {op.xs[pt % N], op.xs[(pt / N) % N], op.xs[pt / (N * N)]};
             sji[pt] = real(1) / jacobian(sc, r);
         }
-        for (int d = 0; d < 3; ++d) {
-            for (int k = tid; k < NFP; k += T) {
-                const int f = k / NQ, q = k - f * NQ;
-                if (f == 0 || f == N) {
-                    const int ee = f == 0 ? e : sdk::neighbour(g, e, d, 1);
-#pragma unroll
-                    for (int v = 0; v < NV; ++v) sG[v * NFP + k] = Fh[(((size_t)d * g.nelem + ee) * NV + v) * NQ + q];
-                    continue;
-                }
-                const real* Lr = o.L + f * N;
-                real uF[NV], vF[3 * NV];
-#pragma unroll
-                for (int v = 0; v < NV; ++v) {
-                    real acc = Lr[0] * su[v * NP + cpt<N>(d, 0, q)];
-#pragma unroll
-                    for (int i = 1; i < N; ++i) acc = fma(Lr[i], su[v * NP + cpt<N>(d, i, q)], acc);
-                    uF[v] = acc;
-                }
-#pragma unroll
-                for (int vm = 0; vm < 3 * NV; ++vm) {
-                    real acc = Lr[0] * svs[vm * NP + cpt<N>(d, 0, q)];
-#pragma unroll
-                    for (int i = 1; i < N; ++i) acc = fma(Lr[i], svs[vm * NP + cpt<N>(d, i, q)], acc);
-                    vF[vm] = acc;
-                }
-                real r[3], S[3];
-                flux_point_coords(o, d, f, q, r);
-                metric_row(sc, r, d, S);
-                if constexpr (NV == 5) {
-                    real Gc[5], Gv[5];
-                    cv_convective(uF, S, P, Gc);
-                    cv_viscous(uF, vF, S, P, Gv);
-#pragma unroll
-                    for (int v = 0; v < 5; ++v) sG[v * NFP + k] = Gc[v] - Gv[v];
-                } else {
-                    sG[k] = -sdk::scalar_coef(P, uF[0]) * (S[0] * vF[0] + S[1] * vF[1] + S[2] * vF[2]);
-                }
-            }
-            __syncthreads();
-            for (int k = tid; k < NV * NP; k += T) {
-                const int v = k / NP, pt = k - v * NP;
-                const int lo = cpow<N>(d);
-                const int i = (pt / lo) % N;
-                const int q = (pt % lo) + lo * (pt / (lo * N));
-                const real* Mr = o.M + i * (N + 1);
-                real acc = Mr[0] * sG[v * NFP + q];
-#pragma unroll
-                for (int f = 1; f <= N; ++f) acc = fma(Mr[f], sG[v * NFP + f * NQ + q], acc);
-                sR[k] -= acc;
-            }
-            __syncthreads();
-        }
+        family_flux<real, N, NV, 0>(sm, Fh, g, e, P);
+        family_flux<real, N, NV, 1>(sm, Fh, g, e, P);
+        family_flux<real, N, NV, 2>(sm, Fh, g, e, P);
         for (int k = tid; k < NV * NP; k += T) {
             const int v = k / NP, pt = k - v * NP;
             R[(size_t)v * g.nelem * NP + (size_t)e * NP + pt] = sR[k] * sji[pt];
@@ -586,20 +752,23 @@ __global__ void __launch_bounds__(CURV_THREADS) k_cflux(const real* __restrict__
 // diagnostics, with the quadrature weights J w_i w_j w_k)
 template <int N, int NV>
 __global__ void __launch_bounds__(CURV_THREADS) k_cdiag(const double* __restrict__ U, const double* __restrict__ Tc,
-                                                        const double* __restrict__ geo, COps<double, N> o, Mesh g,
+                                                        const double* __restrict__ geo,
+                                                        const __grid_constant__ COps<double, N> o, Mesh g,
                                                         const double* __restrict__ wq, int epb,
                                                         double* __restrict__ partial) {
-    using CS = CSizes<N, NV>;
+    using CS = CSizes<double, N, NV>;
     constexpr int NP = CS::NP;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     double* sm = reinterpret_cast<double*>(smem_raw);
+    stage_ops(o, sm);
+    __syncthreads();
     double acc[sdk::NDIAG];
 #pragma unroll
     for (int k = 0; k < sdk::NDIAG; ++k) acc[k] = 0.0;
     for (int le = 0; le < epb; ++le) {
         const int e = blockIdx.x * epb + le;
         if (e >= g.nelem) break;
-        element_gradient<double, N, NV>(U, Tc, geo, o, g, e, 0.0, 0.0, sm);
+        element_gradient<double, N, NV>(U, Tc, geo, g, e, 0.0, 0.0, sm);
         const double* su = sm + CS::G_U;
         const double* vS = sm + CS::G_VS;
         const double* sji = sm + CS::G_JI;
@@ -636,7 +805,8 @@ __global__ void __launch_bounds__(CURV_THREADS) k_cdiag(const double* __restrict
         }
         __syncthreads();
     }
-    // deterministic block reduction (fixed tree over the threads)
+    // deterministic block reduction (fixed tree over the threads); the operators staged at
+    // the front of shared memory are no longer needed
     double* red = sm;
     for (int k = 0; k < sdk::NDIAG; ++k) red[k * blockDim.x + threadIdx.x] = acc[k];
     __syncthreads();
@@ -681,7 +851,7 @@ inline int elem_threads(int n) {
 
 template <typename real, int N, int NV>
 static sd_status residual_impl(sd_ctx* c, const real* U, real* R, int offset_in) {
-    using CS = CSizes<N, NV>;
+    using CS = CSizes<real, N, NV>;
     const COps<real, N> o = make_cops<real, N>(c);
     const Mesh g = cmesh(c);
     const Phys<real> P = sdk::make_phys<real>(c);
@@ -752,7 +922,7 @@ static sd_status residual_dispatch(sd_ctx* c, const real* U, real* R, int offset
 
 template <int N, int NV>
 static sd_status diag_impl(sd_ctx* c, const double* U) {
-    using CS = CSizes<N, NV>;
+    using CS = CSizes<double, N, NV>;
     const COps<double, N> o = make_cops<double, N>(c);
     const Mesh g = cmesh(c);
     sdi_prof_begin(c, SD_K_OTHER);
