@@ -241,16 +241,14 @@ struct CSizes {
     static constexpr int NFP = (N + 1) * NQ;          // flux points of one family
     static constexpr int OPS = (N + 1) * N + N * (N + 1) + N + (N + 1);   // L, M, xs, xf
     static constexpr int OPS_PAD = (OPS + 3) / 4 * 4;
-    // gradient staging: operators, u, face corrections, J^-1, v^S, the flux vectors of one
-    // family (H[v][m][k] = u^{F,C} S_m, or u^{F,C} and S_m separately when H does not fit),
-    // the compact corrections of the face gradients, the map
+    // gradient staging: operators, u, face corrections, J^-1, v^S, row D of S at the flux
+    // points of one family, the compact corrections of the face gradients, the map
     static constexpr int G_U = OPS_PAD;
     static constexpr int G_DL = G_U + NV * NP;
     static constexpr int G_JI = G_DL + 6 * NV * NQ;
     static constexpr int G_VS = G_JI + NP;
     static constexpr int G_W = G_VS + 3 * NV * NP;
-    static constexpr bool HSTORE = (size_t)(G_W + 3 * NV * NFP + 18 * NQ + NGEO) * sizeof(real) <= 200 * 1024;
-    static constexpr int G_CR = G_W + (HSTORE ? 3 * NV * NFP : (NV + 3) * NFP);
+    static constexpr int G_CR = G_W + 3 * NFP;
     static constexpr int G_C = G_CR + 18 * NQ;
     static constexpr int GRAD = G_C + NGEO;
     // flux staging: operators, u, v^S, G (one family), R, J^-1, map
@@ -314,46 +312,64 @@ __device__ __forceinline__ void flux_point_coords(const real* xs, const real* xf
     r[t2] = xs[q / N];
 }
 
-// face traces of u: Tc[((e*6 + f)*NV + v)*NQ + q] = l(+-1) . u along d on line q
+// values at the two faces of direction D on line q: (l(-1) . v, l(+1) . v); L0, LN are the
+// first and last rows of L
 template <typename real, int N, int D>
-__device__ __forceinline__ real trace_line(const real* base, const real* Lr, int q, real off) {
-    real acc = Lr[0] * (base[cpt<N, D>(0, q)] - off);
+__device__ __forceinline__ void face_pair(const real* vs, const real* L0, const real* LN, int q, real& lo,
+                                          real& hi) {
+    real x[N];
 #pragma unroll
-    for (int i = 1; i < N; ++i) acc = fma(Lr[i], base[cpt<N, D>(i, q)] - off, acc);
-    return acc;
-}
-
-template <typename real, int N, int NV>
-__global__ void __launch_bounds__(256) k_ctrace(const real* __restrict__ U, real* __restrict__ Tc,
-                                                const __grid_constant__ COps<real, N> o, Mesh g, real off0,
-                                                real off4) {
-    using CS = CSizes<real, N, NV>;
-    const long long total = (long long)g.nelem * 6 * NV * CS::NQ;
-    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-         idx += (long long)gridDim.x * blockDim.x) {
-        const int q = (int)(idx % CS::NQ);
-        long long r = idx / CS::NQ;
-        const int v = (int)(r % NV);
-        r /= NV;
-        const int f = (int)(r % 6);
-        const long long e = r / 6;
-        const real* base = U + (size_t)v * g.nelem * CS::NP + (size_t)e * CS::NP;
-        real Lr[N];
+    for (int i = 0; i < N; ++i) x[i] = vs[cpt<N, D>(i, q)];
+    lo = L0[0] * x[0];
+    hi = LN[0] * x[0];
 #pragma unroll
-        for (int i = 0; i < N; ++i) Lr[i] = (f & 1) ? o.L[N * N + i] : o.L[i];
-        const real off = var_offset<real, NV>(v, off0, off4);
-        real acc;
-        switch (f >> 1) {
-            case 0: acc = trace_line<real, N, 0>(base, Lr, q, off); break;
-            case 1: acc = trace_line<real, N, 1>(base, Lr, q, off); break;
-            default: acc = trace_line<real, N, 2>(base, Lr, q, off); break;
-        }
-        Tc[idx] = acc;
+    for (int i = 1; i < N; ++i) {
+        lo = fma(L0[i], x[i], lo);
+        hi = fma(LN[i], x[i], hi);
     }
 }
 
-// One family of Sec. 2.3 step 3: the flux vectors H_m = u^{FD,C} S_Dm at the flux points of
-// family D, then v^S_m += M_D H_m at the solution points. Ends with __syncthreads.
+// face traces of u, one element per block at a time (coalesced loads of the element's u):
+// Tc[((e*6 + f)*NV + v)*NQ + q] = l(+-1) . u along d on line q, faces f = 2d (-d), 2d + 1 (+d)
+template <typename real, int N, int NV>
+__global__ void __launch_bounds__(128) k_ctrace(const real* __restrict__ U, real* __restrict__ Tc,
+                                                const __grid_constant__ COps<real, N> o, Mesh g, real off0,
+                                                real off4) {
+    using CS = CSizes<real, N, NV>;
+    constexpr int NP = CS::NP, NQ = CS::NQ;
+    __shared__ real su[NV * NP];
+    __shared__ real sL[2 * N];
+    const int tid = threadIdx.x, T = blockDim.x;
+    if (tid < N) {
+        sL[tid] = o.L[tid];
+        sL[N + tid] = o.L[N * N + tid];
+    }
+    for (int e = blockIdx.x; e < g.nelem; e += gridDim.x) {
+        for (int k = tid; k < NV * NP; k += T) {
+            const int v = k / NP, pt = k - v * NP;
+            su[k] = U[(size_t)v * g.nelem * NP + (size_t)e * NP + pt] - var_offset<real, NV>(v, off0, off4);
+        }
+        __syncthreads();
+        for (int k = tid; k < 3 * NV * NQ; k += T) {
+            const int d = k / (NV * NQ), rem = k - d * NV * NQ;
+            const int v = rem / NQ, q = rem - v * NQ;
+            real lo, hi;
+            switch (d) {
+                case 0: face_pair<real, N, 0>(su + v * NP, sL, sL + N, q, lo, hi); break;
+                case 1: face_pair<real, N, 1>(su + v * NP, sL, sL + N, q, lo, hi); break;
+                default: face_pair<real, N, 2>(su + v * NP, sL, sL + N, q, lo, hi); break;
+            }
+            Tc[((size_t)e * 6 + 2 * d) * NV * NQ + rem] = lo;
+            Tc[((size_t)e * 6 + 2 * d + 1) * NV * NQ + rem] = hi;
+        }
+        __syncthreads();
+    }
+}
+
+// One family of Sec. 2.3 step 3. Row D of S at the family's flux points goes to shared
+// memory; then one thread per (line q, variable v) forms u^{FD,C} at the line's n + 1 flux
+// points in registers, the flux vectors H_m = u^{FD,C} S_Dm, and adds M_D H_m to v^S_m at the
+// line's n solution points. Ends with __syncthreads.
 template <typename real, int N, int NV, int D>
 __device__ __forceinline__ void family_gradient(real* sm) {
     using CS = CSizes<real, N, NV>;
@@ -363,54 +379,46 @@ __device__ __forceinline__ void family_gradient(real* sm) {
     const real* sdl = sm + CS::G_DL;
     const real* sc = sm + CS::G_C;
     real* svs = sm + CS::G_VS;
-    real* sw = sm + CS::G_W;
+    real* ssf = sm + CS::G_W;
     const int tid = threadIdx.x, T = blockDim.x;
     for (int k = tid; k < NFP; k += T) {
         const int f = k / NQ, q = k - f * NQ;
         real r[3], S[3];
         flux_point_coords<real, N, D>(op.xs, op.xf, f, q, r);
         metric_row<real, D>(sc, r, S);
-        const real* Lr = op.L + f * N;
 #pragma unroll
-        for (int v = 0; v < NV; ++v) {
-            real acc = Lr[0] * su[v * NP + cpt<N, D>(0, q)];
-#pragma unroll
-            for (int i = 1; i < N; ++i) acc = fma(Lr[i], su[v * NP + cpt<N, D>(i, q)], acc);
-            if (f == 0) acc += sdl[(2 * D) * NV * NQ + v * NQ + q];
-            if (f == N) acc += sdl[(2 * D + 1) * NV * NQ + v * NQ + q];
-            if constexpr (CS::HSTORE) {
-#pragma unroll
-                for (int m = 0; m < 3; ++m) sw[(v * 3 + m) * NFP + k] = acc * S[m];
-            } else {
-                sw[v * NFP + k] = acc;
-            }
-        }
-        if constexpr (!CS::HSTORE) {
-#pragma unroll
-            for (int m = 0; m < 3; ++m) sw[(NV + m) * NFP + k] = S[m];
-        }
+        for (int m = 0; m < 3; ++m) ssf[m * NFP + k] = S[m];
     }
     __syncthreads();
-    for (int k = tid; k < 3 * NV * NP; k += T) {
-        const int vm = k / NP, pt = k - vm * NP;
-        int i, q;
-        line_of<N, D>(pt, i, q);
-        const real* Mr = op.M + i * (N + 1);
-        real acc;
-        if constexpr (CS::HSTORE) {
-            const real* h = sw + vm * NFP + q;
-            acc = Mr[0] * h[0];
+    for (int k = tid; k < NV * NQ; k += T) {
+        const int v = k / NQ, q = k - v * NQ;
+        real ul[N];
 #pragma unroll
-            for (int f = 1; f <= N; ++f) acc = fma(Mr[f], h[f * NQ], acc);
-        } else {
-            const int v = vm / 3, m = vm - 3 * v;
-            const real* u = sw + v * NFP + q;
-            const real* s = sw + (NV + m) * NFP + q;
-            acc = (Mr[0] * u[0]) * s[0];
+        for (int i = 0; i < N; ++i) ul[i] = su[v * NP + cpt<N, D>(i, q)];
+        real uf[N + 1];
 #pragma unroll
-            for (int f = 1; f <= N; ++f) acc = fma(Mr[f] * u[f * NQ], s[f * NQ], acc);
+        for (int f = 0; f <= N; ++f) {
+            real acc = op.L[f * N] * ul[0];
+#pragma unroll
+            for (int i = 1; i < N; ++i) acc = fma(op.L[f * N + i], ul[i], acc);
+            uf[f] = acc;
         }
-        svs[k] += acc;
+        uf[0] += sdl[(2 * D) * NV * NQ + v * NQ + q];
+        uf[N] += sdl[(2 * D + 1) * NV * NQ + v * NQ + q];
+#pragma unroll
+        for (int m = 0; m < 3; ++m) {
+            real h[N + 1];
+#pragma unroll
+            for (int f = 0; f <= N; ++f) h[f] = uf[f] * ssf[m * NFP + f * NQ + q];
+            real* vs = svs + (v * 3 + m) * NP;
+#pragma unroll
+            for (int i = 0; i < N; ++i) {
+                real acc = op.M[i * (N + 1)] * h[0];
+#pragma unroll
+                for (int f = 1; f <= N; ++f) acc = fma(op.M[i * (N + 1) + f], h[f], acc);
+                vs[cpt<N, D>(i, q)] += acc;
+            }
+        }
     }
     __syncthreads();
 }
@@ -478,14 +486,6 @@ __device__ __forceinline__ void face_correction(const real* sm, int s, int q, re
     for (int m = 0; m < 3; ++m) cr[m] = kap * S[m];
 }
 
-template <typename real, int N, int D>
-__device__ __forceinline__ real face_extrapolate(const real* vs, const real* Lr, int q) {
-    real val = Lr[0] * vs[cpt<N, D>(0, q)];
-#pragma unroll
-    for (int i = 1; i < N; ++i) val = fma(Lr[i], vs[cpt<N, D>(i, q)], val);
-    return val;
-}
-
 template <typename real, int N, int NV>
 __global__ void __launch_bounds__(CURV_THREADS) k_cgrad(const real* __restrict__ U, const real* __restrict__ Tc,
                                                         const real* __restrict__ geo, real* __restrict__ VS,
@@ -516,23 +516,25 @@ __global__ void __launch_bounds__(CURV_THREADS) k_cgrad(const real* __restrict__
             }
             __syncthreads();
         }
-        for (int k = tid; k < 6 * 3 * NV * NQ; k += T) {
-            const int f = k / (3 * NV * NQ), rem = k - f * 3 * NV * NQ;
+        // both faces of each line of direction d: the -d face (2d) and the +d face (2d+1)
+        for (int k = tid; k < 3 * 3 * NV * NQ; k += T) {
+            const int d = k / (3 * NV * NQ), rem = k - d * 3 * NV * NQ;
             const int vm = rem / NQ, q = rem - vm * NQ;
-            const int d = f >> 1, s = f & 1;
-            const real* Lr = op.L + (s ? N * N : 0);
             const real* vs = svs + vm * NP;
-            real val;
+            real lo, hi;
             switch (d) {
-                case 0: val = face_extrapolate<real, N, 0>(vs, Lr, q); break;
-                case 1: val = face_extrapolate<real, N, 1>(vs, Lr, q); break;
-                default: val = face_extrapolate<real, N, 2>(vs, Lr, q); break;
+                case 0: face_pair<real, N, 0>(vs, op.L, op.L + N * N, q, lo, hi); break;
+                case 1: face_pair<real, N, 1>(vs, op.L, op.L + N * N, q, lo, hi); break;
+                default: face_pair<real, N, 2>(vs, op.L, op.L + N * N, q, lo, hi); break;
             }
             if (compact) {
+                // the -d face removes the +d face's correction and vice versa
                 const int v = vm / 3, m = vm - 3 * v;
-                val -= scr[3 * (f * NQ + q) + m] * sdl[(2 * d + (s ? 0 : 1)) * NV * NQ + v * NQ + q];
+                lo -= scr[3 * ((2 * d) * NQ + q) + m] * sdl[(2 * d + 1) * NV * NQ + v * NQ + q];
+                hi -= scr[3 * ((2 * d + 1) * NQ + q) + m] * sdl[(2 * d) * NV * NQ + v * NQ + q];
             }
-            Tg[((size_t)e * 6 + f) * 3 * NV * NQ + rem] = val;
+            Tg[((size_t)e * 6 + 2 * d) * 3 * NV * NQ + rem] = lo;
+            Tg[((size_t)e * 6 + 2 * d + 1) * 3 * NV * NQ + rem] = hi;
         }
         __syncthreads();
     }
@@ -877,8 +879,7 @@ static sd_status residual_impl(sd_ctx* c, const real* U, real* R, int offset_in)
     const int th = elem_threads(N);
     const int eb = std::min(c->nelem, 1 << 30);
     sdi_prof_begin(c, SD_K_TRACE);
-    k_ctrace<real, N, NV><<<flat_blocks((long long)c->nelem * 6 * NV * CS::NQ), 256, 0, c->stream>>>(U, Tc, o, g,
-                                                                                                   off0, off4);
+    k_ctrace<real, N, NV><<<std::min(c->nelem, 148 * 32), 128, 0, c->stream>>>(U, Tc, o, g, off0, off4);
     sdi_prof_end(c, SD_K_TRACE);
     sdi_prof_begin(c, SD_K_GRAD);
     k_cgrad<real, N, NV><<<eb, th, sg, c->stream>>>(U, Tc, geo, VS, Tg, o, g, off0, off4,
@@ -926,8 +927,7 @@ static sd_status diag_impl(sd_ctx* c, const double* U) {
     const COps<double, N> o = make_cops<double, N>(c);
     const Mesh g = cmesh(c);
     sdi_prof_begin(c, SD_K_OTHER);
-    k_ctrace<double, N, NV><<<flat_blocks((long long)c->nelem * 6 * NV * CS::NQ), 256, 0, c->stream>>>(
-        U, c->Tu64, o, g, 0.0, 0.0);
+    k_ctrace<double, N, NV><<<std::min(c->nelem, 148 * 32), 128, 0, c->stream>>>(U, c->Tu64, o, g, 0.0, 0.0);
     sdi_prof_end(c, SD_K_OTHER);
     const int th = elem_threads(N);
     const size_t smem = std::max<size_t>((size_t)CS::GRAD, (size_t)sdk::NDIAG * th) * sizeof(double);
