@@ -37,8 +37,6 @@ on quadratic polynomials for the heat equation on jittered grids (R = nu lap u, 
 constant); conservation; the 3-versus-5 element stencil of the compact and BR1 schemes;
 the domain volume.
 """
-import itertools
-
 import numpy as np
 
 from .operators import operators
@@ -382,8 +380,3 @@ def ns_diagnostics(U, grid):
         volume=float(np.sum(W)),
         nonfinite=int(not np.all(np.isfinite(U))),
     )
-
-
-def element_pairs(ne):
-    """All element index triples (ex, ey, ez) (test helper)."""
-    return list(itertools.product(range(ne[0]), range(ne[1]), range(ne[2])))

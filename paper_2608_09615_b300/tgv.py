@@ -9,6 +9,11 @@ samples.
 The time step is cfl * h / ((p + 1)(u0 + c0)), with c0 = u0 / Ma the reference sound
 speed, adjusted so that a whole number of steps fills each sampling interval. A run
 stops early, and says so, when the state stops being finite.
+
+With --wavy AMP the grid is the box's lattice with every node moved by the smooth periodic
+field of inputs.wavy_lattice (amplitude AMP h): curved trilinear elements, the Taylor-Green
+field evaluated at their solution points, and the time step scaled by 1 - 2 AMP (the
+smallest node spacing).
 """
 import argparse
 import json
@@ -26,18 +31,25 @@ def time_step(ne, p, Ma=0.1, u0=1.0, cfl=0.2, L=1.0):
 
 
 def run(ne, p, Re=1600.0, scheme="compact", t_end=20.0, every=0.1, precision="f32", cfl=0.2, Ma=0.1,
-        rk="ssprk54", physics=None, closure=None, on_sample=None, perturb_seed=None):
+        rk="ssprk54", physics=None, closure=None, on_sample=None, perturb_seed=None, wavy=0.0):
     """Run and return a dict with the sample times, the diagnostics per sample, the time
-    step, the wall time and the time at which the state stopped being finite (or None)."""
+    step, the wall time and the time at which the state stopped being finite (or None).
+    wavy > 0: the curved grid of inputs.wavy_lattice with node displacement wavy * h."""
     import torch
-    dt = time_step(ne, p, Ma, cfl=cfl)
+    dt = time_step(ne, p, Ma, cfl=cfl) * (1.0 - 2.0 * wavy)
     steps_per = max(1, int(round(every / dt)))
     dt = every / steps_per
     phys = physics or Physics(kind="ns", Re=Re, Ma=Ma)
-    ctx = SD(3, (ne,) * 3, (0.0,) * 3, (2 * math.pi,) * 3, p, scheme, phys, precision)
+    if wavy > 0.0:
+        nodes = inputs.wavy_lattice((ne,) * 3, (0.0,) * 3, (2 * math.pi,) * 3, amp=wavy)
+        ctx = SD.curvilinear(nodes, p, scheme, phys, precision)
+        X = inputs.curvilinear_coordinates(nodes, p)
+    else:
+        ctx = SD(3, (ne,) * 3, (0.0,) * 3, (2 * math.pi,) * 3, p, scheme, phys, precision)
+        X = None
     if closure is not None:
         ctx.closure_enable(*closure)
-    U = torch.from_numpy(inputs.tgv_3d((ne,) * 3, p, Ma=Ma, perturb_seed=perturb_seed)).cuda()
+    U = torch.from_numpy(inputs.tgv_3d((ne,) * 3, p, Ma=Ma, perturb_seed=perturb_seed, X=X)).cuda()
     t = 0.0
     rec = [ctx.diagnostics(U, t, raise_nonfinite=False)]
     if on_sample:
@@ -98,12 +110,14 @@ def main():
     ap.add_argument("--precision", default="f32", choices=["f32", "f64"])
     ap.add_argument("--cfl", type=float, default=0.2)
     ap.add_argument("--ma", type=float, default=0.1)
+    ap.add_argument("--wavy", type=float, default=0.0, metavar="AMP",
+                    help="curved grid: nodes moved by AMP h (inputs.wavy_lattice)")
     ap.add_argument("--series", action="store_true", help="also print KE, enstrophy and dissipation series")
     a = ap.parse_args()
     for scheme in a.scheme:
-        res = run(a.ne, a.p, a.re, scheme, a.t_end, a.every, a.precision, a.cfl, a.ma)
+        res = run(a.ne, a.p, a.re, scheme, a.t_end, a.every, a.precision, a.cfl, a.ma, wavy=a.wavy)
         line = {"ne": a.ne, "p": a.p, "Re": a.re, "Ma": a.ma, "scheme": scheme, "precision": a.precision,
-                "cfl": a.cfl}
+                "cfl": a.cfl, "wavy": a.wavy}
         line.update(summary(res, a.every))
         if a.series:
             line["t"] = res["t"]
