@@ -35,7 +35,7 @@ rotation equivariance (a rigidly rotated grid and field give the rotated residua
 free-stream preservation and the discrete metric identities on jittered grids; exactness
 on quadratic polynomials for the heat equation on jittered grids (R = nu lap u, a
 constant); conservation; the 3-versus-5 element stencil of the compact and BR1 schemes;
-the domain volume.
+the domain volume; the Taylor-Green kinetic energy and enstrophy (ns_diagnostics).
 """
 import numpy as np
 

@@ -1130,6 +1130,9 @@ sd_status sdi_curv_setup(sd_ctx* c, const double* nodes) {
         sdi_set_error("upload of the curvilinear grid data failed: %s", cudaGetErrorString(err));
         return SD_ECUDA;
     }
+    // the Cartesian gradient-trace buffer is not used on a curved grid (cTg replaces it)
+    cudaFree(c->Tg);
+    c->Tg = nullptr;
     c->curv = 1;
     return SD_OK;
 }

@@ -12,7 +12,9 @@ paper and the mathematics fix:
     flux points resolve), and 0 for linear u when p >= 2;
   * conservation, the element stencil of the two schemes (Secs. 2.1-2.3: the compact
     scheme stays within one element per axis), the domain volume, and the scaling of
-    the residual (with interior penalty) under a uniform dilation of the grid.
+    the residual (with interior penalty) under a uniform dilation of the grid;
+  * the volume diagnostics of the Taylor-Green field on a curved grid against their
+    closed forms (Sec. 4.4).
 """
 import itertools
 import math
@@ -20,7 +22,8 @@ import math
 import numpy as np
 import pytest
 
-from oracle.curvilinear import CurvGrid, residual as curv_residual
+from oracle.curvilinear import CurvGrid, ns_diagnostics as curv_ns_diagnostics
+from oracle.curvilinear import residual as curv_residual
 from oracle.grid import Grid
 from oracle.physics import Heat, NavierStokes, NSParams, PorousMedium
 from oracle.residual import along, residual
@@ -230,3 +233,19 @@ def test_roe_normal_reduces_to_axis_solver_and_rotates():
     assert np.allclose(G, rot(F), rtol=1e-13, atol=1e-12)
     # consistency: equal states give the physical normal flux
     assert np.allclose(phys.roe_normal(UL, UL, list(nv)), phys.normal_flux(UL, list(nv)), rtol=1e-14, atol=1e-12)
+
+
+def test_diagnostics_taylor_green_closed_forms_on_wavy_grid():
+    # The Taylor-Green field of Sec. 4.4 sampled on a curved grid: E_k / |Omega| = u0^2 / 8
+    # and enstrophy / |Omega| = 3/4 (u0 / L)^2 up to the discretisation error, the domain
+    # volume exactly, and zero net momentum.
+    ne, p = (8, 8, 8), 4
+    N = inputs.wavy_lattice(ne, *BOX, amp=0.15)
+    U = inputs.tgv_3d(ne, p, X=inputs.curvilinear_coordinates(N, p))
+    d = curv_ns_diagnostics(U, CurvGrid(N, p))
+    vol = (2 * math.pi) ** 3
+    assert abs(d["volume"] - vol) <= 1e-12 * vol
+    assert abs(d["ke"] / vol - 0.125) <= 2e-4
+    assert abs(d["enstrophy"] / vol - 0.75) <= 2e-2
+    for i in range(3):
+        assert abs(d["mom"][i]) <= 1e-10 * vol
