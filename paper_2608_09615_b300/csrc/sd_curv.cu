@@ -12,12 +12,14 @@
 // degree 2, which the n + 1 >= 3 flux points resolve exactly, so the discrete metric
 // identity sum_d M_d S_dm = 0 holds and a uniform flow stays uniform.
 //
-// Kernels (one residual = 4 launches, element-staged in shared memory):
+// Kernels (one residual = 4 launches; the element kernels stage one element at a time in
+// shared memory):
 //   k_ctrace  face traces of u                         Tc[e][face][v][q]
-//   k_cgrad   v^S = J^-1 sum_d M_d (u^{Fd,C} S_dm), kept in VS[e][v][m][pt], and the own
-//             interface gradient of every face (BR1: L v^S; compact: the one-sided form of
-//             Eqs. aux:v:cmp:l-t, i.e. L v^S minus the extrapolated derivative of the opposite
-//             face's correction, a per-line coefficient here since J varies)  Tg[e][face][v][m][q]
+//   k_cgrad   v^S = J^-1 sum_d M_d (u^{Fd,C} S_dm), one thread per (line, variable) with the
+//             line in registers, kept in VS[e][v][m][pt], and the own interface gradient of
+//             every face (BR1: L v^S; compact: the one-sided form of Eqs. aux:v:cmp:l-t,
+//             i.e. L v^S minus the extrapolated derivative of the opposite face's correction,
+//             a per-line coefficient here since J varies)  Tg[e][face][v][m][q]
 //   k_cface   one common flux per interface point: |S| F_riemann(n) - S . F_v  Fh[d][e][v][q]
 //   k_cflux   S . F at the interior flux points, the stored interface fluxes at the ends,
 //             R = -J^-1 sum_d M_d G^{Fd}
