@@ -1,5 +1,5 @@
 """What the learned closure gains over the plain method (the plain SD solver is both its
-fallback and the judge of its error).
+fallback and the reference its error is measured against).
 
 A small version of the closure experiment runs end to end on the GPU:
 * training data: filtered fine runs (24^3 p=4 -> 6^3 p=3, 4^3 fine elements per coarse
