@@ -32,6 +32,11 @@ reading this repository takes, written once here and once in the CUDA kernels:
   52-56  within-element variances of U_v
   57-62  within-element covariances of the velocity components (i <= j)
   63     1000 / Re
+
+Pinned by tests/test_oracle_closure.py: the projection is exact on the coarse space and
+conserves the integral; the sub-grid flux vanishes when the fine field has no content the
+filter removes; the injection is conservative and acts only through interface jumps;
+features of fields with closed-form moments.
 """
 import numpy as np
 

@@ -18,6 +18,12 @@ Readings of the paper used here (where it is silent or garbled):
     Sutherland mu = mu0 (T/T0)^(3/2) (T0 + S)/(T + S) with T/T0 = e/e0 and S/T0 given
     (110.4 K / 300 K by default); Roe flux with a Harten entropy fix on the two acoustic
     eigenvalues, delta = harten * (Roe-averaged sound speed).
+
+Pinned by tests/test_oracle_residual.py (free stream; the closed-form responses of a heat
+conduction and an entropy wave; Roe's textbook properties: consistency, pure upwinding of
+supersonic pairs, exact resolution of a stationary contact), tests/test_oracle_variants.py (options (a) and (b) of the
+interface viscous flux) and tests/test_oracle_curvilinear.py (the Riemann flux along a
+general normal: the axis-aligned case, rotation equivariance, consistency).
 """
 from dataclasses import dataclass
 

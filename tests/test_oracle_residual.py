@@ -289,6 +289,33 @@ def test_roe_flux_textbook_properties():
                        rtol=1e-12, atol=1e-12)
 
 
+def test_roe_resolves_stationary_contact_exactly():
+    # A density jump at rest with equal pressures: the Roe solver puts no dissipation on the
+    # contact wave (its speed is zero) and none on the acoustic waves (their strengths
+    # vanish), so the flux is the exact (0, p n, 0); with or without the entropy fix, along an
+    # axis and along a general normal.
+    rng = np.random.default_rng(5)
+    shp = (6,)
+    pr = rng.uniform(0.5, 2, shp)
+    zero = [np.zeros(shp)] * 3
+    UL = inputs.primitive_to_conservative(rng.uniform(0.5, 2, shp), zero, pr, 1.4)
+    UR = inputs.primitive_to_conservative(rng.uniform(0.5, 2, shp), zero, pr, 1.4)
+    nv = np.array([0.3, -0.5, 0.8])
+    nv = nv / np.linalg.norm(nv)
+    for harten in (0.0, 0.1):
+        phys = NavierStokes(NSParams(harten=harten))
+        for m in range(3):
+            F = phys.roe(UL, UR, m)
+            expect = np.zeros_like(F)
+            expect[1 + m] = pr
+            assert np.allclose(F, expect, rtol=1e-13, atol=1e-13)
+        F = phys.roe_normal(UL, UR, list(nv))
+        expect = np.zeros_like(F)
+        for i in range(3):
+            expect[1 + i] = pr * nv[i]
+        assert np.allclose(F, expect, rtol=1e-13, atol=1e-13)
+
+
 # --------------------------------------------------------------- extended precision
 @pytest.mark.parametrize("scheme", SCHEMES)
 def test_extended_precision_evaluation_agrees(scheme):
