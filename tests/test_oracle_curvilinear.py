@@ -14,7 +14,9 @@ paper and the mathematics fix:
     scheme stays within one element per axis), the domain volume, and the scaling of
     the residual (with interior penalty) under a uniform dilation of the grid;
   * the volume diagnostics of the Taylor-Green field on a curved grid against their
-    closed forms (Sec. 4.4).
+    closed forms (Sec. 4.4);
+  * the truncation error of the discrete Laplacian on a smooth periodic field converges on
+    a curved grid at the rate it has on the Cartesian grid.
 """
 import itertools
 import math
@@ -249,3 +251,30 @@ def test_diagnostics_taylor_green_closed_forms_on_wavy_grid():
     assert abs(d["enstrophy"] / vol - 0.75) <= 2e-2
     for i in range(3):
         assert abs(d["mom"][i]) <= 1e-10 * vol
+
+
+@pytest.mark.parametrize("scheme", SCHEMES)
+@pytest.mark.parametrize("p", [2, 3])
+def test_truncation_error_converges_like_the_cartesian_grid(scheme, p):
+    # R(u) - nu lap u for a smooth periodic u: the discrete Laplacian's truncation error.
+    # On the wavy grid it converges at the Cartesian grid's rate (p - 1 for this pointwise
+    # second-derivative error) and stays within 1.5 times the Cartesian error.
+    def err(nodes=None, ne=None):
+        if nodes is not None:
+            g = CurvGrid(nodes, p)
+            X = g.coordinates()
+        else:
+            g = Grid(3, (ne,) * 3, *BOX, p)
+            X = g.coordinates()
+        u = np.sin(X[0] + 0.3) * np.sin(2 * X[1] + 0.1) * np.cos(X[2])
+        R = (curv_residual if nodes is not None else residual)(u[None], g, scheme, Heat(1.0))[0]
+        W = g.quadrature_weights()
+        return math.sqrt(np.sum(W * (R + 6.0 * u) ** 2) / np.sum(W))
+
+    curved = [err(nodes=inputs.wavy_lattice((ne,) * 3, *BOX, amp=0.15)) for ne in (6, 12)]
+    cart = [err(ne=ne) for ne in (6, 12)]
+    rate_curved = math.log(curved[0] / curved[1]) / math.log(2.0)
+    rate_cart = math.log(cart[0] / cart[1]) / math.log(2.0)
+    assert rate_curved >= p - 1 - 0.15, (curved, rate_curved)
+    assert abs(rate_curved - rate_cart) <= 0.25, (rate_curved, rate_cart)
+    assert curved[1] <= 1.5 * cart[1], (curved, cart)
