@@ -338,3 +338,16 @@ def test_conservation_24(precision, tol):
         tot = np.sum(W * R[v])
         scale = np.sum(W * np.abs(R[v]))
         assert abs(tot) <= tol * scale, (v, tot, scale)
+
+
+@pytest.mark.parametrize("ne,p", [((1, 2, 3), 2), ((1, 1, 1), 3), ((2, 1, 1), 1)])
+@pytest.mark.parametrize("scheme", ["br1", "compact"])
+def test_single_element_axes_fp64_parity(ne, p, scheme):
+    # degenerate periodic grids: along an axis with one element, an element is its own
+    # neighbour on both sides (its two faces are periodic images of each other)
+    prm, phys = ns_phys(eta_ip=0.3)
+    U = inputs.random_state(ne, p, seed=11)
+    N = inputs.jittered_lattice(ne, *BOX, seed=4, amp=0.12)
+    Ro = ext_residual(U, N, p, scheme, NavierStokes(prm), eta_ip=0.3)
+    Rg = gpu_residual(U, N, p, scheme, phys, "f64")
+    assert rel_err(Rg, Ro).max() <= 1e-12
