@@ -52,25 +52,32 @@ def peaks():
 
 
 def residual_flops_per_element(n, nv=5, ng=9, dim=3):
-    """Algorithmic FP32 flops per element of the NS residual kernels (FMA = 2 flops), by the
-    operation counts of the method's steps; one 1D sweep of length n costs 2n - 1 flops.
-    k_line_grad: own face traces, v^S (D sweep + two corrections), the 9 own interface
-    gradient components of the 2 dim faces (compact correction included).
-    k_face_flux: the dim faces owned by the element (its +d faces), each point once:
-    averages of the state and gradient (2 (nv + ng)), viscous flux (~60) and Roe (~150) plus
-    the combination (~25).
-    k_line_flux: own face traces, v^S, the solution and 9 gradient components at the n - 1
-    interior flux points of every line, the flux there (~85 flops), and the M divergence of
-    all n + 1 flux points."""
+    """Algorithmic FP32 flops per element of the NS residual (FMA = 2 flops), by the operation
+    counts of the method's steps, each step counted once per element whichever kernel does
+    it (work a kernel repeats, such as the flux kernel re-deriving the traces and v^S that
+    the gradient kernel also forms, is not counted). One 1D sweep of length n costs 2n - 1.
+      trace: the 2 dim face traces of every variable (step 1, interface rows);
+      vs:    v^S of every variable along every direction (D sweep + two corrections);
+      gfaces: the ng own interface gradient components of the 2 dim faces (compact
+             correction included);
+      face:  the dim faces owned by the element (its +d faces), each point once: averages of
+             the state and gradient (2 (nv + ng)), viscous flux (~60) and Roe (~150) plus the
+             combination (~25);
+      interior: the solution and ng gradient components at the n - 1 interior flux points of
+             every line and the flux there (~85);
+      div:   the M divergence of all n + 1 flux points.
+    Returns the per-step counts and their attribution to the kernels that perform them
+    ("flux" = interior + div: the work of the flux/divergence kernel)."""
     npnt, nq, nf = n ** dim, n ** (dim - 1), 2 * dim
     sw = 2 * n - 1
-    trace = nf * nv * nq * sw
-    vs = nv * dim * npnt * (sw + 4)
-    interior = dim * (n - 1) * nq * ((nv + ng) * sw + 85)
-    div = dim * nv * npnt * (2 * (n + 1) - 1 + 2)
-    return {"flux": trace + vs + interior + div,
-            "face": dim * nq * (2 * (nv + ng) + 235),
-            "grad": trace + vs + nf * ng * nq * (sw + 2)}
+    st = {"trace": nf * nv * nq * sw,
+          "vs": nv * dim * npnt * (sw + 4),
+          "gfaces": nf * ng * nq * (sw + 2),
+          "face": dim * nq * (2 * (nv + ng) + 235),
+          "interior": dim * (n - 1) * nq * ((nv + ng) * sw + 85),
+          "div": dim * nv * npnt * (2 * (n + 1) - 1 + 2)}
+    return {"trace": st["trace"], "grad": st["vs"] + st["gfaces"], "face": st["face"],
+            "flux": st["interior"] + st["div"], "steps": st, "total": sum(st.values())}
 
 
 def curv_flops_per_element(n, nv=5):
@@ -101,8 +108,8 @@ def curv_flops_per_element(n, nv=5):
 
 
 # DRAM traffic of one k_line_flux launch at 48^3 p=4 (FP32, compact), from one ncu capture
-# (dram__bytes_read.sum + dram__bytes_write.sum; profiles/dram_residual_kernels_tgv48_p4_f32.md),
-# valid only while the kernel sources hash to the value recorded with it.
+# (dram__bytes_read.sum + dram__bytes_write.sum of that kernel), valid only while the kernel
+# sources hash to the value recorded with it.
 FLUX_TRAFFIC = {"ne": 48, "bytes": 796335360 + 253035264,
                 "sources_sha256": "a09622cb15fb1beebb215fe8cf6072c867da72f71ace0f77318838e6163d44fe"}
 FLUX_SOURCES = ("paper_2608_09615_b300/csrc/sd_line.cuh", "paper_2608_09615_b300/csrc/sd_kernels.cuh")
@@ -446,11 +453,15 @@ def main():
     flops = residual_flops_per_element(P + 1)
     nelem = int(np.prod(ne))
     flux_avg_ms = kms["flux_div"]
-    fp32_peak = 148 * 128 * 2 * smax * 1e6 / 1e12      # TFLOP/s at the maximum SM clock
+    nsm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    fp32_derived = nsm * 128 * 2 * smax * 1e6 / 1e12    # TFLOP/s at the maximum SM clock
+    # measured FMA throughput (scalar and paired FMA), the roofline's denominator
+    fp32_meas = {"scalar": sd.measure_fp32_peak(False), "paired_f32x2": sd.measure_fp32_peak(True)}
+    fp32_peak = max(fp32_meas.values())
     achieved = flops["flux"] * nelem / (flux_avg_ms * 1e-3) / 1e12
     alg_bytes_res = 2 * 5 * npts * 4                    # read U, write R (FP32)
     res_ms = sum(kms[k] for k in ("trace", "grad", "face", "flux_div"))
-    res_alu = sum(flops.values()) * nelem / (res_ms * 1e-3) / 1e12
+    res_alu = flops["total"] * nelem / (res_ms * 1e-3) / 1e12
 
     # standalone residual rates, FP32 and FP64
     Ug32 = U64.float()
@@ -526,8 +537,11 @@ def main():
                          "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                          "frac": achieved / fp32_peak, "traffic": flux_traffic(ne),
                          "traffic_unit": "bytes per launch (ncu dram read + write)",
-                         "peak_source": "FP32 CUDA-core peak 148 SM x 128 lanes x 2 x %.0f MHz "
-                                        "(derived)" % smax,
+                         "peak_source": "measured FP32 FMA throughput (sd_measure_fp32_peak, the larger "
+                                        "of scalar and paired FMA): %s TFLOP/s; derived %d SM x 128 lanes "
+                                        "x 2 x %.0f MHz = %.1f TFLOP/s"
+                                        % ({k: round(v, 1) for k, v in fp32_meas.items()}, nsm, smax,
+                                           fp32_derived),
                          "flops_per_element": flops["flux"],
                          "avg_launch_ms": flux_avg_ms,
                          "residual": {"ms": res_ms, "alu_tflops": res_alu, "alu_frac": res_alu / fp32_peak,

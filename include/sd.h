@@ -17,8 +17,9 @@
  * element (Sec. 2). NS variables: rho, rho u, rho v, rho w, rho E. Scalar: u.
  *
  * Ownership: the caller owns every state/residual buffer it passes. The context owns
- * all scratch (face-trace buffers, Runge-Kutta registers, staging buffers); everything
- * is allocated in sd_init and freed in sd_destroy -- no call allocates afterwards.
+ * all scratch (face-trace buffers, Runge-Kutta registers, staging buffers), allocated in
+ * sd_init and freed in sd_destroy; afterwards only the calls that say so allocate
+ * (sd_closure_enable, sd_set_rk_stages), each once.
  * Errors: every call returns an sd_status; nothing throws across the ABI. On error the
  * outputs are unspecified and sd_last_error() describes the failure (thread-local).
  * Streams: all device work is enqueued on the context's stream (sd_init / sd_set_stream).
@@ -36,7 +37,7 @@ extern "C" {
 typedef enum {
     SD_OK = 0,
     SD_EINVAL = 1,          /* bad argument (null pointer, size, enum, aliasing)      */
-    SD_ENOMEM = 2,          /* device or host allocation failed (sd_init only)        */
+    SD_ENOMEM = 2,          /* device or host allocation failed (allocating calls)    */
     SD_ECUDA = 3,           /* a CUDA runtime call failed                             */
     SD_EUNSUPPORTED = 4,    /* valid but not supported here (p, dim, shared memory)   */
     SD_ENONFINITE = 5,      /* sd_diagnostics found a NaN/Inf in the state            */
@@ -166,12 +167,30 @@ sd_status sd_residual(sd_ctx* ctx, const void* U, void* R);
  * gives full copy bandwidth; pageable memory works). */
 sd_status sd_residual_host(sd_ctx* ctx, const void* U_host, void* R_host);
 
-/* One explicit time step of the FP64 state U64 (device, sd_state_size doubles), in
- * place: U64 <- U64 + dt-integral of R. Stage arithmetic and the Runge-Kutta registers
- * are FP64 always; with SD_F32 the residual of each stage is evaluated in FP32 on an FP32
- * copy of the stage state. t is the time at the start of the step (the residual is
- * autonomous; t is recorded only). Asynchronous on the context stream. */
+/* One explicit time step of the FP64 state U64 (device, sd_state_size doubles), in place:
+ * U64 <- U64 + dt-integral of R, with the Runge-Kutta scheme rk (Sec. 4.4 integrates in
+ * time with the five-stage, fourth-order strong-stability-preserving scheme of Spiteri and
+ * Ruuth, SD_SSPRK54; SD_RK4 is the classical scheme; SD_LSRK54 the two-register low-storage
+ * scheme of Carpenter and Kennedy). t is the time at the start of the step (the residual
+ * is autonomous; t is recorded only). Asynchronous on the context stream.
+ * How the stages are held depends on the context's precision and stage mode:
+ *   SD_F64 contexts: FP64 residual, FP64 stage states and registers.
+ *   SD_F32 contexts, SD_RK_STAGES_F32 (the default): within a step every stage state is
+ *     U + d_j, U the FP64 state at the start of the step. The increments d_j = O(dt) and
+ *     the stage registers are FP32; each stage's FP32 residual is evaluated on X + d_j,
+ *     X = U minus the reference offsets rounded to FP32 once per step. U itself is updated
+ *     in FP64 once per step (U <- U + d_s).
+ *   SD_F32 contexts, SD_RK_STAGES_F64 (sd_set_rk_stages): FP64 stage states and registers
+ *     as in SD_F64 contexts; only each stage's residual is FP32, evaluated on the FP64 stage
+ *     state (offsets removed) rounded to FP32. */
 sd_status sd_rk_step(sd_ctx* ctx, double* U64, double t, double dt, sd_rk rk);
+
+/* Stage arithmetic of sd_rk_step on an SD_F32 context (see sd_rk_step). Selecting
+ * SD_RK_STAGES_F64 allocates three FP64 state-sized registers the first time (the one call
+ * besides sd_init and sd_closure_enable that allocates; SD_ENOMEM if that fails). On an SD_F64
+ * context only SD_RK_STAGES_F64 is accepted (SD_EUNSUPPORTED otherwise). */
+typedef enum { SD_RK_STAGES_F32 = 0, SD_RK_STAGES_F64 = 1 } sd_rk_stages;
+sd_status sd_set_rk_stages(sd_ctx* ctx, sd_rk_stages mode);
 
 /* FP64 volume diagnostics of the FP64 device state U64 at time t. Synchronises the
  * context stream and writes *out (host). Returns SD_ENONFINITE (with *out filled)
@@ -282,6 +301,13 @@ sd_status sd_closure_enable(sd_ctx* ctx, const void* Wb, const float* P, const f
  * them one stream, or order them). No memory is allocated by this call. */
 sd_status sd_residual_f32_noalloc(const sd_mesh* mesh, int p, sd_scheme scheme,
                                   const sd_physics* phys, const float* U, float* R, void* stream);
+
+/* FP32 FMA throughput of the current device in TFLOP/s (FMA = 2 flops), measured by a
+ * fully occupied kernel of independent FMA chains; the denominator of the residual kernels'
+ * ALU roofline. Not part of the method (the paper has no counterpart). packed = 0: scalar
+ * fma.rn.f32; packed = 1: paired fma.rn.f32x2. Synchronous; allocates and frees 1 KB of
+ * device memory and its own stream; takes about 20 ms. */
+sd_status sd_measure_fp32_peak(int packed, double* tflops);
 
 const char* sd_status_str(sd_status s);
 /* Text of the last error raised on the calling thread ("" if none). */

@@ -21,8 +21,12 @@ Readings of the paper used here (where it is silent or garbled):
 
 Pinned by tests/test_oracle_residual.py (free stream; the closed-form responses of a heat
 conduction and an entropy wave; Roe's textbook properties: consistency, pure upwinding of
-supersonic pairs, exact resolution of a stationary contact), tests/test_oracle_variants.py (options (a) and (b) of the
-interface viscous flux) and tests/test_oracle_curvilinear.py (the Riemann flux along a
+supersonic pairs, exact resolution of a stationary contact), tests/test_oracle_physics_pins.py
+(Sutherland's law away from T0: the textbook air ratios and a closed-form heat conduction
+with T/T0 in [0.77, 1.43]; the viscous stress with its transpose and lambda = 0: closed-form
+viscous residuals of a compressive and a shear velocity field; Harten's fix: the exact Roe
+flux of a pure near-sonic acoustic wave), tests/test_oracle_variants.py (options (a) and (b)
+of the interface viscous flux) and tests/test_oracle_curvilinear.py (the Riemann flux along a
 general normal: the axis-aligned case, rotation equivariance, consistency).
 """
 from dataclasses import dataclass
@@ -170,6 +174,12 @@ class NavierStokes:
     def flux(self, U, grad, m):
         return self.convective_flux(U, m) - self.viscous_flux(U, grad, m)
 
+    def entropy_fix(self, lam, c):
+        """Harten's entropy fix of an acoustic eigenvalue magnitude |lambda| (Sec. 4.4, reading
+        R8): below delta = harten * c it is replaced by (lambda^2 + delta^2) / (2 delta)."""
+        delta = self.prm.harten * c
+        return np.where(lam < delta, (lam ** 2 + delta ** 2) / (2.0 * delta), lam)
+
     def riemann(self, UL, UR, m):
         if self.prm.riemann == "roe":
             return self.roe(UL, UR, m)
@@ -211,10 +221,9 @@ class NavierStokes:
         lam1 = np.abs(qn - c)
         lam2 = np.abs(qn)
         lam5 = np.abs(qn + c)
-        delta = self.prm.harten * c
         if self.prm.harten > 0.0:
-            lam1 = np.where(lam1 < delta, (lam1 ** 2 + delta ** 2) / (2.0 * delta), lam1)
-            lam5 = np.where(lam5 < delta, (lam5 ** 2 + delta ** 2) / (2.0 * delta), lam5)
+            lam1 = self.entropy_fix(lam1, c)
+            lam5 = self.entropy_fix(lam5, c)
         a1 = (dp - rt * c * dvn) / (2.0 * c2)
         a2 = drho - dp / c2
         a5 = (dp + rt * c * dvn) / (2.0 * c2)
@@ -274,10 +283,9 @@ class NavierStokes:
         lam1 = np.abs(qn - c)
         lam2 = np.abs(qn)
         lam5 = np.abs(qn + c)
-        delta = self.prm.harten * c
         if self.prm.harten > 0.0:
-            lam1 = np.where(lam1 < delta, (lam1 ** 2 + delta ** 2) / (2.0 * delta), lam1)
-            lam5 = np.where(lam5 < delta, (lam5 ** 2 + delta ** 2) / (2.0 * delta), lam5)
+            lam1 = self.entropy_fix(lam1, c)
+            lam5 = self.entropy_fix(lam5, c)
         a1 = (dp - rt * c * dvn) / (2.0 * c2)
         a2 = drho - dp / c2
         a5 = (dp + rt * c * dvn) / (2.0 * c2)

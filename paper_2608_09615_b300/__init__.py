@@ -26,6 +26,7 @@ VISCOUS_FLUX = {"a": 0, "b": 1}
 PME_COEF = {"flux": 0, "solution": 1}
 PRECISIONS = {"f64": 0, "f32": 1}
 RK = {"rk4": 0, "ssprk54": 1, "lsrk54": 2}
+RK_STAGES = {"f32": 0, "f64": 1}
 
 
 class SDError(RuntimeError):
@@ -62,7 +63,7 @@ EXPORTS = ("sd_init", "sd_destroy", "sd_set_stream", "sd_state_size", "sd_nvar",
            "sd_mlp_adam", "sd_residual_f32_noalloc", "sd_set_flux_tau", "sd_closure_data",
            "sd_filter_matrix", "sd_filter_project", "sd_closure_targets", "sd_colstats",
            "sd_standardise", "sd_unstandardise", "sd_closure_enable", "sd_init_curvilinear",
-           "sd_is_curvilinear")
+           "sd_is_curvilinear", "sd_set_rk_stages", "sd_measure_fp32_peak")
 KERNEL_CLASSES = ("trace", "grad", "flux_div", "other", "face")
 
 _lib_handle = None
@@ -102,6 +103,10 @@ def load_library(path=LIB_PATH):
     lib.sd_residual_host.restype = I
     lib.sd_rk_step.argtypes = [P, P, D, D, I]
     lib.sd_rk_step.restype = I
+    lib.sd_measure_fp32_peak.argtypes = [I, P]
+    lib.sd_measure_fp32_peak.restype = I
+    lib.sd_set_rk_stages.argtypes = [P, I]
+    lib.sd_set_rk_stages.restype = I
     lib.sd_diagnostics.argtypes = [P, P, D, ctypes.POINTER(_Diag)]
     lib.sd_diagnostics.restype = I
     lib.sd_status_str.argtypes = [I]
@@ -150,6 +155,13 @@ def load_library(path=LIB_PATH):
     lib.sd_closure_enable.restype = I
     _lib_handle = lib
     return lib
+
+
+def measure_fp32_peak(packed=False):
+    """Measured FP32 FMA throughput of the current device, TFLOP/s (sd_measure_fp32_peak)."""
+    out = ctypes.c_double()
+    _check(load_library().sd_measure_fp32_peak(int(bool(packed)), ctypes.byref(out)), "sd_measure_fp32_peak")
+    return out.value
 
 
 def _check(status, where):
@@ -232,23 +244,34 @@ def sd_init_curvilinear(nodes, p, scheme, physics, precision, stream=None):
 def sd_residual_f32_noalloc(dim, ne, lo, hi, p, scheme, physics, U, R, stream=None):
     """FP32 residual through the allocation-free entry point (no context, no device
     allocation; the library's static scratch is shared by all calls). U, R: contiguous
-    CUDA float32 tensors in the state layout."""
+    CUDA float32 tensors on one device, each holding the nvar * prod(ne) * (p+1)^dim values
+    of the state layout. The call runs on U's device."""
     import torch
     for t, nm in ((U, "U"), (R, "R")):
         if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float32 or \
                 not t.is_contiguous():
             raise ValueError("%s must be a contiguous CUDA float32 tensor" % nm)
-    if U.numel() != R.numel():
-        raise ValueError("U and R differ in size")
+    if U.device != R.device:
+        raise ValueError("U and R must be on the same device")
     ne = list(ne) + [1] * (3 - len(ne))
+    nelem = 1
+    for d in range(dim):
+        nelem *= int(ne[d])
+    nvar = 5 if physics.kind == "ns" else 1
+    expect = nvar * nelem * (int(p) + 1) ** int(dim)
+    for t, nm in ((U, "U"), (R, "R")):
+        if t.numel() != expect:
+            raise ValueError("%s must hold %d values (nvar %d, %d elements, p = %d), not %d"
+                             % (nm, expect, nvar, nelem, p, t.numel()))
     lo = list(lo) + [0.0] * (3 - len(lo))
     hi = list(hi) + [1.0] * (3 - len(hi))
     m = _Mesh(dim, (ctypes.c_int * 3)(*ne), (ctypes.c_double * 3)(*lo), (ctypes.c_double * 3)(*hi))
     ph = physics.to_c()
-    _check(load_library().sd_residual_f32_noalloc(ctypes.byref(m), int(p), SCHEMES[scheme],
-                                                  ctypes.byref(ph), ctypes.c_void_p(U.data_ptr()),
-                                                  ctypes.c_void_p(R.data_ptr()),
-                                                  _stream_handle(stream)), "sd_residual_f32_noalloc")
+    with torch.cuda.device(U.device):
+        st = load_library().sd_residual_f32_noalloc(ctypes.byref(m), int(p), SCHEMES[scheme],
+                                                    ctypes.byref(ph), ctypes.c_void_p(U.data_ptr()),
+                                                    ctypes.c_void_p(R.data_ptr()), _stream_handle(stream))
+    _check(st, "sd_residual_f32_noalloc")
     return R
 
 
@@ -354,6 +377,11 @@ class SD:
 
     def rk_step(self, U64, t, dt, rk="ssprk54"):
         sd_rk_step(self._ctx, U64, t, dt, rk, self.numel)
+
+    def set_rk_stages(self, mode):
+        """Stage arithmetic of rk_step on an FP32 context: "f32" (FP32 stage increments, the
+        default) or "f64" (FP64 stage states; allocates three FP64 registers once)."""
+        _check(load_library().sd_set_rk_stages(self._ctx, RK_STAGES[mode]), "sd_set_rk_stages")
 
     def diagnostics(self, U64, t=0.0, raise_nonfinite=True):
         return sd_diagnostics(self._ctx, U64, t, self.numel, raise_nonfinite)

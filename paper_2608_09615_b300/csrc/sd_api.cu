@@ -266,7 +266,7 @@ static void free_all(sd_ctx* c) {
         if (c->ev_out[k]) cudaEventDestroy(c->ev_out[k]);
     }
     if (c->cl_tmode) cudaFree(c->cl_tmode);
-    void* ptrs[] = {c->Tu, c->Tg, c->Fh, c->S, c->K, c->rA, c->rB, c->rC, c->rX, c->dW,
+    void* ptrs[] = {c->Tu, c->Tg, c->Fh, c->S, c->K, c->rA, c->rB, c->rC, c->rX, c->rA64, c->rB64, c->rC64, c->dW,
                     c->partial, c->partial2, c->dsum, c->hU, c->hR, c->cih, c->cvs, c->cTg, c->cgeo64};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -280,11 +280,12 @@ static int ipow_h(int b, int e) {
     return r;
 }
 
-extern "C" sd_status sd_init(const sd_mesh* mesh, int p, sd_scheme scheme, const sd_physics* phys,
-                             sd_precision prec, void* stream, sd_ctx** out) {
-    g_err[0] = 0;
-    if (!mesh || !phys || !out) { sdi_set_error("null argument"); return SD_EINVAL; }
-    *out = nullptr;
+// Validate a problem description and fill the context's problem fields, operators and
+// scratch sizes (no CUDA call, no allocation). Shared by sd_init and the allocation-free
+// entry point, so both accept exactly the same problems.
+sd_status sdi_setup(const sd_mesh* mesh, int p, sd_scheme scheme, const sd_physics* phys, sd_precision prec,
+                    void* stream, sd_ctx* c) {
+    if (!mesh || !phys) { sdi_set_error("null argument"); return SD_EINVAL; }
     if (mesh->dim != 1 && mesh->dim != 3) { sdi_set_error("dim must be 1 or 3"); return SD_EUNSUPPORTED; }
     if (p < 1 || p > SD_MAX_N - 1) { sdi_set_error("p must be in 1..%d", SD_MAX_N - 1); return SD_EUNSUPPORTED; }
     if (scheme != SD_BR1 && scheme != SD_COMPACT) { sdi_set_error("bad scheme"); return SD_EINVAL; }
@@ -320,8 +321,7 @@ extern "C" sd_status sd_init(const sd_mesh* mesh, int p, sd_scheme scheme, const
     }
     if (nelem > (1LL << 30)) { sdi_set_error("too many elements"); return SD_EUNSUPPORTED; }
 
-    sd_ctx* c = (sd_ctx*)calloc(1, sizeof(sd_ctx));
-    if (!c) return SD_ENOMEM;
+    memset(c, 0, sizeof(*c));
     c->dim = mesh->dim;
     for (int d = 0; d < 3; ++d) {
         c->ne[d] = d < mesh->dim ? mesh->ne[d] : 1;
@@ -364,10 +364,27 @@ extern "C" sd_status sd_init(const sd_mesh* mesh, int p, sd_scheme scheme, const
         const size_t diag = (size_t)(NV * np + 2 * 2 * DIM * NV * nq + NV * DIM * np) * sizeof(double);
         if (blk > 227 * 1024 || diag > 227 * 1024) {
             sdi_set_error("n = %d needs %zu bytes of shared memory per block", n, blk);
-            free(c);
             return SD_EUNSUPPORTED;
         }
     }
+    return SD_OK;
+}
+
+extern "C" sd_status sd_init(const sd_mesh* mesh, int p, sd_scheme scheme, const sd_physics* phys,
+                             sd_precision prec, void* stream, sd_ctx** out) {
+    g_err[0] = 0;
+    if (!mesh || !phys || !out) { sdi_set_error("null argument"); return SD_EINVAL; }
+    *out = nullptr;
+    sd_ctx* c = (sd_ctx*)calloc(1, sizeof(sd_ctx));
+    if (!c) return SD_ENOMEM;
+    {
+        const sd_status st = sdi_setup(mesh, p, scheme, phys, prec, stream, c);
+        if (st != SD_OK) {
+            free(c);
+            return st;
+        }
+    }
+    const int np = ipow_h(c->n, c->dim);
     if (cudaGetDevice(&c->device) != cudaSuccess) {
         sdi_set_error("no CUDA device");
         free(c);
@@ -796,6 +813,36 @@ static sd_status rk_step_f64(sd_ctx* c, double* U, double dt, sd_rk rk) {
     return SD_OK;
 }
 
+// FP32 contexts with FP64 stage states (sd_set_rk_stages(ctx, SD_RK_STAGES_F64)): the
+// registers and every stage combination in FP64, as in FP64 contexts; each stage's FP32
+// residual is evaluated on the stage state rounded to FP32 (offsets removed in FP64 first)
+static sd_status rk_step_f32_f64stages(sd_ctx* c, double* U, double dt, sd_rk rk) {
+    const size_t n = c->nstate;
+    float* S = (float*)c->S;
+    float* K = (float*)c->K;
+    double *rA = c->rA64, *rB = c->rB64, *rC = c->rC64;
+    const int gb = grid_for(n);
+    cudaStream_t st = c->stream;
+    sdk::StageOff so;
+    so.npts = c->npts;
+    sdk::stage_offsets(c, so.off0, so.off4);
+    sdi_prof_begin(c, SD_K_OTHER);
+    sdk::k_to_real<float><<<gb, 256, 0, st>>>(U, S, n, so);
+    sdi_prof_end(c, SD_K_OTHER);
+    sd_status s;
+    const int nst = rk == SD_RK4 ? 4 : 5;
+    for (int k = 0; k < nst; ++k) {
+        if ((s = residual_any(c, S, K, 1)) != SD_OK) return s;
+        sdi_prof_begin(c, SD_K_OTHER);
+        if (rk == SD_RK4) sdk::k_rk4<float><<<gb, 256, 0, st>>>(k, U, rA, K, S, dt, n, so);
+        else if (rk == SD_SSPRK54) sdk::k_ssp<float><<<gb, 256, 0, st>>>(k, U, rA, rB, rC, K, S, dt, kSSP, n, so);
+        else sdk::k_lsrk<float><<<gb, 256, 0, st>>>(U, rA, K, S, kLSA[k], kLSB[k], dt, n, so);
+        sdi_prof_end(c, SD_K_OTHER);
+    }
+    CK(cudaGetLastError());
+    return SD_OK;
+}
+
 // FP32 contexts: FP32 stage increments, FP64 accumulation of the state once per step
 static sd_status rk_step_f32(sd_ctx* c, double* U, double dt, sd_rk rk) {
     const size_t n = c->nstate;
@@ -843,8 +890,39 @@ extern "C" sd_status sd_rk_step(sd_ctx* c, double* U64, double t, double dt, sd_
         sdi_set_error("bad Runge-Kutta scheme");
         return SD_EINVAL;
     }
-    if (c->prec == SD_F32) return rk_step_f32(c, U64, dt, rk);
+    if (c->prec == SD_F32) {
+        if (c->rk_stages == SD_RK_STAGES_F64) return rk_step_f32_f64stages(c, U64, dt, rk);
+        return rk_step_f32(c, U64, dt, rk);
+    }
     return rk_step_f64(c, U64, dt, rk);
+}
+
+extern "C" sd_status sd_set_rk_stages(sd_ctx* c, sd_rk_stages mode) {
+    if (!c) { sdi_set_error("null argument"); return SD_EINVAL; }
+    if (mode != SD_RK_STAGES_F32 && mode != SD_RK_STAGES_F64) { sdi_set_error("bad stage mode"); return SD_EINVAL; }
+    if (c->prec == SD_F64) {
+        // FP64 contexts always keep FP64 stage states
+        if (mode != SD_RK_STAGES_F64) {
+            sdi_set_error("FP64 contexts keep FP64 stage states");
+            return SD_EUNSUPPORTED;
+        }
+        return SD_OK;
+    }
+    if (mode == SD_RK_STAGES_F64 && !c->rA64) {
+        // the three FP64 registers, allocated once on first use
+        const size_t bytes = c->nstate * sizeof(double);
+        if (cudaMalloc((void**)&c->rA64, bytes) != cudaSuccess || cudaMalloc((void**)&c->rB64, bytes) != cudaSuccess ||
+            cudaMalloc((void**)&c->rC64, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            if (c->rA64) cudaFree(c->rA64);
+            if (c->rB64) cudaFree(c->rB64);
+            c->rA64 = c->rB64 = c->rC64 = nullptr;
+            sdi_set_error("device allocation of the FP64 stage registers failed");
+            return SD_ENOMEM;
+        }
+    }
+    c->rk_stages = mode;
+    return SD_OK;
 }
 
 // ------------------------------------------------------------------ diagnostics

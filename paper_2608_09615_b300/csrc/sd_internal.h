@@ -49,6 +49,9 @@ struct sd_ctx {
     // states, FP32 contexts keep stage increments (the state itself accumulates in FP64)
     void *rA, *rB, *rC;
     void* rX;                // FP32 contexts: the step's start state minus the offsets
+    // FP32 contexts in SD_RK_STAGES_F64 mode: FP64 stage registers (allocated on first use)
+    sd_rk_stages rk_stages;
+    double *rA64, *rB64, *rC64;
     double* dW;              // Gauss weights (device, n values)
     double* partial;         // diagnostics block partials
     double* partial2;        // second-level partials (DIAG_L1 x NDIAG)
@@ -124,6 +127,10 @@ sd_status sdi_diag(sd_ctx* c, const double* U64, double* host_out);
 sd_status sdi_check_smem(sd_ctx* c);
 void sdi_set_error(const char* fmt, ...);
 void sdi_build_operators(sd_ctx* c);
+// validate a problem and fill the problem fields, operators and scratch sizes of c
+// (no CUDA call, no allocation; c is overwritten)
+sd_status sdi_setup(const sd_mesh* mesh, int p, sd_scheme scheme, const sd_physics* phys, sd_precision prec,
+                    void* stream, sd_ctx* c);
 
 // size of the static scratch of sd_residual_f32_noalloc (FP32 values, 36 MiB)
 #define SD_NOALLOC_SCRATCH_FLOATS (9 * 1024 * 1024)

@@ -149,6 +149,13 @@ static bool set_smem(K kernel, size_t bytes) {
                                 (int)bytes) == cudaSuccess;
 }
 
+// the status of a launch whose kernel cannot get the shared memory it needs, with a message
+inline sd_status smem_fail(size_t bytes) {
+    sdi_set_error("a residual kernel needs %zu bytes of shared memory per block, more than the device grants",
+                  bytes);
+    return SD_EUNSUPPORTED;
+}
+
 // number of SMs of a device (cached)
 inline int sm_count(int device) {
     static std::mutex mu;
@@ -187,7 +194,7 @@ static sd_status features_impl(sd_ctx* c, const real* U, float* X, int offset_in
     const Mesh g = make_mesh(c);
     const Phys<real> P = make_phys<real>(c);
     const size_t sg = LL::NBR_BYTES + (size_t)LL::EB * LL::PER_GRAD * sizeof(real);
-    if (!set_smem(k_line_features<real, N>, sg)) return SD_EUNSUPPORTED;
+    if (!set_smem(k_line_features<real, N>, sg)) return smem_fail(sg);
     const int blocks = (g.nelem + LL::EB - 1) / LL::EB;
     const sd_physics& s = c->phys;
     sdi_prof_begin(c, SD_K_OTHER);
@@ -205,7 +212,7 @@ static sd_status fluxmean_impl(sd_ctx* c, const real* U, double* out, int offset
     const Mesh g = make_mesh(c);
     const Phys<real> P = make_phys<real>(c);
     const size_t sg = LL::NBR_BYTES + (size_t)LL::EB * LL::PER_GRAD * sizeof(real);
-    if (!set_smem(k_line_fluxmean<real, N>, sg)) return SD_EUNSUPPORTED;
+    if (!set_smem(k_line_fluxmean<real, N>, sg)) return smem_fail(sg);
     const int blocks = (g.nelem + LL::EB - 1) / LL::EB;
     sdi_prof_begin(c, SD_K_OTHER);
     k_line_fluxmean<real, N><<<blocks, LL::THREADS, sg, c->stream>>>(
@@ -241,7 +248,7 @@ static sd_status residual_phase(sd_ctx* c, const real* U, real* R, int offset_in
     real* Fh = static_cast<real*>(c->Fh);
     if (phase == SDI_PH_TRACE) {
         const size_t st = TracePipe<real, LL>::BYTES;
-        if (!set_smem(k_line_trace<real, N, DIM, NV>, st)) return SD_EUNSUPPORTED;
+        if (!set_smem(k_line_trace<real, N, DIM, NV>, st)) return smem_fail(st);
         const int bt = persistent_grid(k_line_trace<real, N, DIM, NV>, LL::THREADS, st, (ne + LL::EB - 1) / LL::EB,
                                        c->device);
         sdi_prof_begin(c, SD_K_TRACE);
@@ -249,7 +256,7 @@ static sd_status residual_phase(sd_ctx* c, const real* U, real* R, int offset_in
         sdi_prof_end(c, SD_K_TRACE);
     } else if (phase == SDI_PH_GRAD) {
         const size_t sg = GradPipe<real, LL>::BYTES;
-        if (!set_smem(k_line_grad<real, N, DIM, NV>, sg)) return SD_EUNSUPPORTED;
+        if (!set_smem(k_line_grad<real, N, DIM, NV>, sg)) return smem_fail(sg);
         const int bg = persistent_grid(k_line_grad<real, N, DIM, NV>, LL::THREADS, sg, (ne + LL::EB - 1) / LL::EB,
                                        c->device);
         sdi_prof_begin(c, SD_K_GRAD);
@@ -263,7 +270,7 @@ static sd_status residual_phase(sd_ctx* c, const real* U, real* R, int offset_in
         sdi_prof_end(c, SD_K_FACE);
     } else {
         const size_t sf = FluxPipe<real, FL>::BYTES;
-        if (!set_smem(k_line_flux<real, N, DIM, NV>, sf)) return SD_EUNSUPPORTED;
+        if (!set_smem(k_line_flux<real, N, DIM, NV>, sf)) return smem_fail(sf);
         const int bf = persistent_grid(k_line_flux<real, N, DIM, NV>, FL::THREADS, sf, (ne + FL::EB - 1) / FL::EB,
                                        c->device);
         sdi_prof_begin(c, SD_K_FLUX);
@@ -350,7 +357,7 @@ static sd_status closure_data_dispatch(sd_ctx* c, const real* U, float* X, doubl
         const LineGeo<real> geo = make_geo<real>(c, offset_in);                                  \
         const Mesh g = make_mesh(c);                                                             \
         const size_t stb = TracePipe<real, LL>::BYTES;                                           \
-        if (!set_smem(k_line_trace<real, NN, 3, 5>, stb)) return SD_EUNSUPPORTED;               \
+        if (!set_smem(k_line_trace<real, NN, 3, 5>, stb)) return smem_fail(stb);               \
         const int btr = persistent_grid(k_line_trace<real, NN, 3, 5>, LL::THREADS, stb,          \
                                         (g.nelem + LL::EB - 1) / LL::EB, c->device);            \
         k_line_trace<real, NN, 3, 5><<<btr, LL::THREADS, stb, c->stream>>>(                      \

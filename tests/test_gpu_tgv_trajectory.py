@@ -27,8 +27,10 @@ T_END = 10.0
 EVERY = 0.1
 
 
-def run(precision, scheme="compact"):
+def run(precision, scheme="compact", stages=None):
     ctx = sd.SD(3, NE, (0.0,) * 3, (2 * math.pi,) * 3, P, scheme, sd.Physics(kind="ns"), precision)
+    if stages is not None:
+        ctx.set_rk_stages(stages)
     U = torch.from_numpy(inputs.tgv_3d(NE, P)).cuda()
     steps_per = int(round(EVERY / DT))
     nsamp = int(round(T_END / EVERY))
@@ -45,7 +47,10 @@ def run(precision, scheme="compact"):
 
 @pytest.fixture(scope="module")
 def trajectories():
-    return {prec: run(prec) for prec in ("f64", "f32")}
+    out = {prec: run(prec) for prec in ("f64", "f32")}
+    # the FP32 residual with FP64 stage states (sd_set_rk_stages), the alternative stage mode
+    out["f32_f64stages"] = run("f32", stages="f64")
+    return out
 
 
 def dissipation(rec):
@@ -65,13 +70,25 @@ def test_fp32_dissipation_matches_fp64(trajectories, capsys):
     assert err <= 1e-3
 
 
+def test_fp32_dissipation_with_fp64_stages(trajectories, capsys):
+    # The same criterion for the other stage mode of FP32 contexts (FP64 stage states and
+    # registers, FP32 residual only); both modes stay within the bound.
+    ke64, eps64 = dissipation(trajectories["f64"])
+    ke32, eps32 = dissipation(trajectories["f32_f64stages"])
+    err = np.abs(eps32 - eps64).max() / np.abs(eps64).max()
+    with capsys.disabled():
+        print("\nTGV 16^3 p4 Re1600 to t=10, FP32 residual with FP64 stages: "
+              "max|eps32-eps64|/max|eps64| = %.3e" % err)
+    assert err <= 1e-3
+
+
 def test_initial_state_and_conservation(trajectories):
     # FP64 residuals conserve to FP64 round-off per step (accumulated over 8000 steps).
     # FP32 residuals use FP32-rounded operator weights, for which sum_i w_i M_if equals
     # +-delta only to ~6e-8 relative: each interface leaks that fraction of its flux, and
     # the energy flux (rho E + p) u carries rho E ~ 180 at Ma = 0.1, so the total energy
     # drifts systematically at the 1e-8 level over the run.
-    tol = {"f64": (1e-11, 1e-10), "f32": (1e-7, 1e-7)}
+    tol = {"f64": (1e-11, 1e-10), "f32": (1e-7, 1e-7), "f32_f64stages": (1e-7, 1e-7)}
     for prec, rec in trajectories.items():
         r0 = rec[0]
         rel, mom = tol[prec]
