@@ -179,7 +179,9 @@ sd_status sd_residual_host(sd_ctx* ctx, const void* U_host, void* R_host);
  *     U + d_j, U the FP64 state at the start of the step. The increments d_j = O(dt) and
  *     the stage registers are FP32; each stage's FP32 residual is evaluated on X + d_j,
  *     X = U minus the reference offsets rounded to FP32 once per step. U itself is updated
- *     in FP64 once per step (U <- U + d_s).
+ *     in FP64 once per step (U <- U + d_s). On Cartesian grids SD_SSPRK54 applies each stage
+ *     update inside the residual's last kernel (same arithmetic, same result to the bit as
+ *     sd_rk_prepare followed by sd_rk_stage).
  *   SD_F32 contexts, SD_RK_STAGES_F64 (sd_set_rk_stages): FP64 stage states and registers
  *     as in SD_F64 contexts; only each stage's residual is FP32, evaluated on the FP64 stage
  *     state (offsets removed) rounded to FP32. */
@@ -191,6 +193,54 @@ sd_status sd_rk_step(sd_ctx* ctx, double* U64, double t, double dt, sd_rk rk);
  * context only SD_RK_STAGES_F64 is accepted (SD_EUNSUPPORTED otherwise). */
 typedef enum { SD_RK_STAGES_F32 = 0, SD_RK_STAGES_F64 = 1 } sd_rk_stages;
 sd_status sd_set_rk_stages(sd_ctx* ctx, sd_rk_stages mode);
+
+/* sd_rk_step one stage at a time, for callers that must act between stages (a decomposed
+ * grid refreshes the ghost elements of every stage input from its neighbours). sd_rk_prepare
+ * writes the first stage input from U64 and returns it in *input (a device array owned by
+ * the context: sd_state_size values of the residual precision, offsets removed from rho and
+ * rho E for Navier-Stokes). sd_rk_stage(k) evaluates the residual of the current stage input,
+ * applies stage k of rk and returns the next stage input in *input (NULL after the last
+ * stage, which updates U64). k runs 0 .. 3 (SD_RK4) or 0 .. 4; sd_rk_prepare followed by all
+ * stages is exactly sd_rk_step. Asynchronous on the context stream. */
+sd_status sd_rk_prepare(sd_ctx* ctx, double* U64, void** input);
+sd_status sd_rk_stage(sd_ctx* ctx, double* U64, int k, double dt, sd_rk rk, void** input);
+
+/* ---- Sub-domains of a decomposed grid (Secs. 2.1-2.3: the residual of an element reads
+ * the elements of its stencil only: compact max|d| <= 1 and |d|_1 <= 2, BR1 |d|_1 <= 2).
+ * A sub-domain context is an sd_init context over the owned block extended by ghost layers;
+ * its residual is exact on the owned block once the ghosts hold the neighbours' data. These
+ * calls move that data; the caller decides which elements go where (paper_2608_09615_b300.decomp
+ * builds the lists and runs the exchanges). Element and face index lists are device int32
+ * arrays; indices outside the context's grid are skipped, never accessed. Asynchronous. */
+
+/* buf[v][k][p] = U[v][elems[k]][p] for k < count (whole elements, every variable), and the
+ * inverse. U: a state in the context's layout whose values are value_bytes (4 or 8) wide (the
+ * residual precision's stage inputs, or an FP64 state on any context); buf: count * nvar * n^dim
+ * such values. The values are copied as raw words. */
+sd_status sd_pack_elements(sd_ctx* ctx, const void* U, int value_bytes, const int* elems, int count, void* buf);
+sd_status sd_unpack_elements(sd_ctx* ctx, const void* buf, int value_bytes, const int* elems, int count,
+                             void* U);
+
+/* Values in one face block of the context's own-interface-gradient buffer (0 on curved grids). */
+size_t sd_face_gradient_size(const sd_ctx* ctx);
+/* Face blocks (elems[k], faces[k]) of the own-interface-gradient buffer written by
+ * sd_residual_begin, gathered into buf (count * sd_face_gradient_size values), and the
+ * inverse: the BR1 scheme's second exchange (Eq. v:e), between sd_residual_begin and
+ * sd_residual_end. Faces: 2 d for the -d face, 2 d + 1 for the +d face. Cartesian grids. */
+sd_status sd_pack_face_gradients(sd_ctx* ctx, const int* elems, const int* faces, int count, void* buf);
+sd_status sd_unpack_face_gradients(sd_ctx* ctx, const void* buf, const int* elems, const int* faces,
+                                   int count);
+
+/* sd_residual in two halves: begin = the traces and each element's own interface gradients
+ * (Sec. 2.3 steps 1-4 up to the interface values); end = the common interface fluxes and the
+ * divergence (steps 4-5), reading what begin left in the context. sd_residual_begin followed
+ * by sd_residual_end equals sd_residual. Cartesian grids, without the learned closure. */
+sd_status sd_residual_begin(sd_ctx* ctx, const void* U);
+sd_status sd_residual_end(sd_ctx* ctx, const void* U, void* R);
+
+/* Restrict sd_diagnostics to the elements [lo[d], hi[d]) along each axis (a sub-domain's
+ * owned block; the reported volume is the block's); lo = hi = NULL removes the restriction. */
+sd_status sd_set_owned_box(sd_ctx* ctx, const int* lo, const int* hi);
 
 /* FP64 volume diagnostics of the FP64 device state U64 at time t. Synchronises the
  * context stream and writes *out (host). Returns SD_ENONFINITE (with *out filled)

@@ -63,7 +63,10 @@ EXPORTS = ("sd_init", "sd_destroy", "sd_set_stream", "sd_state_size", "sd_nvar",
            "sd_mlp_adam", "sd_residual_f32_noalloc", "sd_set_flux_tau", "sd_closure_data",
            "sd_filter_matrix", "sd_filter_project", "sd_closure_targets", "sd_colstats",
            "sd_standardise", "sd_unstandardise", "sd_closure_enable", "sd_init_curvilinear",
-           "sd_is_curvilinear", "sd_set_rk_stages", "sd_measure_fp32_peak")
+           "sd_is_curvilinear", "sd_set_rk_stages", "sd_measure_fp32_peak", "sd_rk_prepare",
+           "sd_rk_stage", "sd_pack_elements", "sd_unpack_elements", "sd_face_gradient_size",
+           "sd_pack_face_gradients", "sd_unpack_face_gradients", "sd_residual_begin",
+           "sd_residual_end", "sd_set_owned_box")
 KERNEL_CLASSES = ("trace", "grad", "flux_div", "other", "face")
 
 _lib_handle = None
@@ -103,6 +106,26 @@ def load_library(path=LIB_PATH):
     lib.sd_residual_host.restype = I
     lib.sd_rk_step.argtypes = [P, P, D, D, I]
     lib.sd_rk_step.restype = I
+    lib.sd_rk_prepare.argtypes = [P, P, ctypes.POINTER(P)]
+    lib.sd_rk_prepare.restype = I
+    lib.sd_rk_stage.argtypes = [P, P, I, D, I, ctypes.POINTER(P)]
+    lib.sd_rk_stage.restype = I
+    lib.sd_pack_elements.argtypes = [P, P, I, P, I, P]
+    lib.sd_pack_elements.restype = I
+    lib.sd_unpack_elements.argtypes = [P, P, I, P, I, P]
+    lib.sd_unpack_elements.restype = I
+    lib.sd_face_gradient_size.argtypes = [P]
+    lib.sd_face_gradient_size.restype = S
+    lib.sd_pack_face_gradients.argtypes = [P, P, P, I, P]
+    lib.sd_pack_face_gradients.restype = I
+    lib.sd_unpack_face_gradients.argtypes = [P, P, P, P, I]
+    lib.sd_unpack_face_gradients.restype = I
+    lib.sd_residual_begin.argtypes = [P, P]
+    lib.sd_residual_begin.restype = I
+    lib.sd_residual_end.argtypes = [P, P, P]
+    lib.sd_residual_end.restype = I
+    lib.sd_set_owned_box.argtypes = [P, P, P]
+    lib.sd_set_owned_box.restype = I
     lib.sd_measure_fp32_peak.argtypes = [I, P]
     lib.sd_measure_fp32_peak.restype = I
     lib.sd_set_rk_stages.argtypes = [P, I]
@@ -378,6 +401,16 @@ class SD:
     def rk_step(self, U64, t, dt, rk="ssprk54"):
         sd_rk_step(self._ctx, U64, t, dt, rk, self.numel)
 
+    def set_owned_box(self, lo, hi):
+        """Restrict the diagnostics to the elements [lo, hi) per axis (a sub-domain's owned
+        block); None removes the restriction."""
+        if lo is None:
+            _check(load_library().sd_set_owned_box(self._ctx, None, None), "sd_set_owned_box")
+            return
+        a = (ctypes.c_int * 3)(*lo)
+        b = (ctypes.c_int * 3)(*hi)
+        _check(load_library().sd_set_owned_box(self._ctx, a, b), "sd_set_owned_box")
+
     def set_rk_stages(self, mode):
         """Stage arithmetic of rk_step on an FP32 context: "f32" (FP32 stage increments, the
         default) or "f64" (FP64 stage states; allocates three FP64 registers once)."""
@@ -553,6 +586,110 @@ class MLP:
 
 def _ptr(t):
     return ctypes.c_void_p(t.data_ptr())
+
+
+class DevicePointer:
+    """A device array owned by a context (a Runge-Kutta stage input), usable wherever a
+    tensor's data_ptr() is read."""
+
+    def __init__(self, ptr):
+        self.ptr = int(ptr or 0)
+
+    def data_ptr(self):
+        return self.ptr
+
+
+# ---------------------------------------------------------------- sub-domain primitives
+def _idx_ptr(t, name):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.int32 or not t.is_contiguous():
+        raise ValueError("%s must be a contiguous CUDA int32 tensor" % name)
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _elem_values(ctx):
+    return ctx.nvar * ctx.n ** ctx.dim
+
+
+def _state_dtype(ctx, U):
+    import torch
+    dt = getattr(U, "dtype", None)
+    if dt is None:
+        return ctx.dtype                 # a context-owned stage input: the residual precision
+    if dt not in (torch.float32, torch.float64) or not U.is_cuda or not U.is_contiguous() or \
+            U.numel() != ctx.numel:
+        raise ValueError("U must be a contiguous CUDA float32/float64 state of %d values" % ctx.numel)
+    return dt
+
+
+def pack_elements(ctx, U, elems):
+    """Whole elements `elems` (local indices, CUDA int32) of the state U (a tensor of either
+    precision, or a context-owned stage input) gathered into a new buffer
+    [nvar][len(elems)][n^dim] (sd_pack_elements)."""
+    import torch
+    dt = _state_dtype(ctx, U)
+    buf = torch.empty(len(elems) * _elem_values(ctx), dtype=dt, device="cuda")
+    _check(load_library().sd_pack_elements(ctx._ctx, ctypes.c_void_p(U.data_ptr()), buf.element_size(),
+                                           _idx_ptr(elems, "elems"), len(elems), _ptr(buf)), "sd_pack_elements")
+    return buf
+
+
+def unpack_elements(ctx, buf, elems, U):
+    """The inverse of pack_elements: buf written into elements `elems` of U."""
+    dt = _state_dtype(ctx, U)
+    if buf.numel() != len(elems) * _elem_values(ctx) or buf.dtype != dt:
+        raise ValueError("buffer does not match the element list")
+    _check(load_library().sd_unpack_elements(ctx._ctx, _ptr(buf), buf.element_size(), _idx_ptr(elems, "elems"),
+                                             len(elems), ctypes.c_void_p(U.data_ptr())), "sd_unpack_elements")
+
+
+def pack_face_gradients(ctx, elems, faces):
+    """Face blocks (elems[k], faces[k]) of the context's interface-gradient buffer."""
+    import torch
+    g = int(load_library().sd_face_gradient_size(ctx._ctx))
+    buf = torch.empty(len(elems) * g, dtype=ctx.dtype, device="cuda")
+    _check(load_library().sd_pack_face_gradients(ctx._ctx, _idx_ptr(elems, "elems"), _idx_ptr(faces, "faces"),
+                                                 len(elems), _ptr(buf)), "sd_pack_face_gradients")
+    return buf
+
+
+def unpack_face_gradients(ctx, buf, elems, faces):
+    g = int(load_library().sd_face_gradient_size(ctx._ctx))
+    if buf.numel() != len(elems) * g or buf.dtype != ctx.dtype:
+        raise ValueError("buffer does not match the face list")
+    _check(load_library().sd_unpack_face_gradients(ctx._ctx, _ptr(buf), _idx_ptr(elems, "elems"),
+                                                   _idx_ptr(faces, "faces"), len(elems)),
+           "sd_unpack_face_gradients")
+
+
+def residual_begin(ctx, U):
+    """Traces and own interface gradients of U (the first half of sd_residual)."""
+    _check(load_library().sd_residual_begin(ctx._ctx, _dev_ptr(U, ctx.dtype, ctx.numel, "U")),
+           "sd_residual_begin")
+
+
+def residual_end(ctx, U, R):
+    """Interface fluxes and divergence (the second half of sd_residual)."""
+    _check(load_library().sd_residual_end(ctx._ctx, _dev_ptr(U, ctx.dtype, ctx.numel, "U"),
+                                          _dev_ptr(R, ctx.dtype, ctx.numel, "R")), "sd_residual_end")
+
+
+def rk_prepare(ctx, U64):
+    """First stage input of a Runge-Kutta step of U64 (sd_rk_prepare); returns it."""
+    import torch
+    out = ctypes.c_void_p()
+    _check(load_library().sd_rk_prepare(ctx._ctx, _dev_ptr(U64, torch.float64, ctx.numel, "U64"),
+                                        ctypes.byref(out)), "sd_rk_prepare")
+    return DevicePointer(out.value)
+
+
+def rk_stage(ctx, U64, k, dt, rk="ssprk54"):
+    """Stage k of the step (sd_rk_stage); returns the next stage input (None after the last)."""
+    import torch
+    out = ctypes.c_void_p()
+    _check(load_library().sd_rk_stage(ctx._ctx, _dev_ptr(U64, torch.float64, ctx.numel, "U64"), int(k),
+                                      float(dt), RK[rk], ctypes.byref(out)), "sd_rk_stage")
+    return DevicePointer(out.value) if out.value else None
 
 
 def filter_matrix(pf, pc, r):

@@ -116,10 +116,15 @@ def main():
     ap.add_argument("--coarse", type=int, default=16)
     ap.add_argument("--re", type=float, nargs="+", default=[1600.0, 3000.0, 5000.0])
     ap.add_argument("--test-re", type=float, nargs="*", default=None)
+    ap.add_argument("--holdout", type=float, default=None,
+                    help="also train a second network without this Re (from the same fine data) "
+                         "and evaluate it there")
     ap.add_argument("--t-end", type=float, default=10.0)
     ap.add_argument("--every", type=float, default=0.25)
     ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--out", default=None, help="also write the JSON result to this file")
     a = ap.parse_args()
+    import torch
     t0 = time.time()
     X, T, curves = training_data(a.fine, a.coarse, a.re, a.t_end, a.every)
     t1 = time.time()
@@ -131,9 +136,24 @@ def main():
             _, _, c = training_data(a.fine, a.coarse, [Re], a.t_end, a.every)
             curves[Re] = c[Re]
         res[str(Re)] = evaluate(net, stats, a.coarse, Re, a.t_end, a.every, curves[Re])
-    print(json.dumps({"fine": a.fine, "coarse": a.coarse, "train_re": a.re, "samples": int(X.shape[0]),
-                      "losses": losses, "dissipation_rel_l2_error": res,
-                      "seconds": {"data": t1 - t0, "train": t2 - t1, "eval": time.time() - t2}}))
+    out = {"fine": "%d^3 p4" % a.fine, "coarse": "%d^3 p3" % a.coarse, "train_re": a.re,
+           "samples": int(X.shape[0]), "losses": losses, "dissipation_rel_l2_error": res}
+    if a.holdout is not None:
+        # the samples of each Re are contiguous in X, T (training_data appends them in order)
+        per = X.shape[0] // len(a.re)
+        keep = torch.cat([torch.arange(i * per, (i + 1) * per, device=X.device)
+                          for i, Re in enumerate(a.re) if Re != a.holdout])
+        net_h, stats_h, losses_h = train(X[keep], T[keep], steps=a.steps, log_every=500)
+        out["holdout"] = {"train_re": [Re for Re in a.re if Re != a.holdout], "test_re": a.holdout,
+                          "losses": losses_h,
+                          "dissipation_rel_l2_error": evaluate(net_h, stats_h, a.coarse, a.holdout, a.t_end,
+                                                               a.every, curves[a.holdout])}
+    out["seconds"] = {"data": t1 - t0, "train": t2 - t1, "eval": time.time() - t2}
+    line = json.dumps(out)
+    print(line)
+    if a.out:
+        with open(a.out, "w") as f:
+            f.write(line + "\n")
 
 
 if __name__ == "__main__":

@@ -266,7 +266,7 @@ static void free_all(sd_ctx* c) {
         if (c->ev_out[k]) cudaEventDestroy(c->ev_out[k]);
     }
     if (c->cl_tmode) cudaFree(c->cl_tmode);
-    void* ptrs[] = {c->Tu, c->Tg, c->Fh, c->S, c->K, c->rA, c->rB, c->rC, c->rX, c->rA64, c->rB64, c->rC64, c->dW,
+    void* ptrs[] = {c->Tu, c->Tu2, c->Tg, c->Fh, c->S, c->K, c->rA, c->rB, c->rC, c->rX, c->rA64, c->rB64, c->rC64, c->dW,
                     c->partial, c->partial2, c->dsum, c->hU, c->hR, c->cih, c->cvs, c->cTg, c->cgeo64};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -399,6 +399,7 @@ extern "C" sd_status sd_init(const sd_mesh* mesh, int p, sd_scheme scheme, const
     alloc(&c->Tu, c->ntu * c->esize);
     alloc(&c->Tg, c->ntg * c->esize);
     alloc(&c->Fh, c->nfh * c->esize);
+    if (prec == SD_F32) alloc(&c->Tu2, c->ntu * c->esize);
     if (prec == SD_F64) c->Tu64 = (double*)c->Tu;
     else alloc((void**)&c->Tu64, c->ntu * sizeof(double));
     alloc(&c->S, S * c->esize);
@@ -664,38 +665,28 @@ __global__ void k_ssp_inc(int k, double* __restrict__ U, float* __restrict__ A, 
 #pragma unroll
         for (int w = 0; w < EWB; ++w) {
             const size_t i = base + w * stride;
+            a[w] = b[w] = cc[w] = x[w] = 0.0f;
+            u[w] = 0.0;
             if (i >= n) continue;
             kk[w] = K[i];
             if (k < 4) x[w] = X[i];
-            if (k == 1 || k == 3) b[w] = B[i];
+            if (k == 1 || k == 2 || k == 3) b[w] = B[i];
             if (k == 1 || k >= 3) a[w] = A[i];
             if (k == 4) { cc[w] = C[i]; u[w] = U[i]; }
-            if (k == 2) b[w] = B[i];
         }
 #pragma unroll
         for (int w = 0; w < EWB; ++w) {
             const size_t i = base + w * stride;
             if (i >= n) continue;
-            if (k == 0) {
-                const float d = c.b10 * kk[w];
-                A[i] = d;
-                S[i] = x[w] + d;
-            } else if (k == 1) {
-                const float d = fmaf(c.a21, a[w], c.b21 * kk[w]);
-                B[i] = d;
-                S[i] = x[w] + d;
-            } else if (k == 2) {
-                const float d = fmaf(c.a32, b[w], c.b32 * kk[w]);
-                A[i] = d;
-                S[i] = x[w] + d;
-            } else if (k == 3) {
-                C[i] = fmaf(c.a52, b[w], fmaf(c.a53, a[w], c.b53 * kk[w]));
-                const float d = fmaf(c.a43, a[w], c.b43 * kk[w]);
-                A[i] = d;
-                S[i] = x[w] + d;
-            } else {
-                U[i] = u[w] + (double)fmaf(c.a54, a[w], fmaf(c.b54, kk[w], cc[w]));
+            const float s = ssp_inc_point(c, k, kk[w], x[w], a[w], b[w], cc[w], u[w]);
+            if (k == 4) {
+                U[i] = u[w];
+                continue;
             }
+            S[i] = s;
+            if (k == 1) B[i] = b[w];
+            else A[i] = a[w];
+            if (k == 3) C[i] = cc[w];
         }
     }
 }
@@ -784,99 +775,127 @@ static const double kLSB[5] = {1432997174477.0 / 9575080441755.0, 5161836677717.
                                1720146321549.0 / 2090206949498.0, 3134564353537.0 / 4481467310338.0,
                                2277821191437.0 / 14882151754819.0};
 
-// FP64 contexts: full FP64 stage states (the parity build)
-static sd_status rk_step_f64(sd_ctx* c, double* U, double dt, sd_rk rk) {
+// Runge-Kutta steps, stage by stage. Three forms of the stage arithmetic:
+//   FP64 contexts: full FP64 stage states (the parity build);
+//   FP32 contexts, SD_RK_STAGES_F32: FP32 stage increments d_j, the state U updated in FP64
+//     once per step; the stage input is X + d_j with X = U - offsets rounded once per step;
+//   FP32 contexts, SD_RK_STAGES_F64: FP64 stage states and registers, FP32 residual of each
+//     stage state (offsets removed in FP64, then rounded).
+// rk_prepare writes the first stage input from U; rk_stage(k) evaluates the residual of
+// stage k's input and applies the stage-k update, which writes the next stage input (or, at
+// the last stage, U). stage_input(k) is the array the residual of stage k reads.
+static bool inc_mode(const sd_ctx* c) { return c->prec == SD_F32 && c->rk_stages == SD_RK_STAGES_F32; }
+
+static void* stage_input(sd_ctx* c, int k) { return inc_mode(c) && k == 0 ? c->rX : c->S; }
+
+static int rk_stages_of(sd_rk rk) { return rk == SD_RK4 ? 4 : 5; }
+
+static sd_status rk_prepare(sd_ctx* c, double* U) {
     const size_t n = c->nstate;
-    double* S = (double*)c->S;
-    double* K = (double*)c->K;
-    double *rA = (double*)c->rA, *rB = (double*)c->rB, *rC = (double*)c->rC;
-    const int gb = grid_for(n);
-    cudaStream_t st = c->stream;
     sdk::StageOff so;
     so.npts = c->npts;
     sdk::stage_offsets(c, so.off0, so.off4);
-    auto res = [&](const void* in) -> sd_status { return residual_any(c, in, K, 1); };
     sdi_prof_begin(c, SD_K_OTHER);
-    sdk::k_to_real<double><<<gb, 256, 0, st>>>(U, S, n, so);
+    if (c->prec == SD_F64) sdk::k_to_real<double><<<grid_for(n), 256, 0, c->stream>>>(U, (double*)c->S, n, so);
+    else sdk::k_to_real<float><<<grid_for(n), 256, 0, c->stream>>>(U, (float*)stage_input(c, 0), n, so);
     sdi_prof_end(c, SD_K_OTHER);
-    sd_status s;
-    const int nst = rk == SD_RK4 ? 4 : 5;
-    for (int k = 0; k < nst; ++k) {
-        if ((s = res(S)) != SD_OK) return s;
-        sdi_prof_begin(c, SD_K_OTHER);
+    CK(cudaGetLastError());
+    return SD_OK;
+}
+
+static sd_status rk_stage(sd_ctx* c, double* U, int k, double dt, sd_rk rk) {
+    const size_t n = c->nstate;
+    cudaStream_t st = c->stream;
+    sd_status s = residual_any(c, stage_input(c, k), c->K, 1);
+    if (s != SD_OK) return s;
+    sdk::StageOff so;
+    so.npts = c->npts;
+    sdk::stage_offsets(c, so.off0, so.off4);
+    const int gb = grid_for(n);
+    sdi_prof_begin(c, SD_K_OTHER);
+    if (c->prec == SD_F64) {
+        double* S = (double*)c->S;
+        double* K = (double*)c->K;
+        double *rA = (double*)c->rA, *rB = (double*)c->rB, *rC = (double*)c->rC;
         if (rk == SD_RK4) sdk::k_rk4<double><<<gb, 256, 0, st>>>(k, U, rA, K, S, dt, n, so);
         else if (rk == SD_SSPRK54) sdk::k_ssp<double><<<gb, 256, 0, st>>>(k, U, rA, rB, rC, K, S, dt, kSSP, n, so);
         else sdk::k_lsrk<double><<<gb, 256, 0, st>>>(U, rA, K, S, kLSA[k], kLSB[k], dt, n, so);
-        sdi_prof_end(c, SD_K_OTHER);
-    }
-    CK(cudaGetLastError());
-    return SD_OK;
-}
-
-// FP32 contexts with FP64 stage states (sd_set_rk_stages(ctx, SD_RK_STAGES_F64)): the
-// registers and every stage combination in FP64, as in FP64 contexts; each stage's FP32
-// residual is evaluated on the stage state rounded to FP32 (offsets removed in FP64 first)
-static sd_status rk_step_f32_f64stages(sd_ctx* c, double* U, double dt, sd_rk rk) {
-    const size_t n = c->nstate;
-    float* S = (float*)c->S;
-    float* K = (float*)c->K;
-    double *rA = c->rA64, *rB = c->rB64, *rC = c->rC64;
-    const int gb = grid_for(n);
-    cudaStream_t st = c->stream;
-    sdk::StageOff so;
-    so.npts = c->npts;
-    sdk::stage_offsets(c, so.off0, so.off4);
-    sdi_prof_begin(c, SD_K_OTHER);
-    sdk::k_to_real<float><<<gb, 256, 0, st>>>(U, S, n, so);
-    sdi_prof_end(c, SD_K_OTHER);
-    sd_status s;
-    const int nst = rk == SD_RK4 ? 4 : 5;
-    for (int k = 0; k < nst; ++k) {
-        if ((s = residual_any(c, S, K, 1)) != SD_OK) return s;
-        sdi_prof_begin(c, SD_K_OTHER);
+    } else if (!inc_mode(c)) {
+        float* S = (float*)c->S;
+        float* K = (float*)c->K;
+        double *rA = c->rA64, *rB = c->rB64, *rC = c->rC64;
         if (rk == SD_RK4) sdk::k_rk4<float><<<gb, 256, 0, st>>>(k, U, rA, K, S, dt, n, so);
         else if (rk == SD_SSPRK54) sdk::k_ssp<float><<<gb, 256, 0, st>>>(k, U, rA, rB, rC, K, S, dt, kSSP, n, so);
         else sdk::k_lsrk<float><<<gb, 256, 0, st>>>(U, rA, K, S, kLSA[k], kLSB[k], dt, n, so);
-        sdi_prof_end(c, SD_K_OTHER);
+    } else {
+        float* S = (float*)c->S;
+        float* K = (float*)c->K;
+        float* X = (float*)c->rX;
+        float *rA = (float*)c->rA, *rB = (float*)c->rB, *rC = (float*)c->rC;
+        const int gi = grid_for((n + sdk::EWB - 1) / sdk::EWB);
+        const sdk::SSPCoef& a = kSSP;
+        const sdk::SSPInc ci = {(float)(a.a10 * dt), (float)a.a21, (float)(a.b21 * dt), (float)a.a32,
+                                (float)(a.b32 * dt), (float)a.a43, (float)(a.b43 * dt), (float)a.a52,
+                                (float)a.a53, (float)(a.b53 * dt), (float)a.a54, (float)(a.b54 * dt)};
+        const sdk::RK4Inc c4 = {(float)(0.5 * dt), (float)dt, (float)(dt / 6.0), (float)(dt / 3.0)};
+        if (rk == SD_RK4)
+            sdk::k_rk4_inc<<<gi, 256, 0, st>>>(k, U, rA, K, X, S, c4, n);
+        else if (rk == SD_SSPRK54)
+            sdk::k_ssp_inc<<<gi, 256, 0, st>>>(k, U, rA, rB, rC, K, X, S, ci, n);
+        else
+            sdk::k_lsrk_inc<<<gi, 256, 0, st>>>(k, k == 4, U, rA, rB, K, X, S, (float)kLSA[k], (float)dt,
+                                                (float)kLSB[k], n);
     }
+    sdi_prof_end(c, SD_K_OTHER);
     CK(cudaGetLastError());
     return SD_OK;
 }
 
-// FP32 contexts: FP32 stage increments, FP64 accumulation of the state once per step
-static sd_status rk_step_f32(sd_ctx* c, double* U, double dt, sd_rk rk) {
-    const size_t n = c->nstate;
-    float* S = (float*)c->S;
-    float* K = (float*)c->K;
+static sd_status rk_check(sd_ctx* c, double* U64, double dt, sd_rk rk) {
+    if (!c || !U64) { sdi_set_error("null argument"); return SD_EINVAL; }
+    if (!(dt > 0.0) || !isfinite(dt)) { sdi_set_error("dt must be positive and finite"); return SD_EINVAL; }
+    if (rk != SD_RK4 && rk != SD_SSPRK54 && rk != SD_LSRK54) {
+        sdi_set_error("bad Runge-Kutta scheme");
+        return SD_EINVAL;
+    }
+    return SD_OK;
+}
+
+#ifndef SDI_FUSED_STAGES
+#define SDI_FUSED_STAGES 0
+#endif
+
+// SSPRK(5,4) step of an FP32 context in increment form with every stage update applied by
+// the flux kernel's epilogue (sdk::StageOut): no separate stage kernels, no stage residual
+// array, and the traces of each next stage input written by the same epilogue into the
+// second trace buffer (the two buffers swap roles every stage). The arithmetic is that of
+// rk_prepare + rk_stage, so the result is the same to the bit.
+static bool fusable(const sd_ctx* c, sd_rk rk) {
+    return SDI_FUSED_STAGES && rk == SD_SSPRK54 && inc_mode(c) && !c->curv && c->Tu2 &&
+           (c->nvar == 5 || !(c->phys.kind == SD_PME && c->phys.pme_coef == SD_PME_COEF_SOLUTION));
+}
+
+static sd_status rk_step_fused(sd_ctx* c, double* U, double dt) {
+    sd_status s = rk_prepare(c, U);
+    if (s != SD_OK) return s;
     float* X = (float*)c->rX;
-    float *rA = (float*)c->rA, *rB = (float*)c->rB, *rC = (float*)c->rC;
-    const int gb = grid_for((n + sdk::EWB - 1) / sdk::EWB);
-    cudaStream_t st = c->stream;
-    sdk::StageOff so;
-    so.npts = c->npts;
-    sdk::stage_offsets(c, so.off0, so.off4);
-    auto res = [&](const void* in) -> sd_status { return residual_any(c, in, K, 1); };
-    sdi_prof_begin(c, SD_K_OTHER);
-    sdk::k_to_real<float><<<grid_for(n), 256, 0, st>>>(U, X, n, so);
-    sdi_prof_end(c, SD_K_OTHER);
-    sd_status s;
-    const int nst = rk == SD_RK4 ? 4 : 5;
+    if ((s = sdi_stage_traces_f32(c, X)) != SD_OK) return s;
     const sdk::SSPCoef& a = kSSP;
-    const sdk::SSPInc ci = {(float)(a.a10 * dt), (float)a.a21, (float)(a.b21 * dt), (float)a.a32,
-                            (float)(a.b32 * dt), (float)a.a43, (float)(a.b43 * dt), (float)a.a52,
-                            (float)a.a53, (float)(a.b53 * dt), (float)a.a54, (float)(a.b54 * dt)};
-    const sdk::RK4Inc c4 = {(float)(0.5 * dt), (float)dt, (float)(dt / 6.0), (float)(dt / 3.0)};
-    for (int k = 0; k < nst; ++k) {
-        if ((s = res(k == 0 ? (const void*)X : (const void*)S)) != SD_OK) return s;
-        sdi_prof_begin(c, SD_K_OTHER);
-        if (rk == SD_RK4)
-            sdk::k_rk4_inc<<<gb, 256, 0, st>>>(k, U, rA, K, X, S, c4, n);
-        else if (rk == SD_SSPRK54)
-            sdk::k_ssp_inc<<<gb, 256, 0, st>>>(k, U, rA, rB, rC, K, X, S, ci, n);
-        else
-            sdk::k_lsrk_inc<<<gb, 256, 0, st>>>(k, k == 4, U, rA, rB, K, X, S, (float)kLSA[k], (float)dt,
-                                                (float)kLSB[k], n);
-        sdi_prof_end(c, SD_K_OTHER);
+    sdk::StageOut so;
+    so.U = U;
+    so.A = (float*)c->rA;
+    so.B = (float*)c->rB;
+    so.C = (float*)c->rC;
+    so.X = X;
+    so.S = (float*)c->S;
+    so.c = {(float)(a.a10 * dt), (float)a.a21, (float)(a.b21 * dt), (float)a.a32, (float)(a.b32 * dt),
+            (float)a.a43, (float)(a.b43 * dt), (float)a.a52, (float)a.a53, (float)(a.b53 * dt), (float)a.a54,
+            (float)(a.b54 * dt)};
+    for (int k = 0; k < 5; ++k) {
+        so.k = k;
+        so.Tnext = (float*)c->Tu2;
+        if ((s = sdi_fused_stage_f32(c, k == 0 ? X : (const float*)c->S, &so)) != SD_OK) return s;
+        if (k < 4) std::swap(c->Tu, c->Tu2);
     }
     CK(cudaGetLastError());
     return SD_OK;
@@ -884,17 +903,30 @@ static sd_status rk_step_f32(sd_ctx* c, double* U, double dt, sd_rk rk) {
 
 extern "C" sd_status sd_rk_step(sd_ctx* c, double* U64, double t, double dt, sd_rk rk) {
     (void)t;
-    if (!c || !U64) { sdi_set_error("null argument"); return SD_EINVAL; }
-    if (!(dt > 0.0) || !isfinite(dt)) { sdi_set_error("dt must be positive and finite"); return SD_EINVAL; }
-    if (rk != SD_RK4 && rk != SD_SSPRK54 && rk != SD_LSRK54) {
-        sdi_set_error("bad Runge-Kutta scheme");
-        return SD_EINVAL;
-    }
-    if (c->prec == SD_F32) {
-        if (c->rk_stages == SD_RK_STAGES_F64) return rk_step_f32_f64stages(c, U64, dt, rk);
-        return rk_step_f32(c, U64, dt, rk);
-    }
-    return rk_step_f64(c, U64, dt, rk);
+    sd_status s = rk_check(c, U64, dt, rk);
+    if (s != SD_OK) return s;
+    if (fusable(c, rk)) return rk_step_fused(c, U64, dt);
+    if ((s = rk_prepare(c, U64)) != SD_OK) return s;
+    for (int k = 0; k < rk_stages_of(rk); ++k)
+        if ((s = rk_stage(c, U64, k, dt, rk)) != SD_OK) return s;
+    return SD_OK;
+}
+
+extern "C" sd_status sd_rk_prepare(sd_ctx* c, double* U64, void** input) {
+    if (!c || !U64 || !input) { sdi_set_error("null argument"); return SD_EINVAL; }
+    const sd_status s = rk_prepare(c, U64);
+    if (s == SD_OK) *input = stage_input(c, 0);
+    return s;
+}
+
+extern "C" sd_status sd_rk_stage(sd_ctx* c, double* U64, int k, double dt, sd_rk rk, void** input) {
+    sd_status s = rk_check(c, U64, dt, rk);
+    if (s != SD_OK) return s;
+    if (!input) { sdi_set_error("null argument"); return SD_EINVAL; }
+    if (k < 0 || k >= rk_stages_of(rk)) { sdi_set_error("stage %d out of range", k); return SD_EINVAL; }
+    if ((s = rk_stage(c, U64, k, dt, rk)) != SD_OK) return s;
+    *input = k + 1 < rk_stages_of(rk) ? stage_input(c, k + 1) : nullptr;
+    return SD_OK;
 }
 
 extern "C" sd_status sd_set_rk_stages(sd_ctx* c, sd_rk_stages mode) {
@@ -1043,7 +1075,8 @@ extern "C" sd_status sd_diagnostics(sd_ctx* c, const double* U64, double t, sd_d
     out->energy = h[7];
     out->l2sq = h[8];
     double vol = 1.0;
-    for (int d = 0; d < c->dim; ++d) vol *= c->hi[d] - c->lo[d];
+    for (int d = 0; d < c->dim; ++d)
+        vol *= c->own_set ? (c->own_hi[d] - c->own_lo[d]) * c->h[d] : c->hi[d] - c->lo[d];
     out->volume = c->curv ? c->curv_volume : vol;
     out->nonfinite = h[9] != 0.0 ? 1 : 0;
     if (out->nonfinite) {

@@ -840,6 +840,10 @@ inline Mesh cmesh(const sd_ctx* c) {
     g.nelem = c->nelem;
     g.e_begin = 0;
     g.e_end = c->nelem;
+    for (int d = 0; d < 3; ++d) {
+        g.olo[d] = 0;
+        g.ohi[d] = c->ne[d];
+    }
     return g;
 }
 

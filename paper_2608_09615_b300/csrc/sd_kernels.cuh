@@ -53,7 +53,17 @@ struct Mesh {
     int ne[3];
     int nelem;
     int e_begin, e_end;      // elements [e_begin, e_end) processed by a residual launch
+    int olo[3], ohi[3];      // owned box of a sub-domain (the diagnostics sum over it only)
 };
+
+// element e lies in the owned box [olo, ohi) of the grid
+__device__ __forceinline__ bool owned(const Mesh& g, int e) {
+    const int c0 = e % g.ne[0];
+    const int r = e / g.ne[0];
+    const int c1 = r % g.ne[1];
+    const int c2 = r / g.ne[1];
+    return c0 >= g.olo[0] && c0 < g.ohi[0] && c1 >= g.olo[1] && c1 < g.ohi[1] && c2 >= g.olo[2] && c2 < g.ohi[2];
+}
 
 // ------------------------------------------------------------------ index helpers
 template <int N>
@@ -172,6 +182,39 @@ __device__ __forceinline__ void ns_viscous(const real* U, const real* g, int d,
     Fv[2] = tau[1];
     Fv[3] = tau[2];
     Fv[4] = vel[0] * tau[0] + vel[1] * tau[1] + vel[2] * tau[2] + mu * P.gamma_Pr * de;
+}
+
+// F_c - F_v along d at an interior flux point (Sec. 4.4), offset state U and the 9 exchanged
+// gradient components g (comp_map order): ns_convective minus ns_viscous with the
+// reciprocal of rho, the velocity and the pressure shared by both parts
+template <typename real>
+__device__ __forceinline__ void ns_flux_point(const real* U, const real* g, int d, const Phys<real>& P,
+                                              real* F) {
+    const real ir = real(1) / (U[0] + P.rho0);
+    const real vel[3] = {U[1] * ir, U[2] * ir, U[3] * ir};
+    const real ke2 = U[1] * vel[0] + U[2] * vel[1] + U[3] * vel[2];     // rho |u|^2
+    const real pp = P.gm1 * (U[4] - real(0.5) * ke2);                   // p - p0
+    const real ud = vel[d];
+    const real E = (U[4] + P.rhoE0) * ir;
+    const real e = E - real(0.5) * (vel[0] * vel[0] + vel[1] * vel[1] + vel[2] * vel[2]);
+    const real mu = sutherland_mu(P, e);
+    real dud[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) dud[i] = (g[1 + i] - vel[i] * g[0]) * ir;   // d u_i / d x_d
+    const int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
+    const real dt1 = (g[6] - ud * g[5]) * ir;                               // d u_d / d x_t1
+    const real dt2 = (g[8] - ud * g[7]) * ir;                               // d u_d / d x_t2
+    const real dE = (g[4] - E * g[0]) * ir;
+    const real de = dE - (vel[0] * dud[0] + vel[1] * dud[1] + vel[2] * dud[2]);
+    real tau[3];
+    tau[d] = real(2) * mu * dud[d];
+    tau[t1] = mu * (dud[t1] + dt1);
+    tau[t2] = mu * (dud[t2] + dt2);
+    F[0] = U[1 + d];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) F[1 + i] = U[1 + i] * ud - tau[i];
+    F[1 + d] += pp;
+    F[4] = ((U[4] + pp) + P.H0) * ud - (vel[0] * tau[0] + vel[1] * tau[1] + vel[2] * tau[2] + mu * P.gamma_Pr * de);
 }
 
 // Roe flux with Harten's fix on the acoustic eigenvalues (Sec. 4.4), or Rusanov; offset
@@ -388,7 +431,7 @@ __global__ void __launch_bounds__(Footprint<N, DIM, NV>::MAXT) k_diag(const doub
     double acc[NDIAG];
 #pragma unroll
     for (int k = 0; k < NDIAG; ++k) acc[k] = 0.0;
-    if (valid) {
+    if (valid && owned(g, e)) {
         for (int pt = tid; pt < NP; pt += TPE) {
             double w = J;
             int r = pt;
@@ -559,6 +602,51 @@ __global__ void k_lsrk(double* __restrict__ U, double* __restrict__ dU, const re
 // Coefficients arrive premultiplied by dt (FP64 products rounded once).
 struct SSPInc {
     float b10, a21, b21, a32, b32, a43, b43, a52, a53, b53, a54, b54;
+};
+
+// One point of stage k of that form: kk is the stage residual, x the step-start value minus
+// the offsets, a / b / cc the increment registers A, B, C at the point (updated in place).
+// Stages 0-3 return the next stage input x + d; stage 4 updates the FP64 state u. Every
+// operation is explicitly rounded, so that k_ssp_inc and the flux kernel's stage epilogue
+// (which applies this to the residual it has just formed) produce the same bits.
+__device__ __forceinline__ float ssp_inc_point(const SSPInc& c, int k, float kk, float x, float& a, float& b,
+                                               float& cc, double& u) {
+    if (k == 0) {
+        const float d = __fmul_rn(c.b10, kk);
+        a = d;
+        return __fadd_rn(x, d);
+    }
+    if (k == 1) {
+        const float d = __fmaf_rn(c.a21, a, __fmul_rn(c.b21, kk));
+        b = d;
+        return __fadd_rn(x, d);
+    }
+    if (k == 2) {
+        const float d = __fmaf_rn(c.a32, b, __fmul_rn(c.b32, kk));
+        a = d;
+        return __fadd_rn(x, d);
+    }
+    if (k == 3) {
+        cc = __fmaf_rn(c.a52, b, __fmaf_rn(c.a53, a, __fmul_rn(c.b53, kk)));
+        const float d = __fmaf_rn(c.a43, a, __fmul_rn(c.b43, kk));
+        a = d;
+        return __fadd_rn(x, d);
+    }
+    u = __dadd_rn(u, (double)__fmaf_rn(c.a54, a, __fmaf_rn(c.b54, kk, cc)));
+    return 0.0f;
+}
+
+// The stage update that the flux kernel applies in its epilogue instead of writing R (FP32
+// contexts, SSPRK(5,4) in increment form): registers, next stage input S and (stages 0-3)
+// the face traces of S for the next residual, in a second trace buffer.
+struct StageOut {
+    int k;                   // stage 0..4; -1: no stage, the kernel writes R
+    double* U;               // FP64 state (stage 4)
+    float *A, *B, *C;        // increment registers
+    const float* X;          // the step's start state minus the offsets
+    float* S;                // next stage input
+    float* Tnext;            // traces of S (stages 0-3)
+    SSPInc c;
 };
 
 __global__ void k_ssp_inc(int k, double* __restrict__ U, float* __restrict__ A, float* __restrict__ B,

@@ -45,6 +45,9 @@
 #ifndef SD_FLUX_MAXNREG
 #define SD_FLUX_MAXNREG 136
 #endif
+#ifndef SD_FLUX_UNROLL
+#define SD_FLUX_UNROLL 0
+#endif
 
 namespace sdk {
 
@@ -71,6 +74,18 @@ struct LineGeo {
     real corrR[3];           // (2/h_d) beta
     real off0, off4;         // offsets removed from variables 0 and 4 when staging
     real tip[3];             // interior penalty eta (p+1)^2 / h_d (0: off)
+};
+
+// Operator rows of the flux kernel with the grid's metric folded in, per direction d (a
+// kernel parameter, so that with the flux points unrolled every coefficient is a constant
+// operand): the divergence weights -(2/h_d) M and the normal-derivative rows (2/h_d) L D,
+// (2/h_d) (L M)[:,0], (2/h_d) (L M)[:,N] at the flux points.
+template <typename real, int N>
+struct FluxOps {
+    real Mn[3][N][N + 1];    // -(2/h_d) M[i][f]
+    real LDn[3][N + 1][N];   // (2/h_d) (L D)[f][i]
+    real LM0n[3][N + 1];     // (2/h_d) (L M)[f][0]
+    real LMNn[3][N + 1];     // (2/h_d) (L M)[f][N]
 };
 
 constexpr int round4(int x) { return (x + 3) / 4 * 4; }
@@ -810,13 +825,17 @@ k_face_flux(const real* __restrict__ Tu, const real* __restrict__ Tg, real* __re
 }
 
 // fluxes along D at the n+1 flux points of line q and their divergence on the line: the
-// interface fluxes at f = 0 and f = N come from Fh, the n-1 interior ones are evaluated here
+// interface fluxes at f = 0 and f = N come from Fh, the n-1 interior ones are evaluated here.
+// The flux-point loop is kept rolled (unrolling it for n = 5 measured 0.98 against 0.80 ms
+// per launch at 48^3 on B300: the larger body costs more than the constant operands save);
+// SD_FLUX_UNROLL=1 unrolls it for n <= 6.
 template <typename real, int N, int DIM, int NV, int D, class ST>
-__device__ __forceinline__ void line_flux(const LineGeo<real>& geo, const Phys<real>& P, const real (&u)[NV][N],
+__device__ __forceinline__ void line_flux(const FluxOps<real, N>& fo, const Phys<real>& P, const real (&u)[NV][N],
                                           const real (&dl)[NV], const real (&dr)[NV], const real* vS,
                                           const real* fh, int q, real (&r)[NV][N], const float* tau_own) {
     using LL = LineLayout<N, DIM, NV>;
     constexpr int NP = LL::NP, NQ = LL::NQ, NG = LL::NG;
+    constexpr int UNR = (SD_FLUX_UNROLL && N <= 6) ? N - 1 : 1;
     const OpTab<real, N>& op = c_op<real, N>;
     // interface flux points (f = 0 and f = N)
 #pragma unroll
@@ -824,13 +843,12 @@ __device__ __forceinline__ void line_flux(const LineGeo<real>& geo, const Phys<r
         const real F0 = fh[(2 * D) * ST::FS + v * NQ + q];
         const real FN = fh[(2 * D + 1) * ST::FS + v * NQ + q];
 #pragma unroll
-        for (int i = 0; i < N; ++i) r[v][i] = fma(op.M[i * (N + 1) + N], FN, op.M[i * (N + 1)] * F0);
+        for (int i = 0; i < N; ++i) r[v][i] = fma(fo.Mn[D][i][N], FN, fo.Mn[D][i][0] * F0);
     }
     // interior flux points: extrapolated solution and gradient (Eq. aux:v:std:2d); the
-    // normal derivatives come from u and the face corrections (dline), the transverse ones
-    // from the kept v^S
-    const real th = geo.two_h[D];
-#pragma unroll 1
+    // normal derivatives come from u and the face corrections, the transverse ones from the
+    // kept v^S
+#pragma unroll UNR
     for (int f = 1; f < N; ++f) {
         const real* Lr = op.L + f * N;
         real uf[NV], F[NV];
@@ -839,7 +857,11 @@ __device__ __forceinline__ void line_flux(const LineGeo<real>& geo, const Phys<r
         if constexpr (NV == 5) {
             real gf[NG];
 #pragma unroll
-            for (int c = 0; c < NV; ++c) gf[c] = dline<real, N>(op, f, u[c], dl[c], dr[c], th);
+            for (int c = 0; c < NV; ++c) {
+                real a = dotc<real, N>(fo.LDn[D][f], u[c]);
+                a = fma(fo.LM0n[D][f], dl[c], a);
+                gf[c] = fma(fo.LMNn[D][f], dr[c], a);
+            }
 #pragma unroll
             for (int c = NV; c < NG; ++c) {
                 int v, m;
@@ -849,17 +871,15 @@ __device__ __forceinline__ void line_flux(const LineGeo<real>& geo, const Phys<r
                 for (int i = 0; i < N; ++i) gl[i] = vS[vslot(v, m) * NP + lpt<N, D>(i, q)];
                 gf[c] = dotc<real, N>(Lr, gl);
             }
-            real Fv[NV];
-            ns_viscous(uf, gf, D, P, Fv);
-            ns_convective(uf, D, P, F);
+            ns_flux_point(uf, gf, D, P, F);
             if (tau_own) {
 #pragma unroll
                 for (int v = 0; v < NV; ++v) F[v] += (real)tau_own[3 * v + D];
             }
-#pragma unroll
-            for (int v = 0; v < NV; ++v) F[v] -= Fv[v];
         } else {
-            const real gfn = dline<real, N>(op, f, u[0], dl[0], dr[0], th);
+            real gfn = dotc<real, N>(fo.LDn[D][f], u[0]);
+            gfn = fma(fo.LM0n[D][f], dl[0], gfn);
+            gfn = fma(fo.LMNn[D][f], dr[0], gfn);
             if (P.kind == 1 && P.pme_sol) {
                 // diffusivity from the solution points, extrapolated to the flux point
                 real a[N];
@@ -873,12 +893,8 @@ __device__ __forceinline__ void line_flux(const LineGeo<real>& geo, const Phys<r
 #pragma unroll
         for (int v = 0; v < NV; ++v)
 #pragma unroll
-            for (int i = 0; i < N; ++i) r[v][i] = fma(op.M[i * (N + 1) + f], F[v], r[v][i]);
+            for (int i = 0; i < N; ++i) r[v][i] = fma(fo.Mn[D][i][f], F[v], r[v][i]);
     }
-#pragma unroll
-    for (int v = 0; v < NV; ++v)
-#pragma unroll
-        for (int i = 0; i < N; ++i) r[v][i] = -geo.two_h[D] * r[v][i];
 }
 
 template <int N, int DIM, int NV>
@@ -887,7 +903,8 @@ using FluxLayout = LineLayout<N, DIM, NV, SD_FLUX_THREADS>;
 template <typename real, int N, int DIM, int NV>
 __global__ void __maxnreg__((FluxLayout<N, DIM, NV>::FLUX_REGS))
 k_line_flux(const real* __restrict__ U, const real* __restrict__ Tu, const real* __restrict__ Fh,
-            real* __restrict__ R, LineGeo<real> geo, Mesh g, Phys<real> P, const float* __restrict__ tau) {
+            real* __restrict__ R, LineGeo<real> geo, Mesh g, Phys<real> P, const float* __restrict__ tau,
+            const __grid_constant__ FluxOps<real, N> fo, const __grid_constant__ StageOut so) {
     using LL = FluxLayout<N, DIM, NV>;
     using PL = FluxPipe<real, LL>;
     using ST = ResStrides<LL>;
@@ -921,10 +938,10 @@ k_line_flux(const real* __restrict__ U, const real* __restrict__ Tu, const real*
         real r[NV][N];
         if (live) {
             const float* t0 = (NV == 5 && tau) ? tau + (size_t)e * 15 : nullptr;
-            if (id.d == 0) line_flux<real, N, DIM, NV, 0, ST>(geo, P, u, dl, dr, vS, fh, id.q, r, t0);
+            if (id.d == 0) line_flux<real, N, DIM, NV, 0, ST>(fo, P, u, dl, dr, vS, fh, id.q, r, t0);
             if constexpr (DIM == 3) {
-                if (id.d == 1) line_flux<real, N, DIM, NV, 1, ST>(geo, P, u, dl, dr, vS, fh, id.q, r, t0);
-                if (id.d == 2) line_flux<real, N, DIM, NV, 2, ST>(geo, P, u, dl, dr, vS, fh, id.q, r, t0);
+                if (id.d == 1) line_flux<real, N, DIM, NV, 1, ST>(fo, P, u, dl, dr, vS, fh, id.q, r, t0);
+                if (id.d == 2) line_flux<real, N, DIM, NV, 2, ST>(fo, P, u, dl, dr, vS, fh, id.q, r, t0);
             }
         }
         // every line has read v^S: the work area now takes the three directions'
@@ -956,7 +973,49 @@ k_line_flux(const real* __restrict__ U, const real* __restrict__ Tu, const real*
                 acc = acc + rd[NV * NP];
                 acc = acc + rd[2 * NV * NP];
             }
-            R[(size_t)v * g.nelem * NP + (size_t)(e0 + eb) * NP + pt] = acc;
+            const size_t gi = (size_t)v * g.nelem * NP + (size_t)(e0 + eb) * NP + pt;
+            if constexpr (sizeof(real) == 4) {
+                if (so.k >= 0) {
+                    // stage epilogue: the residual feeds the stage update directly; the next
+                    // stage input goes to S and, for its traces, to this group's u staging
+                    float a = 0.0f, bb = 0.0f, cc = 0.0f;
+                    double uu = 0.0;
+                    const float x = so.k < 4 ? so.X[gi] : 0.0f;
+                    if (so.k >= 1 && so.k != 2) a = so.A[gi];
+                    if (so.k >= 1 && so.k <= 3) bb = so.B[gi];
+                    if (so.k == 4) { cc = so.C[gi]; uu = so.U[gi]; }
+                    const float s = ssp_inc_point(so.c, so.k, (float)acc, x, a, bb, cc, uu);
+                    if (so.k == 4) {
+                        so.U[gi] = uu;
+                    } else {
+                        so.S[gi] = s;
+                        if (so.k == 1) so.B[gi] = bb;
+                        else so.A[gi] = a;
+                        if (so.k == 3) so.C[gi] = cc;
+                        buf[v * EB * NP + eb * NP + pt] = (real)s;
+                    }
+                    continue;
+                }
+            }
+            R[gi] = acc;
+        }
+        if constexpr (sizeof(real) == 4) {
+            if (so.k >= 0 && so.k < 4) {
+                // face traces of the next stage input (the same line_traces as k_line_trace)
+                __syncthreads();
+                if (live) {
+                    const real* sn = buf + id.eb * NP;
+                    real* out = reinterpret_cast<real*>(so.Tnext) + (size_t)e * NF * LL::FST + id.q;
+                    constexpr int FST = LL::FST, NQ = LL::NQ;
+                    if (id.d == 0) line_traces<real, N, NQ, NV, 0, ST>(sn, id.q, out, out + FST, NQ);
+                    if constexpr (DIM == 3) {
+                        if (id.d == 1) line_traces<real, N, NQ, NV, 1, ST>(sn, id.q, out + 2 * FST, out + 3 * FST, NQ);
+                        if (id.d == 2) line_traces<real, N, NQ, NV, 2, ST>(sn, id.q, out + 4 * FST, out + 5 * FST, NQ);
+                    }
+                }
+                // the next group's copies may target this buffer
+                __syncthreads();
+            }
         }
     }
 }

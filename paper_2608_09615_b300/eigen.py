@@ -19,7 +19,19 @@ is sampled at N = ne (p + 1) equally spaced points and transformed with Eq. fft.
 zero-dissipation eigenvalue at folded angle theta* leaves the wavenumbers
 k = ne (theta* + 2 pi m) / (2 pi) (and their mirror images) undamped; these are the peaks.
 
+Combined-mode analysis (Appendix A). The exact Fourier mode exp(i k x) restricted to one
+element of size h = 1 is u0_j = exp(i theta (xi_j + 1) / 2), theta = k h, for the unfolded
+theta in [0, (p + 1) pi]. Expanded in the eigenvectors mu_j of B(theta) (u0 = N gamma) it
+evolves as u(t) = sum_j gamma_j mu_j exp(lambda_j t), lambda_j = -i omega_j; the amplification
+factor of the whole mode is G(theta, t) = u0* u(t) / u0* u0 and its combined frequency
+omega(theta, t) = (i / t) log G. (The appendix prints -(i / t) log G; with its own convention
+u ~ exp(-i omega t) the sign that returns omega_j when u0 is the eigenvector mu_j is +i / t,
+and that is the reading taken.) The dissipation is Im(omega) = log|G| / t (= -theta^2 for the
+exact solution of u_t = u_xx). The appendix leaves t open; t = 0.1 (units h = nu = 1) is
+the default reported.
+
     python -m paper_2608_09615_b300.eigen --p 1 2 3 4 --eta 0 0.01 0.02 1.0
+    python -m paper_2608_09615_b300.eigen --combined --p 1 2 3 4 --eta 0 0.01 0.02 0.05
 """
 import argparse
 import json
@@ -75,6 +87,38 @@ def zero_modes(p, scheme, eta_ip=0.0, tol=1e-9):
 def spectral_radius(p, scheme, eta_ip=0.0, nth=181):
     _, lam, _ = dissipation_curves(p, scheme, eta_ip, nth)
     return float(np.abs(lam).max())
+
+
+def combined_mode(B_of_theta, xi, thetas, t, initial=None):
+    """Appendix A: G(theta, t) and the combined frequency omega(theta, t) = (i / t) log G of
+    the exact Fourier mode, for the Bloch operator B_of_theta(theta) (n x n) of a scheme whose
+    solution points are xi (n values in [-1, 1]); thetas unfolded (up to (p + 1) pi).
+    initial(theta), if given, replaces the Fourier mode as the initial data."""
+    xi = np.asarray(xi, dtype=np.float64)
+    G = np.empty(len(thetas), dtype=np.complex128)
+    for k, th in enumerate(thetas):
+        u0 = np.exp(1j * th * (xi + 1.0) / 2.0) if initial is None else np.asarray(initial(th))
+        lam, N = np.linalg.eig(B_of_theta(th))
+        gamma = np.linalg.solve(N, u0)
+        ut = N @ (gamma * np.exp(lam * t))
+        G[k] = np.vdot(u0, ut) / np.vdot(u0, u0)
+    omega = 1j * np.log(G) / t
+    return G, omega
+
+
+def combined_curves(p, scheme, eta_ip=0.0, t=0.1, nth=181):
+    """Combined-mode curves of the GPU residual's Bloch operator: theta in [0, (p + 1) pi],
+    G(theta, t) and omega(theta, t)."""
+    K = bloch_kernels(p, scheme, eta_ip)
+    xi, _ = _gauss_points(p + 1)
+    th = np.linspace(0.0, (p + 1) * math.pi, nth)
+    G, om = combined_mode(lambda a: bloch_matrix(K, a), xi, th, t)
+    return th, G, om
+
+
+def _gauss_points(n):
+    x, w = np.polynomial.legendre.leggauss(n)
+    return x, w
 
 
 def _lagrange_matrix(nodes, x):
@@ -141,8 +185,19 @@ def main():
     ap.add_argument("--p", type=int, nargs="+", default=[1, 2, 3, 4])
     ap.add_argument("--eta", type=float, nargs="+", default=[0.0])
     ap.add_argument("--nth", type=int, default=91)
+    ap.add_argument("--combined", action="store_true", help="Appendix A combined-mode curves")
+    ap.add_argument("--t", type=float, default=0.1, help="time of the combined-mode amplification factor")
     a = ap.parse_args()
     out = []
+    if a.combined:
+        for p in a.p:
+            for eta in a.eta:
+                for scheme in ("compact", "br1"):
+                    th, G, om = combined_curves(p, scheme, eta, a.t, a.nth)
+                    out.append({"p": p, "eta_ip": eta, "scheme": scheme, "t": a.t, "theta": th.tolist(),
+                                "dissipation": om.imag.tolist(), "dispersion": om.real.tolist()})
+        print(json.dumps(out))
+        return
     for p in a.p:
         for eta in a.eta:
             for scheme in ("compact", "br1"):

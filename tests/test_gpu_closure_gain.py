@@ -11,8 +11,9 @@ A small version of the closure experiment runs end to end on the GPU:
 The error is the relative L2 distance, over time, between the coarse run's kinetic-energy
 dissipation rate and that of the filtered fine run at the same Re. The test asserts that
 training converges, that the closure run stays finite, and that the closure lowers the
-error at the held-out Re. The measured errors are printed (on B300: Re 3000 0.354 -> 0.342,
-Re 1600 0.325 -> 0.315)."""
+error at the held-out Re by at least 1.5% (measured on B300: Re 3000 0.354 -> 0.342, a 3.4%
+gain; Re 1600 0.325 -> 0.315). The full-size experiment (64^3 p4 -> 16^3 p3) is
+`python -m paper_2608_09615_b300.closure --holdout 3000`."""
 import math
 
 import pytest
@@ -49,4 +50,4 @@ def test_closure_lowers_dissipation_error_at_held_out_re(trained):
         print("Re %g: dissipation-rate error plain %.4f, closure %.4f (gain %.2f%%)"
               % (re, r["plain"], r["closure"], 100.0 * (1.0 - r["closure"] / r["plain"])))
         assert math.isfinite(r["plain"]) and math.isfinite(r["closure"])
-    assert res[3000.0]["closure"] < res[3000.0]["plain"]
+    assert res[3000.0]["closure"] < (1.0 - 0.015) * res[3000.0]["plain"]

@@ -126,7 +126,15 @@ def test_ns_fp64_parity_tgv_wavy():
 
 
 # ------------------------------------------------------------------ FP32
-def test_fp32_error_tgv_wavy_report(capsys):
+# Relative L2 error per variable of the FP32 residual, held to twice the level measured on
+# B300 (compact and BR1 alike: 5.1e-5 2.8e-5 2.8e-5 2.6e-6 6.5e-5). As on Cartesian grids
+# these sit at the FP32 rounding floor of the divergence (tests/fp32_floor.py): the wavy
+# grid's metric terms are a 15% perturbation of the uniform grid's, and the levels match the
+# uniform grid's to within 25%.
+FP32_WAVY_LEVEL_8 = np.array([5.1e-5, 2.8e-5, 2.8e-5, 2.6e-6, 6.5e-5])
+
+
+def test_fp32_error_tgv_wavy(capsys):
     ne, p = (8, 8, 8), 4
     prm, phys = ns_phys()
     N = lattice("wavy", ne)
@@ -142,7 +150,7 @@ def test_fp32_error_tgv_wavy_report(capsys):
             print("\nFP32 TGV 8^3 p4 wavy %s: max-rel %s  l2-rel %s" % (
                 scheme, " ".join("%.2e" % x for x in e_max), " ".join("%.2e" % x for x in e_l2)))
         assert np.all(np.isfinite(Rg))
-        assert e_l2.max() < 1e-2
+        assert np.all(e_l2 <= 2.0 * FP32_WAVY_LEVEL_8), e_l2
 
 
 @pytest.mark.parametrize("precision,tol", [("f64", 1e-11), ("f32", 2e-3)])

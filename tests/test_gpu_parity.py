@@ -129,24 +129,40 @@ def test_ns_fp64_parity_tgv(scheme):
     assert rel_err(Rg, Ro).max() <= 1e-12
 
 
-# ------------------------------------------------------------------ FP32 error report
-def test_fp32_error_tgv_report(capsys):
+# ------------------------------------------------------------------ FP32 error
+# The FP32 residual against the oracle on the same FP32-rounded input, relative L2 error per
+# variable (||R32_v - R_v||_2 / ||R_v||_2). Its floor is u kappa_v (tests/fp32_floor.py): the
+# sum of the magnitudes of the divergence terms over the residual, times FP32's unit
+# roundoff. On these Taylor-Green fields u kappa is already 8e-5 for rho and rho E at 8^3 and
+# grows like 1/h, so the benchmark's 1e-5 per residual is out of reach for any evaluation
+# that rounds the flux-point values to FP32; the tests hold the kernels to a small multiple
+# of that floor and to the measured levels (recorded on B300 at 8^3, compact and BR1: l2
+# 4.1e-5 2.8e-5 2.8e-5 2.0e-6 5.8e-5; ratio to u kappa 0.53 3.9 4.0 0.91 0.72).
+FP32_LEVEL_8 = np.array([4.1e-5, 2.8e-5, 2.8e-5, 2.0e-6, 5.8e-5])
+FLOOR_FACTOR = 8.0
+
+
+@pytest.mark.parametrize("scheme", ["compact", "br1"])
+def test_fp32_error_tgv_within_rounding_floor(scheme, capsys):
+    from fp32_floor import U32 as UNIT_ROUNDOFF, conditioning, kappa
     prm, phys = ns_phys()
     ne, p = (8, 8, 8), 4
     lo, hi = (0.0,) * 3, (TWO_PI,) * 3
     g = Grid(3, ne, lo, hi, p)
     U = inputs.tgv_3d(ne, p, perturb_seed=0)
     U32 = U.astype(np.float32).astype(np.float64)       # both sides see the FP32 input
-    for scheme in ("compact", "br1"):
-        Ro = oracle_residual(U32, g, scheme, NavierStokes(prm))
-        Rg = gpu_residual(U32, 3, ne, lo, hi, p, scheme, phys, "f32")
-        e_max = rel_err(Rg, Ro)
-        e_l2 = np.array([np.linalg.norm(Rg[v] - Ro[v]) / np.linalg.norm(Ro[v]) for v in range(5)])
-        with capsys.disabled():
-            print("\nFP32 TGV 8^3 p4 %s: max-rel %s  l2-rel %s" % (
-                scheme, " ".join("%.2e" % x for x in e_max), " ".join("%.2e" % x for x in e_l2)))
-        assert np.all(np.isfinite(Rg))
-        assert e_l2.max() < 1e-2
+    Ro, C = conditioning(U32, g, scheme, prm)
+    Rg = gpu_residual(U32, 3, ne, lo, hi, p, scheme, phys, "f32")
+    e_max = rel_err(Rg, Ro)
+    e_l2 = np.array([np.linalg.norm(Rg[v] - Ro[v]) / np.linalg.norm(Ro[v]) for v in range(5)])
+    floor = UNIT_ROUNDOFF * kappa(Ro, C)
+    with capsys.disabled():
+        print("\nFP32 TGV 8^3 p4 %s: max-rel %s  l2-rel %s  u*kappa %s" % (
+            scheme, " ".join("%.2e" % x for x in e_max), " ".join("%.2e" % x for x in e_l2),
+            " ".join("%.2e" % x for x in floor)))
+    assert np.all(np.isfinite(Rg))
+    assert np.all(e_l2 <= FLOOR_FACTOR * floor), (e_l2, floor)
+    assert np.all(e_l2 <= 2.0 * FP32_LEVEL_8), e_l2
 
 
 # ------------------------------------------------------------------ host path, RK, diagnostics
@@ -204,6 +220,45 @@ def test_rk_step_fp32_residual_close_to_fp64():
         ctx.close()
     dU = out["f64"] - U
     assert rel_err(out["f32"] - U, dU).max() < 1e-3
+
+
+@pytest.mark.parametrize("case", ["ns_compact", "ns_br1", "heat3d", "ns_closure_tau"])
+def test_fused_ssprk_step_equals_stage_by_stage(case):
+    # FP32 contexts apply each SSPRK(5,4) stage update in the flux kernel's epilogue (and write
+    # the next stage's traces there); the stage-by-stage calls run the separate stage kernels.
+    # Same arithmetic: the states agree to the bit, over several steps (odd and even grids,
+    # whose element groups end mid-block).
+    import ctypes
+    if case == "heat3d":
+        ne, p, scheme = (5, 3, 4), 3, "compact"
+        phys = sd.Physics(kind="heat", nu=0.05)
+        U = inputs.heat_modes_3d(ne, p, seed=2)[0]
+    else:
+        ne, p = (5, 4, 3), 4
+        scheme = "br1" if case == "ns_br1" else "compact"
+        phys = sd.Physics(kind="ns", Re=500.0)
+        U = inputs.tgv_3d(ne, p, perturb_seed=6)
+    dt = 2e-3
+    out = []
+    for fused in (True, False):
+        ctx = sd.SD(3, ne, (0.0,) * 3, (TWO_PI,) * 3, p, scheme, phys, "f32")
+        if case == "ns_closure_tau":
+            tau = torch.linspace(-1e-3, 1e-3, int(np.prod(ne)) * 15, device="cuda").view(-1, 15).contiguous()
+            ctx.set_flux_tau(tau)
+        Ug = torch.from_numpy(U.copy()).cuda()
+        for k in range(3):
+            if fused:
+                ctx.rk_step(Ug, k * dt, dt, "ssprk54")
+            else:
+                x = sd.rk_prepare(ctx, Ug)
+                for j in range(5):
+                    x = sd.rk_stage(ctx, Ug, j, dt, "ssprk54")
+        torch.cuda.synchronize()
+        out.append(Ug.cpu().numpy())
+        ctx.close()
+    assert np.all(np.isfinite(out[0]))
+    assert np.array_equal(out[0], out[1])
+    del ctypes
 
 
 @pytest.mark.parametrize("p", [2, 4])
@@ -320,6 +375,34 @@ def test_full_size_fp64_sampled(full_tgv, scheme):
         rg = Rg[:, c[2], c[1], c[0]]
         err = np.abs(rg - ro).reshape(5, -1).max(axis=1) / scale
         assert err.max() <= 1e-12, (c, err)
+
+
+@pytest.mark.parametrize("scheme", ["compact", "br1"])
+def test_full_size_fp32_sampled_within_rounding_floor(full_tgv, scheme, capsys):
+    # The FP32 residual of the benchmark grid (48^3 p4, the launch configuration the bench
+    # times) at the sampled elements, against the oracle on their 5^3 blocks (FP32-rounded
+    # input on both sides), relative L2 over the sampled elements' points: within a small
+    # multiple of the rounding floor u kappa of those points (fp32_floor.py). At this
+    # resolution the floor is 6x the 8^3 one.
+    from fp32_floor import U32 as UNIT_ROUNDOFF, conditioning, kappa
+    prm, phys = ns_phys()
+    h = 2 * np.pi / 48
+    U = full_tgv.astype(np.float32).astype(np.float64)
+    Rg = gpu_residual(U, 3, FULL_NE, (0.0,) * 3, (2 * np.pi,) * 3, FULL_P, scheme, phys, "f32")
+    ro, rg, cc = [], [], []
+    for c in SAMPLES:
+        B = _block_around(U, c)
+        Rb, Cb = conditioning(B, Grid(3, (5, 5, 5), (0.0,) * 3, (5 * h,) * 3, FULL_P), scheme, prm)
+        ro.append(Rb[:, 2, 2, 2])
+        cc.append(Cb[:, 2, 2, 2])
+        rg.append(Rg[:, c[2], c[1], c[0]])
+    ro, rg, cc = (np.stack(x, axis=1) for x in (ro, rg, cc))
+    e_l2 = np.array([np.linalg.norm(rg[v] - ro[v]) / np.linalg.norm(ro[v]) for v in range(5)])
+    floor = UNIT_ROUNDOFF * kappa(ro, cc)
+    with capsys.disabled():
+        print("\nFP32 TGV 48^3 p4 %s, sampled elements: l2-rel %s  u*kappa %s" % (
+            scheme, " ".join("%.2e" % x for x in e_l2), " ".join("%.2e" % x for x in floor)))
+    assert np.all(e_l2 <= FLOOR_FACTOR * floor), (e_l2, floor)
 
 
 @pytest.mark.parametrize("precision,tol", [("f64", 1e-13), ("f32", 1e-6)])
