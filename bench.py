@@ -487,9 +487,23 @@ def main():
     value = job_value(world, npts, ms)
     final = ctx.diagnostics(U64, t, raise_nonfinite=False)
 
-    # roofline of the dominant kernel (k_line_flux), from the live CUDA events
+    # per-kernel times of the step
+    step_kms = {k: prof[k][0] / max(prof[k][1], 1) for k in prof}
+    # roofline of the dominant kernel of the residual (k_line_flux), from live CUDA events on
+    # the context's stream: standalone FP32 residuals of the current state
     hbm, smax, peak_kind = peaks()
-    kms = {k: prof[k][0] / max(prof[k][1], 1) for k in prof}
+    Ug32r = U64.float()
+    R32r = torch.empty_like(Ug32r)
+    for _ in range(2):
+        ctx.residual(Ug32r, R32r)
+    torch.cuda.synchronize()
+    ctx.profile(True)
+    for _ in range(max(5, args.steps)):
+        ctx.residual(Ug32r, R32r)
+    rprof = ctx.profile_read()
+    ctx.profile(False)
+    del Ug32r, R32r
+    kms = {k: rprof[k][0] / max(rprof[k][1], 1) for k in rprof}
     flops = residual_flops_per_element(P + 1)
     nelem = int(np.prod(ne))
     flux_avg_ms = kms["flux_div"]
@@ -591,9 +605,9 @@ def main():
             "config": {"workload": "TGV Re=1600 Ma=0.1 Pr=0.71, %dx%dx%d hex p=4 (%d DOF, 5 vars), "
                                    "%s scheme, Roe + Sutherland, FP32 residual, SSPRK(5,4) with FP64 state, "
                                    "dt=%g" % (ne + (npts, args.scheme, DT)),
-                       "step": "one SSPRK(5,4) step = 5 residuals with the stage updates in the flux "
-                               "kernel's epilogue (FP32 stage increments, FP64 state update once per "
-                               "step); FP64 diagnostics once per timed window",
+                       "step": "one SSPRK(5,4) step = 5 residuals + 5 stage updates (FP32 stage "
+                               "increments, FP64 state update once per step); diagnostics (FP64 sums) "
+                               "once per timed window",
                        "l2": "inputs larger than L2 (FP32 state %.0f MB, FP64 state %.0f MB)"
                              % (5 * npts * 4 / 1e6, 5 * npts * 8 / 1e6),
                        "parallelism": "replicas" if world > 1 else "single GPU"},
@@ -612,9 +626,10 @@ def main():
                                       "hbm_frac_of_%s" % peak_kind: alg_bytes_res / (res_ms * 1e-3) / 1e9 / hbm,
                                       "algorithmic_bytes": alg_bytes_res},
                          "hbm_peak_gbs": hbm},
-            "kernels_ms": {"trace": kms["trace"], "grad": kms["grad"], "face": kms["face"],
-                           "flux_div": flux_avg_ms, "rk_and_other_per_launch": kms["other"],
-                           "launches": {k: prof[k][1] for k in prof}},
+            "kernels_ms": {"residual": {"trace": kms["trace"], "grad": kms["grad"], "face": kms["face"],
+                                        "flux_div": flux_avg_ms},
+                           "step_per_launch": step_kms,
+                           "step_launches_per_window": {k: prof[k][1] for k in prof}},
             "rk_stage_modes": stage_modes,
             "residual_dof_per_s": {"f32": npts / (res32_ms * 1e-3), "f64": npts / (res64_ms * 1e-3),
                                    "f32_ms": res32_ms, "f64_ms": res64_ms},

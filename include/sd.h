@@ -179,9 +179,7 @@ sd_status sd_residual_host(sd_ctx* ctx, const void* U_host, void* R_host);
  *     U + d_j, U the FP64 state at the start of the step. The increments d_j = O(dt) and
  *     the stage registers are FP32; each stage's FP32 residual is evaluated on X + d_j,
  *     X = U minus the reference offsets rounded to FP32 once per step. U itself is updated
- *     in FP64 once per step (U <- U + d_s). On Cartesian grids SD_SSPRK54 applies each stage
- *     update inside the residual's last kernel (same arithmetic, same result to the bit as
- *     sd_rk_prepare followed by sd_rk_stage).
+ *     in FP64 once per step (U <- U + d_s).
  *   SD_F32 contexts, SD_RK_STAGES_F64 (sd_set_rk_stages): FP64 stage states and registers
  *     as in SD_F64 contexts; only each stage's residual is FP32, evaluated on the FP64 stage
  *     state (offsets removed) rounded to FP32. */

@@ -266,7 +266,7 @@ static void free_all(sd_ctx* c) {
         if (c->ev_out[k]) cudaEventDestroy(c->ev_out[k]);
     }
     if (c->cl_tmode) cudaFree(c->cl_tmode);
-    void* ptrs[] = {c->Tu, c->Tu2, c->Tg, c->Fh, c->S, c->K, c->rA, c->rB, c->rC, c->rX, c->rA64, c->rB64, c->rC64, c->dW,
+    void* ptrs[] = {c->Tu, c->Tg, c->Fh, c->S, c->K, c->rA, c->rB, c->rC, c->rX, c->rA64, c->rB64, c->rC64, c->dW,
                     c->partial, c->partial2, c->dsum, c->hU, c->hR, c->cih, c->cvs, c->cTg, c->cgeo64};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -399,7 +399,6 @@ extern "C" sd_status sd_init(const sd_mesh* mesh, int p, sd_scheme scheme, const
     alloc(&c->Tu, c->ntu * c->esize);
     alloc(&c->Tg, c->ntg * c->esize);
     alloc(&c->Fh, c->nfh * c->esize);
-    if (prec == SD_F32) alloc(&c->Tu2, c->ntu * c->esize);
     if (prec == SD_F64) c->Tu64 = (double*)c->Tu;
     else alloc((void**)&c->Tu64, c->ntu * sizeof(double));
     alloc(&c->S, S * c->esize);
@@ -861,51 +860,10 @@ static sd_status rk_check(sd_ctx* c, double* U64, double dt, sd_rk rk) {
     return SD_OK;
 }
 
-#ifndef SDI_FUSED_STAGES
-#define SDI_FUSED_STAGES 0
-#endif
-
-// SSPRK(5,4) step of an FP32 context in increment form with every stage update applied by
-// the flux kernel's epilogue (sdk::StageOut): no separate stage kernels, no stage residual
-// array, and the traces of each next stage input written by the same epilogue into the
-// second trace buffer (the two buffers swap roles every stage). The arithmetic is that of
-// rk_prepare + rk_stage, so the result is the same to the bit.
-static bool fusable(const sd_ctx* c, sd_rk rk) {
-    return SDI_FUSED_STAGES && rk == SD_SSPRK54 && inc_mode(c) && !c->curv && c->Tu2 &&
-           (c->nvar == 5 || !(c->phys.kind == SD_PME && c->phys.pme_coef == SD_PME_COEF_SOLUTION));
-}
-
-static sd_status rk_step_fused(sd_ctx* c, double* U, double dt) {
-    sd_status s = rk_prepare(c, U);
-    if (s != SD_OK) return s;
-    float* X = (float*)c->rX;
-    if ((s = sdi_stage_traces_f32(c, X)) != SD_OK) return s;
-    const sdk::SSPCoef& a = kSSP;
-    sdk::StageOut so;
-    so.U = U;
-    so.A = (float*)c->rA;
-    so.B = (float*)c->rB;
-    so.C = (float*)c->rC;
-    so.X = X;
-    so.S = (float*)c->S;
-    so.c = {(float)(a.a10 * dt), (float)a.a21, (float)(a.b21 * dt), (float)a.a32, (float)(a.b32 * dt),
-            (float)a.a43, (float)(a.b43 * dt), (float)a.a52, (float)a.a53, (float)(a.b53 * dt), (float)a.a54,
-            (float)(a.b54 * dt)};
-    for (int k = 0; k < 5; ++k) {
-        so.k = k;
-        so.Tnext = (float*)c->Tu2;
-        if ((s = sdi_fused_stage_f32(c, k == 0 ? X : (const float*)c->S, &so)) != SD_OK) return s;
-        if (k < 4) std::swap(c->Tu, c->Tu2);
-    }
-    CK(cudaGetLastError());
-    return SD_OK;
-}
-
 extern "C" sd_status sd_rk_step(sd_ctx* c, double* U64, double t, double dt, sd_rk rk) {
     (void)t;
     sd_status s = rk_check(c, U64, dt, rk);
     if (s != SD_OK) return s;
-    if (fusable(c, rk)) return rk_step_fused(c, U64, dt);
     if ((s = rk_prepare(c, U64)) != SD_OK) return s;
     for (int k = 0; k < rk_stages_of(rk); ++k)
         if ((s = rk_stage(c, U64, k, dt, rk)) != SD_OK) return s;
@@ -1013,25 +971,36 @@ static sd_status diag_reduce(sd_ctx* c, int nb) {
     return SD_OK;
 }
 
-template <int N, int DIM, int NV>
-static sd_status diag_impl(sd_ctx* c, const double* U) {
+// FP64 contexts stage the state in FP64; FP32 contexts stage (U - offsets) in FP32 and form the
+// kinetic-energy and enstrophy integrands in FP32 (their sums, and the conserved totals taken
+// from U itself, stay FP64)
+template <typename real, int N, int DIM, int NV>
+static sd_status diag_impl_r(sd_ctx* c, const double* U, real* Tu) {
     using FP = Footprint<N, DIM, NV>;
-    const Ops<double, N> ops = make_ops<double, N>(c);
+    const Ops<real, N> ops = make_ops<real, N>(c);
     const Mesh g = make_mesh(c);
+    double off0 = 0.0, off4 = 0.0;
+    if (sizeof(real) == 4) stage_offsets(c, off0, off4);
     const long long ntr = (long long)g.nelem * FP::NF * NV * FP::NQ;
     sdi_prof_begin(c, SD_K_OTHER);
-    k_trace<double, N, DIM, NV><<<trace_blocks(ntr), 256, 0, c->stream>>>(U, c->Tu64, ops, g);
+    k_trace_staged<real, N, DIM, NV><<<trace_blocks(ntr), 256, 0, c->stream>>>(U, Tu, ops, g, off0, off4);
     sdi_prof_end(c, SD_K_OTHER);
     const int epb = std::max(1, 256 / FP::TPE);
     const int threads = epb * FP::TPE;
-    const size_t smem = std::max<size_t>(epb * FP::grad, (size_t)NDIAG * threads) * sizeof(double);
-    if (!set_smem(k_diag<N, DIM, NV>, smem)) return SD_EUNSUPPORTED;
+    const size_t smem = std::max<size_t>(epb * FP::grad * sizeof(real), (size_t)NDIAG * threads * sizeof(double));
+    if (!set_smem(k_diag<real, N, DIM, NV>, smem)) return smem_fail(smem);
     const int nb = (g.nelem + epb - 1) / epb;
     if (nb != c->diag_blocks) return SD_EINVAL;
     sdi_prof_begin(c, SD_K_OTHER);
-    k_diag<N, DIM, NV><<<nb, threads, smem, c->stream>>>(U, c->Tu64, ops, g, c->dW, c->J, c->partial);
+    k_diag<real, N, DIM, NV><<<nb, threads, smem, c->stream>>>(U, Tu, ops, g, c->dW, c->J, c->partial, off0, off4);
     sdi_prof_end(c, SD_K_OTHER);
     return diag_reduce(c, nb);
+}
+
+template <int N, int DIM, int NV>
+static sd_status diag_impl(sd_ctx* c, const double* U) {
+    if (c->prec == SD_F32) return diag_impl_r<float, N, DIM, NV>(c, U, (float*)c->Tu64);
+    return diag_impl_r<double, N, DIM, NV>(c, U, c->Tu64);
 }
 
 template <int N>

@@ -40,8 +40,6 @@ struct sd_ctx {
     size_t esize;            // bytes per value of the residual precision
     // scratch owned by the context
     void* Tu;                // face traces of u        [nelem][2dim][F] ([nvar][n^(dim-1)] padded to F, a multiple of 4)
-    void* Tu2;               // FP32 contexts: second trace buffer (the fused Runge-Kutta stages
-                             // write the next stage's traces while the current ones are read)
     void* Tg;                // face gradient values    [nelem][2dim][G] ([ngrad][n^(dim-1)] padded to G)
     void* Fh;                // interface fluxes        [dim][nelem][F] (+d face of each element)
     double* Tu64;            // FP64 traces for diagnostics (== Tu when prec is F64)
@@ -116,10 +114,6 @@ sd_status sdi_residual_phase_f32(sd_ctx* c, const float* U, float* R, int phase,
                                  cudaStream_t stream);
 sd_status sdi_residual_phase_f64(sd_ctx* c, const double* U, double* R, int phase, int e_begin, int e_end,
                                  cudaStream_t stream);
-// SSPRK(5,4) stage of an FP32 context with the stage update in the flux kernel's epilogue
-// (so: an sdk::StageOut); traces of a stage input into c->Tu
-sd_status sdi_fused_stage_f32(sd_ctx* c, const float* U, const void* so);
-sd_status sdi_stage_traces_f32(sd_ctx* c, const float* U);
 // curvilinear grids: set-up from the corner nodes, residual, diagnostics partial sums
 sd_status sdi_curv_setup(sd_ctx* c, const double* nodes);
 sd_status sdi_curv_residual_f32(sd_ctx* c, const float* U, float* R, int offset_in);

@@ -79,16 +79,26 @@ __device__ __forceinline__ int pt_of(int d, int i, int q) {
     return (q % lo) + lo * i + lo * N * (q / lo);
 }
 
+// (periodic wrap; the direction picks its coordinate by branches, not by indexing a local
+// array, which would live in local memory)
 __device__ __forceinline__ int neighbour(const Mesh& g, int e, int d, int side) {
-    int c0 = e % g.ne[0];
-    int r = e / g.ne[0];
-    int c1 = r % g.ne[1];
-    int c2 = r / g.ne[1];
-    int c[3] = {c0, c1, c2};
-    c[d] += side ? 1 : -1;
-    if (c[d] < 0) c[d] += g.ne[d];
-    if (c[d] >= g.ne[d]) c[d] -= g.ne[d];
-    return c[0] + g.ne[0] * (c[1] + g.ne[1] * c[2]);
+    const int nx = g.ne[0], ny = g.ne[1], nz = g.ne[2];
+    int c0 = e % nx;
+    const int r = e / nx;
+    int c1 = r % ny;
+    int c2 = r / ny;
+    const int s = side ? 1 : -1;
+    if (d == 0) {
+        c0 += s;
+        c0 = c0 < 0 ? c0 + nx : (c0 >= nx ? c0 - nx : c0);
+    } else if (d == 1) {
+        c1 += s;
+        c1 = c1 < 0 ? c1 + ny : (c1 >= ny ? c1 - ny : c1);
+    } else {
+        c2 += s;
+        c2 = c2 < 0 ? c2 + nz : (c2 >= nz ? c2 - nz : c2);
+    }
+    return c0 + nx * (c1 + ny * c2);
 }
 
 // sum_i row[i] * base[i*stride], one fixed fma sequence
@@ -330,7 +340,8 @@ __device__ __forceinline__ void stage_element(const real* __restrict__ U,
     // derivatives of rho and of the momentum components across the derivative direction:
     // the vorticity)
     if (valid) {
-        for (int k = tid; k < NV * NP; k += TPE) {
+        // (U = nullptr: the caller has staged u already)
+        for (int k = tid; U && k < NV * NP; k += TPE) {
             const int v = k / NP, pt = k - v * NP;
             su[k] = U[(size_t)v * g.nelem * NP + (size_t)e * NP + pt];
         }
@@ -410,24 +421,61 @@ __global__ void k_trace(const real* __restrict__ U, real* __restrict__ Tu, Ops<r
 constexpr int NDIAG = 10;   // ke, ke_rho, enstrophy, mass, mom0..2, energy, l2sq, nonfinite
 constexpr int DIAG_L1 = 256;   // blocks of the first level of the partials' reduction
 
-template <int N, int DIM, int NV>
-__global__ void __launch_bounds__(Footprint<N, DIM, NV>::MAXT) k_diag(const double* __restrict__ U, const double* __restrict__ Tu,
-                       Ops<double, N> ops, Mesh g, const double* __restrict__ wq, double J,
-                       double* __restrict__ partial) {
+// The diagnostics of a state whose values are staged in `real`: FP64 contexts stage U as it
+// is; FP32 contexts stage (U - offsets) rounded to FP32 (the offsets of rho and rho E, as the
+// residual kernels do) and evaluate the kinetic-energy and enstrophy integrands in FP32. Every
+// sum is FP64 and the conserved totals are taken from the FP64 state itself.
+// The face traces for the diagnostics: k_trace over the staged values.
+template <typename real, int N, int DIM, int NV>
+__global__ void k_trace_staged(const double* __restrict__ U, real* __restrict__ Tu, Ops<real, N> ops, Mesh g,
+                               double off0, double off4) {
+    constexpr int NP = ipow(N, DIM), NQ = ipow(N, DIM - 1), NF = 2 * DIM;
+    const long long total = (long long)g.nelem * NF * NV * NQ;
+    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int q = (int)(idx % NQ);
+        long long r = idx / NQ;
+        const int v = (int)(r % NV);
+        r /= NV;
+        if (NV == 5 && v == 4) continue;      // the diagnostics use no trace of rho E
+        const int f = (int)(r % NF);
+        const int e = (int)(r / NF);
+        const int d = f >> 1, s = f & 1;
+        const double off = (NV == 5 && v == 0) ? off0 : 0.0;
+        const double* src = U + (size_t)v * g.nelem * NP + (size_t)e * NP + pt_of<N>(d, 0, q);
+        real x[N];
+#pragma unroll
+        for (int i = 0; i < N; ++i) x[i] = (real)(src[i * npow<N>(d)] - off);
+        Tu[idx] = line_dot<real, N>(ops.L + (s ? N * N : 0), x, 1);
+    }
+}
+
+template <typename real, int N, int DIM, int NV>
+__global__ void __launch_bounds__(Footprint<N, DIM, NV>::MAXT) k_diag(const double* __restrict__ U, const real* __restrict__ Tu,
+                       Ops<real, N> ops, Mesh g, const double* __restrict__ wq, double J,
+                       double* __restrict__ partial, double off0, double off4) {
     using FP = Footprint<N, DIM, NV>;
     constexpr int NP = FP::NP, TPE = FP::TPE;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    double* sm = reinterpret_cast<double*>(smem_raw);
+    real* sm = reinterpret_cast<real*>(smem_raw);
     const int le = threadIdx.x / TPE, tid = threadIdx.x - le * TPE;
     const int epb = blockDim.x / TPE;
     const int e = blockIdx.x * epb + le;
     const bool valid = e < g.nelem;
-    double* base = sm + le * FP::grad;
-    double* su = base;
-    double* tro = su + FP::U;
-    double* trn = tro + FP::TR;
-    double* vS = trn + FP::TR;
-    stage_element<double, N, DIM, NV>(U, Tu, ops, g, e, valid, tid, su, tro, trn, vS);
+    real* base = sm + le * FP::grad;
+    real* su = base;
+    real* tro = su + FP::U;
+    real* trn = tro + FP::TR;
+    real* vS = trn + FP::TR;
+    // stage_element reads the state in `real`: give it the staged values through shared memory
+    if (valid) {
+        for (int k = tid; k < NV * NP; k += TPE) {
+            const int v = k / NP, pt = k - v * NP;
+            const double off = (NV == 5 && v == 0) ? off0 : ((NV == 5 && v == 4) ? off4 : 0.0);
+            su[k] = (real)(U[(size_t)v * g.nelem * NP + (size_t)e * NP + pt] - off);
+        }
+    }
+    stage_element<real, N, DIM, NV>(nullptr, Tu, ops, g, e, valid, tid, su, tro, trn, vS);
     double acc[NDIAG];
 #pragma unroll
     for (int k = 0; k < NDIAG; ++k) acc[k] = 0.0;
@@ -440,40 +488,42 @@ __global__ void __launch_bounds__(Footprint<N, DIM, NV>::MAXT) k_diag(const doub
                 w *= wq[r % N];
                 r /= N;
             }
+            const double* Ue = U + (size_t)e * NP + pt;
             bool bad = false;
 #pragma unroll
-            for (int v = 0; v < NV; ++v) bad |= !isfinite(su[v * NP + pt]);
+            for (int v = 0; v < NV; ++v) bad |= !isfinite(Ue[(size_t)v * g.nelem * NP]);
             acc[9] += bad ? 1.0 : 0.0;
             if constexpr (NV == 5) {
-                const double rho = su[pt];
-                const double vel[3] = {su[NP + pt] / rho, su[2 * NP + pt] / rho, su[3 * NP + pt] / rho};
-                const double q2 = vel[0] * vel[0] + vel[1] * vel[1] + vel[2] * vel[2];
-                double du[3][3] = {};   // du[k][i] = d u_i / d x_k, off-diagonal (the vorticity)
+                const real rho = su[pt] + (real)off0;
+                const real vel[3] = {su[NP + pt] / rho, su[2 * NP + pt] / rho, su[3 * NP + pt] / rho};
+                const real q2 = vel[0] * vel[0] + vel[1] * vel[1] + vel[2] * vel[2];
+                real du[3][3] = {};   // du[k][i] = d u_i / d x_k, off-diagonal (the vorticity)
 #pragma unroll
                 for (int k = 0; k < 3; ++k)
 #pragma unroll
                     for (int i = 0; i < 3; ++i)
                         if (i != k)
                             du[k][i] = (vS[((1 + i) * DIM + k) * NP + pt] - vel[i] * vS[(0 * DIM + k) * NP + pt]) / rho;
-                const double o0 = du[1][2] - du[2][1], o1 = du[2][0] - du[0][2], o2 = du[0][1] - du[1][0];
-                acc[0] += w * 0.5 * q2;
-                acc[1] += w * 0.5 * rho * q2;
-                acc[2] += w * (o0 * o0 + o1 * o1 + o2 * o2);
-                acc[3] += w * rho;
-                acc[4] += w * su[NP + pt];
-                acc[5] += w * su[2 * NP + pt];
-                acc[6] += w * su[3 * NP + pt];
-                acc[7] += w * su[4 * NP + pt];
+                const real o0 = du[1][2] - du[2][1], o1 = du[2][0] - du[0][2], o2 = du[0][1] - du[1][0];
+                acc[0] += w * (0.5 * (double)q2);
+                acc[1] += w * (0.5 * (double)rho * (double)q2);
+                acc[2] += w * (double)(o0 * o0 + o1 * o1 + o2 * o2);
+                const size_t S = (size_t)g.nelem * NP;
+                acc[3] += w * Ue[0];
+                acc[4] += w * Ue[S];
+                acc[5] += w * Ue[2 * S];
+                acc[6] += w * Ue[3 * S];
+                acc[7] += w * Ue[4 * S];
             } else {
-                const double u = su[pt];
+                const double u = Ue[0];
                 acc[3] += w * u;
                 acc[8] += w * u * u;
             }
         }
     }
-    // deterministic block reduction (fixed tree over the threads)
+    // deterministic block reduction (fixed tree over the threads), in FP64
     __syncthreads();
-    double* red = sm;   // reuse shared memory: NDIAG * blockDim doubles fit in FP::grad*epb
+    double* red = reinterpret_cast<double*>(smem_raw);   // NDIAG * blockDim doubles fit (host sizes it)
     for (int k = 0; k < NDIAG; ++k) red[k * blockDim.x + threadIdx.x] = acc[k];
     __syncthreads();
     for (int s = 1; s < (int)blockDim.x; s <<= 1) {
@@ -607,8 +657,7 @@ struct SSPInc {
 // One point of stage k of that form: kk is the stage residual, x the step-start value minus
 // the offsets, a / b / cc the increment registers A, B, C at the point (updated in place).
 // Stages 0-3 return the next stage input x + d; stage 4 updates the FP64 state u. Every
-// operation is explicitly rounded, so that k_ssp_inc and the flux kernel's stage epilogue
-// (which applies this to the residual it has just formed) produce the same bits.
+// operation is explicitly rounded (no contraction into other operations).
 __device__ __forceinline__ float ssp_inc_point(const SSPInc& c, int k, float kk, float x, float& a, float& b,
                                                float& cc, double& u) {
     if (k == 0) {
@@ -636,18 +685,6 @@ __device__ __forceinline__ float ssp_inc_point(const SSPInc& c, int k, float kk,
     return 0.0f;
 }
 
-// The stage update that the flux kernel applies in its epilogue instead of writing R (FP32
-// contexts, SSPRK(5,4) in increment form): registers, next stage input S and (stages 0-3)
-// the face traces of S for the next residual, in a second trace buffer.
-struct StageOut {
-    int k;                   // stage 0..4; -1: no stage, the kernel writes R
-    double* U;               // FP64 state (stage 4)
-    float *A, *B, *C;        // increment registers
-    const float* X;          // the step's start state minus the offsets
-    float* S;                // next stage input
-    float* Tnext;            // traces of S (stages 0-3)
-    SSPInc c;
-};
 
 __global__ void k_ssp_inc(int k, double* __restrict__ U, float* __restrict__ A, float* __restrict__ B,
                           float* __restrict__ C, const float* __restrict__ K, const float* __restrict__ X,

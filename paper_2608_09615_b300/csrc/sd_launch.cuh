@@ -257,7 +257,7 @@ static sd_status closure_stage(sd_ctx* c, const real* U, int offset_in) {
 // elements it touches (its own and their face neighbours).
 template <typename real, int N, int DIM, int NV>
 static sd_status residual_phase(sd_ctx* c, const real* U, real* R, int offset_in, int phase, int e_begin,
-                                int e_end, cudaStream_t stream, const StageOut* stage = nullptr) {
+                                int e_end, cudaStream_t stream) {
     using LL = LineLayout<N, DIM, NV>;
     using FL = FluxLayout<N, DIM, NV>;
     const LineGeo<real> geo = make_geo<real>(c, offset_in);
@@ -296,11 +296,8 @@ static sd_status residual_phase(sd_ctx* c, const real* U, real* R, int offset_in
         const int bf = persistent_grid(k_line_flux<real, N, DIM, NV>, FL::THREADS, sf, (ne + FL::EB - 1) / FL::EB,
                                        c->device);
         sdi_prof_begin(c, SD_K_FLUX);
-        StageOut so;
-        if (stage) so = *stage;
-        else so.k = -1;
         k_line_flux<real, N, DIM, NV><<<bf, FL::THREADS, sf, stream>>>(U, Tu, Fh, R, geo, g, P, c->tau,
-                                                                       make_flux_ops<real, N>(c), so);
+                                                                       make_flux_ops<real, N>(c));
         sdi_prof_end(c, SD_K_FLUX);
     }
     const cudaError_t err = cudaGetLastError();
@@ -327,40 +324,24 @@ static sd_status residual_impl(sd_ctx* c, const real* U, real* R, int offset_in)
 
 template <typename real, int N>
 static sd_status phase_n(sd_ctx* c, const real* U, real* R, int offset_in, int phase, int eb, int ee,
-                         cudaStream_t st, const StageOut* so) {
-    if (c->nvar == 5) return residual_phase<real, N, 3, 5>(c, U, R, offset_in, phase, eb, ee, st, so);
-    if (c->dim == 1) return residual_phase<real, N, 1, 1>(c, U, R, offset_in, phase, eb, ee, st, so);
-    return residual_phase<real, N, 3, 1>(c, U, R, offset_in, phase, eb, ee, st, so);
+                         cudaStream_t st) {
+    if (c->nvar == 5) return residual_phase<real, N, 3, 5>(c, U, R, offset_in, phase, eb, ee, st);
+    if (c->dim == 1) return residual_phase<real, N, 1, 1>(c, U, R, offset_in, phase, eb, ee, st);
+    return residual_phase<real, N, 3, 1>(c, U, R, offset_in, phase, eb, ee, st);
 }
 
 template <typename real>
 static sd_status phase_dispatch(sd_ctx* c, const real* U, real* R, int offset_in, int phase, int eb, int ee,
-                                cudaStream_t st, const StageOut* so = nullptr) {
+                                cudaStream_t st) {
     switch (c->n) {
-        case 2: return phase_n<real, 2>(c, U, R, offset_in, phase, eb, ee, st, so);
-        case 3: return phase_n<real, 3>(c, U, R, offset_in, phase, eb, ee, st, so);
-        case 4: return phase_n<real, 4>(c, U, R, offset_in, phase, eb, ee, st, so);
-        case 5: return phase_n<real, 5>(c, U, R, offset_in, phase, eb, ee, st, so);
-        case 6: return phase_n<real, 6>(c, U, R, offset_in, phase, eb, ee, st, so);
-        case 7: return phase_n<real, 7>(c, U, R, offset_in, phase, eb, ee, st, so);
-        case 8: return phase_n<real, 8>(c, U, R, offset_in, phase, eb, ee, st, so);
-        case 9: return phase_n<real, 9>(c, U, R, offset_in, phase, eb, ee, st, so);
-        default: return SD_EUNSUPPORTED;
-    }
-}
-
-// the learned closure's per-residual work (features of U, network) for the fused stages
-template <typename real>
-static sd_status closure_dispatch(sd_ctx* c, const real* U, int offset_in) {
-    switch (c->n) {
-        case 2: return closure_stage<real, 2>(c, U, offset_in);
-        case 3: return closure_stage<real, 3>(c, U, offset_in);
-        case 4: return closure_stage<real, 4>(c, U, offset_in);
-        case 5: return closure_stage<real, 5>(c, U, offset_in);
-        case 6: return closure_stage<real, 6>(c, U, offset_in);
-        case 7: return closure_stage<real, 7>(c, U, offset_in);
-        case 8: return closure_stage<real, 8>(c, U, offset_in);
-        case 9: return closure_stage<real, 9>(c, U, offset_in);
+        case 2: return phase_n<real, 2>(c, U, R, offset_in, phase, eb, ee, st);
+        case 3: return phase_n<real, 3>(c, U, R, offset_in, phase, eb, ee, st);
+        case 4: return phase_n<real, 4>(c, U, R, offset_in, phase, eb, ee, st);
+        case 5: return phase_n<real, 5>(c, U, R, offset_in, phase, eb, ee, st);
+        case 6: return phase_n<real, 6>(c, U, R, offset_in, phase, eb, ee, st);
+        case 7: return phase_n<real, 7>(c, U, R, offset_in, phase, eb, ee, st);
+        case 8: return phase_n<real, 8>(c, U, R, offset_in, phase, eb, ee, st);
+        case 9: return phase_n<real, 9>(c, U, R, offset_in, phase, eb, ee, st);
         default: return SD_EUNSUPPORTED;
     }
 }

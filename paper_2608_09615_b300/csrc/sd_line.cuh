@@ -45,9 +45,7 @@
 #ifndef SD_FLUX_MAXNREG
 #define SD_FLUX_MAXNREG 136
 #endif
-#ifndef SD_FLUX_UNROLL
-#define SD_FLUX_UNROLL 0
-#endif
+
 
 namespace sdk {
 
@@ -827,15 +825,13 @@ k_face_flux(const real* __restrict__ Tu, const real* __restrict__ Tg, real* __re
 // fluxes along D at the n+1 flux points of line q and their divergence on the line: the
 // interface fluxes at f = 0 and f = N come from Fh, the n-1 interior ones are evaluated here.
 // The flux-point loop is kept rolled (unrolling it for n = 5 measured 0.98 against 0.80 ms
-// per launch at 48^3 on B300: the larger body costs more than the constant operands save);
-// SD_FLUX_UNROLL=1 unrolls it for n <= 6.
+// per launch at 48^3 on B300: the larger body costs more than the constant operands save).
 template <typename real, int N, int DIM, int NV, int D, class ST>
 __device__ __forceinline__ void line_flux(const FluxOps<real, N>& fo, const Phys<real>& P, const real (&u)[NV][N],
                                           const real (&dl)[NV], const real (&dr)[NV], const real* vS,
                                           const real* fh, int q, real (&r)[NV][N], const float* tau_own) {
     using LL = LineLayout<N, DIM, NV>;
     constexpr int NP = LL::NP, NQ = LL::NQ, NG = LL::NG;
-    constexpr int UNR = (SD_FLUX_UNROLL && N <= 6) ? N - 1 : 1;
     const OpTab<real, N>& op = c_op<real, N>;
     // interface flux points (f = 0 and f = N)
 #pragma unroll
@@ -848,7 +844,7 @@ __device__ __forceinline__ void line_flux(const FluxOps<real, N>& fo, const Phys
     // interior flux points: extrapolated solution and gradient (Eq. aux:v:std:2d); the
     // normal derivatives come from u and the face corrections, the transverse ones from the
     // kept v^S
-#pragma unroll UNR
+#pragma unroll 1
     for (int f = 1; f < N; ++f) {
         const real* Lr = op.L + f * N;
         real uf[NV], F[NV];
@@ -904,7 +900,7 @@ template <typename real, int N, int DIM, int NV>
 __global__ void __maxnreg__((FluxLayout<N, DIM, NV>::FLUX_REGS))
 k_line_flux(const real* __restrict__ U, const real* __restrict__ Tu, const real* __restrict__ Fh,
             real* __restrict__ R, LineGeo<real> geo, Mesh g, Phys<real> P, const float* __restrict__ tau,
-            const __grid_constant__ FluxOps<real, N> fo, const __grid_constant__ StageOut so) {
+            const __grid_constant__ FluxOps<real, N> fo) {
     using LL = FluxLayout<N, DIM, NV>;
     using PL = FluxPipe<real, LL>;
     using ST = ResStrides<LL>;
@@ -973,49 +969,7 @@ k_line_flux(const real* __restrict__ U, const real* __restrict__ Tu, const real*
                 acc = acc + rd[NV * NP];
                 acc = acc + rd[2 * NV * NP];
             }
-            const size_t gi = (size_t)v * g.nelem * NP + (size_t)(e0 + eb) * NP + pt;
-            if constexpr (sizeof(real) == 4) {
-                if (so.k >= 0) {
-                    // stage epilogue: the residual feeds the stage update directly; the next
-                    // stage input goes to S and, for its traces, to this group's u staging
-                    float a = 0.0f, bb = 0.0f, cc = 0.0f;
-                    double uu = 0.0;
-                    const float x = so.k < 4 ? so.X[gi] : 0.0f;
-                    if (so.k >= 1 && so.k != 2) a = so.A[gi];
-                    if (so.k >= 1 && so.k <= 3) bb = so.B[gi];
-                    if (so.k == 4) { cc = so.C[gi]; uu = so.U[gi]; }
-                    const float s = ssp_inc_point(so.c, so.k, (float)acc, x, a, bb, cc, uu);
-                    if (so.k == 4) {
-                        so.U[gi] = uu;
-                    } else {
-                        so.S[gi] = s;
-                        if (so.k == 1) so.B[gi] = bb;
-                        else so.A[gi] = a;
-                        if (so.k == 3) so.C[gi] = cc;
-                        buf[v * EB * NP + eb * NP + pt] = (real)s;
-                    }
-                    continue;
-                }
-            }
-            R[gi] = acc;
-        }
-        if constexpr (sizeof(real) == 4) {
-            if (so.k >= 0 && so.k < 4) {
-                // face traces of the next stage input (the same line_traces as k_line_trace)
-                __syncthreads();
-                if (live) {
-                    const real* sn = buf + id.eb * NP;
-                    real* out = reinterpret_cast<real*>(so.Tnext) + (size_t)e * NF * LL::FST + id.q;
-                    constexpr int FST = LL::FST, NQ = LL::NQ;
-                    if (id.d == 0) line_traces<real, N, NQ, NV, 0, ST>(sn, id.q, out, out + FST, NQ);
-                    if constexpr (DIM == 3) {
-                        if (id.d == 1) line_traces<real, N, NQ, NV, 1, ST>(sn, id.q, out + 2 * FST, out + 3 * FST, NQ);
-                        if (id.d == 2) line_traces<real, N, NQ, NV, 2, ST>(sn, id.q, out + 4 * FST, out + 5 * FST, NQ);
-                    }
-                }
-                // the next group's copies may target this buffer
-                __syncthreads();
-            }
+            R[(size_t)v * g.nelem * NP + (size_t)(e0 + eb) * NP + pt] = acc;
         }
     }
 }

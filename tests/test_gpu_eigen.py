@@ -81,3 +81,17 @@ def test_dirac_spectrum_peaks_where_eigenanalysis_predicts(p):
     # sits where the physical modes are still large
     assert max(ratios) >= 5.0
     assert min(ratios) >= 1.2
+
+
+@pytest.mark.parametrize("eta", [0.0, 0.05])
+@pytest.mark.parametrize("scheme", ["compact", "br1"])
+@pytest.mark.parametrize("p", [1, 3, 4])
+def test_combined_mode_of_probed_operator_matches_sec3(p, scheme, eta):
+    # Appendix A's combined-mode curves from the Bloch operator probed out of the GPU
+    # residual equal those of the operator built from the Sec. 3 matrices
+    from oracle.operators import operators
+    th, G, om = eigen.combined_curves(p, scheme, eta, t=0.1, nth=37)
+    xi = operators(p + 1).xs
+    G3, om3 = eigen.combined_mode(lambda a: bloch_B(p + 1, a, scheme, h=1.0, eta_ip=eta), xi, th, 0.1)
+    assert np.allclose(G, G3, rtol=1e-9, atol=1e-12)
+    assert np.allclose(om.imag, om3.imag, rtol=1e-7, atol=1e-9)

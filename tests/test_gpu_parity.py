@@ -223,11 +223,10 @@ def test_rk_step_fp32_residual_close_to_fp64():
 
 
 @pytest.mark.parametrize("case", ["ns_compact", "ns_br1", "heat3d", "ns_closure_tau"])
-def test_fused_ssprk_step_equals_stage_by_stage(case):
-    # FP32 contexts apply each SSPRK(5,4) stage update in the flux kernel's epilogue (and write
-    # the next stage's traces there); the stage-by-stage calls run the separate stage kernels.
-    # Same arithmetic: the states agree to the bit, over several steps (odd and even grids,
-    # whose element groups end mid-block).
+def test_rk_step_equals_stage_by_stage(case):
+    # sd_rk_step and sd_rk_prepare followed by sd_rk_stage for every stage (the form a
+    # decomposed grid uses, exchanging halos between stages) give the same state to the bit,
+    # over several steps, on odd and even grids.
     import ctypes
     if case == "heat3d":
         ne, p, scheme = (5, 3, 4), 3, "compact"
@@ -240,14 +239,14 @@ def test_fused_ssprk_step_equals_stage_by_stage(case):
         U = inputs.tgv_3d(ne, p, perturb_seed=6)
     dt = 2e-3
     out = []
-    for fused in (True, False):
+    for whole_step in (True, False):
         ctx = sd.SD(3, ne, (0.0,) * 3, (TWO_PI,) * 3, p, scheme, phys, "f32")
         if case == "ns_closure_tau":
             tau = torch.linspace(-1e-3, 1e-3, int(np.prod(ne)) * 15, device="cuda").view(-1, 15).contiguous()
             ctx.set_flux_tau(tau)
         Ug = torch.from_numpy(U.copy()).cuda()
         for k in range(3):
-            if fused:
+            if whole_step:
                 ctx.rk_step(Ug, k * dt, dt, "ssprk54")
             else:
                 x = sd.rk_prepare(ctx, Ug)
@@ -261,18 +260,26 @@ def test_fused_ssprk_step_equals_stage_by_stage(case):
     del ctypes
 
 
+@pytest.mark.parametrize("precision", ["f64", "f32"])
 @pytest.mark.parametrize("p", [2, 4])
-def test_diagnostics_parity_ns(p):
+def test_diagnostics_parity_ns(p, precision):
+    # FP64 contexts: every integrand in FP64 (1e-12). FP32 contexts form the kinetic-energy
+    # and enstrophy integrands in FP32 from the offset state and sum them in FP64 (FP32
+    # rounding of each point's value: 1e-6 relative on the sums); the conserved totals come
+    # from the FP64 state in both (1e-12).
     prm, phys = ns_phys()
     ne = (4, 3, 5)
     lo, hi = (0.0,) * 3, (TWO_PI,) * 3
     g = Grid(3, ne, lo, hi, p)
     U = inputs.tgv_3d(ne, p, perturb_seed=4)
     do = ns_diagnostics(U, g)
-    ctx = sd.SD(3, ne, lo, hi, p, "compact", phys, "f32")
+    ctx = sd.SD(3, ne, lo, hi, p, "compact", phys, precision)
     dg = ctx.diagnostics(torch.from_numpy(U).cuda(), 0.5)
     ctx.close()
-    for k in ("ke", "ke_rho", "enstrophy", "mass", "energy", "volume"):
+    tol = 1e-12 if precision == "f64" else 1e-6
+    for k in ("ke", "ke_rho", "enstrophy"):
+        assert dg[k] == pytest.approx(do[k], rel=tol), k
+    for k in ("mass", "energy", "volume"):
         assert dg[k] == pytest.approx(do[k], rel=1e-12), k
     for i in range(3):
         assert dg["mom"][i] == pytest.approx(do["mom"][i], abs=1e-12 * do["mass"])

@@ -92,7 +92,8 @@ def test_initial_state_and_conservation(trajectories):
     for prec, rec in trajectories.items():
         r0 = rec[0]
         rel, mom = tol[prec]
-        assert r0["ke"] / r0["volume"] == pytest.approx(1.0 / 8.0, abs=1e-12)
+        # (FP32 contexts form the kinetic-energy integrand in FP32, summed in FP64)
+        assert r0["ke"] / r0["volume"] == pytest.approx(1.0 / 8.0, abs=1e-12 if prec == "f64" else 1e-7)
         for r in rec:
             assert r["nonfinite"] == 0
             assert r["mass"] == pytest.approx(r0["mass"], rel=rel)
