@@ -7,8 +7,9 @@
 // direction is a template parameter, so every index into the per-thread arrays below is a
 // compile-time constant and the arrays live in registers. A lane loads its line once and
 // produces all n+1 flux-point values, the fluxes there and the divergence contribution
-// to the n points of the line. The flux-point loop is not unrolled (its operator rows
-// come from constant memory), which keeps one copy of the flux code per direction.
+// to the n points of the line. The flux-point loop is not unrolled (its operator rows,
+// with the grid metric folded in, are a __grid_constant__ kernel parameter), which keeps
+// one copy of the flux code per direction.
 //
 // Kernels per residual (Sec. 2.3 steps 1-5):
 //   k_line_trace  u at the 2*DIM faces (step 1, interface rows)            -> Tu
@@ -34,8 +35,9 @@
 // the trace and gradient kernels, 96 for k_line_flux, with a register cap of 136 for the
 // latter (further limited to what one block of the layout can use). For the FP32
 // Navier-Stokes n = 5 case on B300 this gives 5 resident flux blocks per SM without
-// spills; it measured fastest among the layouts tried (192 threads / 143 registers:
-// 1.24 ms per launch at 48^3, 96 / 136: 1.11 ms; 192 / 112: 1.25 ms).
+// spills; it measured fastest among the layouts tried (on an earlier form of the kernel,
+// per launch at 48^3: 192 threads / 143 registers 1.24 ms, 96 / 136 1.11 ms, 192 / 112
+// 1.25 ms).
 #ifndef SD_LINE_THREADS
 #define SD_LINE_THREADS 192
 #endif
@@ -75,9 +77,10 @@ struct LineGeo {
 };
 
 // Operator rows of the flux kernel with the grid's metric folded in, per direction d (a
-// kernel parameter, so that with the flux points unrolled every coefficient is a constant
-// operand): the divergence weights -(2/h_d) M and the normal-derivative rows (2/h_d) L D,
-// (2/h_d) (L M)[:,0], (2/h_d) (L M)[:,N] at the flux points.
+// kernel parameter, read from the constant bank by the flux-point loop, so no per-point
+// scaling by 2/h_d is left in the loop): the divergence weights -(2/h_d) M and the
+// normal-derivative rows (2/h_d) L D, (2/h_d) (L M)[:,0], (2/h_d) (L M)[:,N] at the flux
+// points.
 template <typename real, int N>
 struct FluxOps {
     real Mn[3][N][N + 1];    // -(2/h_d) M[i][f]
