@@ -110,8 +110,8 @@ def curv_flops_per_element(n, nv=5):
 # DRAM traffic of one k_line_flux launch at 48^3 p=4 (FP32, compact), from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum of that kernel), valid only while the kernel
 # sources hash to the value recorded with it.
-FLUX_TRAFFIC = {"ne": 48, "bytes": 796335360 + 253035264,
-                "sources_sha256": "a09622cb15fb1beebb215fe8cf6072c867da72f71ace0f77318838e6163d44fe"}
+FLUX_TRAFFIC = {"ne": 48, "bytes": 799130880 + 251265280,
+                "sources_sha256": "63decc492db74d1c20314b399808b6847c28698c2e8cb0f6ac1ff1395200694e"}
 FLUX_SOURCES = ("paper_2608_09615_b300/csrc/sd_line.cuh", "paper_2608_09615_b300/csrc/sd_kernels.cuh")
 
 
