@@ -552,15 +552,29 @@ __device__ __forceinline__ double stage_offset(const StageOff& o, size_t i) {
     return i < o.npts ? o.off0 : (i >= 4 * o.npts ? o.off4 : 0.0);
 }
 
+// y = x - offsets, rounded to real. Each thread handles 4 values spaced one grid apart per
+// iteration and issues their loads together (one load in flight per thread reached only
+// half the copy bandwidth). FP64 subtraction only in the first and last variable (FP64
+// issue is scarce; the test is on the index, not on the offset's value).
 template <typename real>
 __global__ void k_to_real(const double* __restrict__ x, real* __restrict__ y, size_t n, StageOff o) {
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (size_t)gridDim.x * blockDim.x) {
-        // FP64 subtraction only in the first and last variable (FP64 issue is scarce; the
-        // test is on the index, not on the offset's value)
-        if (i < o.npts) y[i] = (real)(x[i] - o.off0);
-        else if (i >= 4 * o.npts) y[i] = (real)(x[i] - o.off4);
-        else y[i] = (real)x[i];
+    constexpr int W = 4;
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t base = (size_t)blockIdx.x * blockDim.x + threadIdx.x; base < n; base += W * stride) {
+        double v[W];
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+            const size_t i = base + w * stride;
+            v[w] = i < n ? x[i] : 0.0;
+        }
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+            const size_t i = base + w * stride;
+            if (i >= n) continue;
+            if (i < o.npts) y[i] = (real)(v[w] - o.off0);
+            else if (i >= 4 * o.npts) y[i] = (real)(v[w] - o.off4);
+            else y[i] = (real)v[w];
+        }
     }
 }
 

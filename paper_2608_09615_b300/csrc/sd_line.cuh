@@ -311,10 +311,12 @@ struct FluxWork;
 template <typename real, class LL>
 using FluxPipe = Pipe<LL, true, true, real, FluxWork<LL>::value>;
 
-// work values per element of the flux kernel: the kept v^S, later R_d
+// work values per element of the flux kernel: the kept v^S, then the per-direction
+// contributions R_d in a region of their own (so that writing them needs no barrier after
+// the flux loops have read v^S)
 template <class LL>
 struct FluxWork {
-    static constexpr int value = LL::S_VR > LL::S_RD ? LL::S_VR : LL::S_RD;
+    static constexpr int value = LL::S_VR + LL::S_RD;
 };
 
 template <class LL>
@@ -366,10 +368,14 @@ __device__ __forceinline__ void stage_issue(const real* __restrict__ U, const re
     }
 }
 
-// Pipeline steps. The neighbour table of a group is computed one iteration ahead, in the
-// tail of the previous group (pipe_tail, before that group's last barrier), so issuing a
-// group's copies needs no barrier of its own. With two copies the tables alternate
-// (nbr0 / nbr1 for even / odd iterations); with one, nbr0 is used throughout.
+// Pipeline steps. Iteration k of a block handles group g_k = blockIdx + k * grid. With two
+// copies, iteration k waits for the copies of g_k, passes one barrier, and only then issues
+// the copies of g_{k+1} into the other copy: every thread has finished reading that copy
+// (group g_{k-1}) before the barrier, so no barrier is needed at the end of an iteration.
+// The neighbour table of g_{k+2} is built in the same place, into the table g_k used (the
+// tables alternate, nbr0 / nbr1 for even / odd k), so it is complete one barrier before
+// its copies are issued. With one copy (the largest n in FP64) iteration k issues and waits
+// for its own group, behind a barrier that ends the previous iteration's reads.
 template <typename real, class LL, class PL, int NV, bool NB_TR, bool FH>
 __device__ __forceinline__ void pipe_start(const real* __restrict__ U, const real* __restrict__ Tu,
                                            const real* __restrict__ Fh, const Mesh& g, int grp, int ngroups,
@@ -387,29 +393,26 @@ __device__ __forceinline__ void pipe_start(const real* __restrict__ U, const rea
     }
 }
 
-// at the top of iteration b (0, 1, 0, ...) for group grp: with two copies, start loading
-// the next group (if any) into the other copy; with one, load this group. Then wait for
-// this group's copies, make them visible to the block and remove the reference offsets.
-template <typename real, class LL, class PL, int NV, bool NB_TR, bool FH>
+// top of iteration k (b = k & 1) for group grp: wait for this group's copies and make them
+// visible to the block, then start the next group's copies (two copies). With OFFS the
+// reference offsets are removed from the staged u in one pass (one more barrier); without,
+// the staged u keeps the stored values and the line functions remove the offsets as they
+// load their lines (the same FP32 subtraction, so the results are the same).
+template <typename real, class LL, class PL, int NV, bool NB_TR, bool FH, bool OFFS = false>
 __device__ __forceinline__ void pipe_next(const real* __restrict__ U, const real* __restrict__ Tu,
                                           const real* __restrict__ Fh, const Mesh& g, int grp, int ngroups, int b,
-                                          real* buf0, real* buf1, int* nbr0, int* nbr1, real off0, real off4) {
+                                          bool first, real* buf0, real* buf1, int* nbr0, int* nbr1,
+                                          real off0 = real(0), real off4 = real(0)) {
     real* buf = b ? buf1 : buf0;
-    if constexpr (PL::NBUF == 2) {
-        const int gn = grp + gridDim.x;
-        if (gn < ngroups)
-            stage_issue<real, LL, PL, NV, NB_TR, FH>(U, Tu, Fh, g, grp_first<LL::EB>(g, gn), grp_count<LL::EB>(g, gn),
-                                                     b ? buf0 : buf1, b ? nbr0 : nbr1);
-        cp_async_commit();
-        cp_async_wait_group<1>();
-    } else {
+    if constexpr (PL::NBUF == 1) {
+        if (!first) __syncthreads();                 // the previous group's reads of buf0 are done
         stage_issue<real, LL, PL, NV, NB_TR, FH>(U, Tu, Fh, g, grp_first<LL::EB>(g, grp), grp_count<LL::EB>(g, grp),
                                                  buf, nbr0);
         cp_async_commit();
-        cp_async_wait_group<0>();
     }
+    cp_async_wait_group<0>();
     __syncthreads();
-    if (NV == 5 && (off0 != real(0) || off4 != real(0))) {
+    if constexpr (OFFS && NV == 5) {
         const int span = grp_count<LL::EB>(g, grp) * LL::NP;
         real* u0 = buf;
         real* u4 = buf + 4 * LL::EB * LL::NP;
@@ -419,31 +422,50 @@ __device__ __forceinline__ void pipe_next(const real* __restrict__ U, const real
         }
         __syncthreads();
     }
+    constexpr bool NB = NB_TR || FH;
+    if constexpr (PL::NBUF == 2) {
+        const int gn = grp + gridDim.x;
+        if (gn < ngroups) {
+            stage_issue<real, LL, PL, NV, NB_TR, FH>(U, Tu, Fh, g, grp_first<LL::EB>(g, gn), grp_count<LL::EB>(g, gn),
+                                                     b ? buf0 : buf1, b ? nbr0 : nbr1);
+            cp_async_commit();
+        }
+        const int ga = grp + 2 * gridDim.x;
+        if (NB && ga < ngroups)
+            nbr_table<LL>(g, grp_first<LL::EB>(g, ga), grp_count<LL::EB>(g, ga), b ? nbr1 : nbr0);
+    } else {
+        const int gn = grp + gridDim.x;
+        if (NB && gn < ngroups) nbr_table<LL>(g, grp_first<LL::EB>(g, gn), grp_count<LL::EB>(g, gn), nbr0);
+    }
 }
 
-// tail of iteration b for group grp, before the iteration's last barrier: the neighbour
-// table of the group whose copies are issued next (two copies: grp + 2 grid into this
-// group's table; one copy: grp + grid into nbr0)
-template <class LL, class PL, bool NB>
-__device__ __forceinline__ void pipe_tail(const Mesh& g, int grp, int ngroups, int b, int* nbr0, int* nbr1) {
-    if constexpr (NB) {
-        const int ga = grp + (PL::NBUF == 2 ? 2 : 1) * gridDim.x;
-        if (ga < ngroups)
-            nbr_table<LL>(g, grp_first<LL::EB>(g, ga), grp_count<LL::EB>(g, ga), (PL::NBUF == 2 && b) ? nbr1 : nbr0);
+// staged value of variable v with the reference offset removed (Navier-Stokes: rho - rho0
+// and rho E - rho E0; the same FP32 subtraction wherever a line loads the point)
+template <typename real, int NV>
+__device__ __forceinline__ real unoffset(real x, int v, real off0, real off4) {
+    if constexpr (NV == 5) {
+        if (v == 0) return x - off0;
+        if (v == 4) return x - off4;
     }
+    return x;
 }
 
 // ---------------------------------------------------------------- line functions
 // own traces at the two faces of direction D for every variable of line q; outL/outR
 // point at the face blocks, ostride between variables
-template <typename real, int N, int NQ, int NV, int D, class ST>
-__device__ __forceinline__ void line_traces(const real* su, int q, real* outL, real* outR, int ostride) {
+// (OFF: su holds the stored values and the reference offsets are removed here)
+template <typename real, int N, int NQ, int NV, int D, class ST, bool OFF = false>
+__device__ __forceinline__ void line_traces(const real* su, int q, real* outL, real* outR, int ostride,
+                                            real off0 = real(0), real off4 = real(0)) {
     const OpTab<real, N>& op = c_op<real, N>;
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
         real u[N];
 #pragma unroll
-        for (int i = 0; i < N; ++i) u[i] = su[v * ST::US + lpt<N, D>(i, q)];
+        for (int i = 0; i < N; ++i) {
+            u[i] = su[v * ST::US + lpt<N, D>(i, q)];
+            if constexpr (OFF) u[i] = unoffset<real, NV>(u[i], v, off0, off4);
+        }
         outL[v * ostride] = dotc<real, N>(op.L, u);
         outR[v * ostride] = dotc<real, N>(op.L + N * N, u);
     }
@@ -518,7 +540,7 @@ __device__ __forceinline__ void prologue(const LineGeo<real>& geo, const LineId&
 // k_line_trace), delta_L = (trace_nb - trace_own)/2 at face 2D, delta_R at face 2D+1
 // (Eq. c:flux), and (Navier-Stokes) v^S along D of rho and of the two momentum
 // components across D (Eq. w:e; vslot)
-template <typename real, int N, int DIM, int NV, int D, class ST>
+template <typename real, int N, int DIM, int NV, int D, class ST, bool OFF>
 __device__ __forceinline__ void line_load(const LineGeo<real>& geo, const real* su, const real* trn, real* vS,
                                           int q, real (&u)[NV][N], real (&dl)[NV], real (&dr)[NV]) {
     constexpr int NP = ipow(N, DIM), NQ = ipow(N, DIM - 1);
@@ -526,7 +548,10 @@ __device__ __forceinline__ void line_load(const LineGeo<real>& geo, const real* 
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
 #pragma unroll
-        for (int i = 0; i < N; ++i) u[v][i] = su[v * ST::US + lpt<N, D>(i, q)];
+        for (int i = 0; i < N; ++i) {
+            u[v][i] = su[v * ST::US + lpt<N, D>(i, q)];
+            if constexpr (OFF) u[v][i] = unoffset<real, NV>(u[v][i], v, geo.off0, geo.off4);
+        }
         const real tl = dotc<real, N>(op.L, u[v]);
         const real tr = dotc<real, N>(op.L + N * N, u[v]);
         dl[v] = real(0.5) * (trn[(2 * D) * ST::FS + v * NQ + q] - tl);
@@ -549,15 +574,15 @@ __device__ __forceinline__ void line_load(const LineGeo<real>& geo, const real* 
 
 // line_load for the warp's direction, then (Navier-Stokes) the barrier after which every
 // kept v^S component is visible
-template <typename real, int N, int DIM, int NV, class ST>
+template <typename real, int N, int DIM, int NV, class ST, bool OFF>
 __device__ __forceinline__ void prologue_res(const LineGeo<real>& geo, const LineId& id, bool live,
                                              const real* su, const real* trn, real* vS, real (&u)[NV][N],
                                              real (&dl)[NV], real (&dr)[NV]) {
     if (live) {
-        if (id.d == 0) line_load<real, N, DIM, NV, 0, ST>(geo, su, trn, vS, id.q, u, dl, dr);
+        if (id.d == 0) line_load<real, N, DIM, NV, 0, ST, OFF>(geo, su, trn, vS, id.q, u, dl, dr);
         if constexpr (DIM == 3) {
-            if (id.d == 1) line_load<real, N, DIM, NV, 1, ST>(geo, su, trn, vS, id.q, u, dl, dr);
-            if (id.d == 2) line_load<real, N, DIM, NV, 2, ST>(geo, su, trn, vS, id.q, u, dl, dr);
+            if (id.d == 1) line_load<real, N, DIM, NV, 1, ST, OFF>(geo, su, trn, vS, id.q, u, dl, dr);
+            if (id.d == 2) line_load<real, N, DIM, NV, 2, ST, OFF>(geo, su, trn, vS, id.q, u, dl, dr);
         }
     }
     if constexpr (NV == 5) __syncthreads();
@@ -619,16 +644,19 @@ k_line_trace(const real* __restrict__ U, real* __restrict__ Tu, LineGeo<real> ge
     for (int b = 0; grp < ngroups; grp += gridDim.x, b ^= 1) {
         real* buf = b ? buf1 : buf0;
         const int e0 = grp_first<LL::EB>(g, grp);
-        pipe_next<real, LL, PL, NV, false, false>(U, nullptr, nullptr, g, grp, ngroups, b, buf0, buf1, nullptr,
-                                                  nullptr, geo.off0, geo.off4);
+        pipe_next<real, LL, PL, NV, false, false>(U, nullptr, nullptr, g, grp, ngroups, b, grp == (int)blockIdx.x,
+                                                  buf0, buf1, nullptr, nullptr);
         const int e = e0 + id.eb;
         if (id.ok && e < g.e_end) {
             const real* su = buf + id.eb * NP;
             real* out = Tu + (size_t)e * NF * FST + id.q;
-            if (id.d == 0) line_traces<real, N, NQ, NV, 0, ST>(su, id.q, out, out + FST, NQ);
+            const real o0 = geo.off0, o4 = geo.off4;
+            if (id.d == 0) line_traces<real, N, NQ, NV, 0, ST, true>(su, id.q, out, out + FST, NQ, o0, o4);
             if constexpr (DIM == 3) {
-                if (id.d == 1) line_traces<real, N, NQ, NV, 1, ST>(su, id.q, out + 2 * FST, out + 3 * FST, NQ);
-                if (id.d == 2) line_traces<real, N, NQ, NV, 2, ST>(su, id.q, out + 4 * FST, out + 5 * FST, NQ);
+                if (id.d == 1)
+                    line_traces<real, N, NQ, NV, 1, ST, true>(su, id.q, out + 2 * FST, out + 3 * FST, NQ, o0, o4);
+                if (id.d == 2)
+                    line_traces<real, N, NQ, NV, 2, ST, true>(su, id.q, out + 4 * FST, out + 5 * FST, NQ, o0, o4);
             }
             if constexpr (NV == 1) {
                 if (P.pme_sol) {
@@ -641,7 +669,6 @@ k_line_trace(const real* __restrict__ U, real* __restrict__ Tu, LineGeo<real> ge
                 }
             }
         }
-        __syncthreads();
     }
 }
 
@@ -668,14 +695,16 @@ k_line_grad(const real* __restrict__ U, const real* __restrict__ Tu, real* __res
     for (int b = 0; grp < ngroups; grp += gridDim.x, b ^= 1) {
         real* buf = b ? buf1 : buf0;
         const int e0 = grp_first<LL::EB>(g, grp);
-        pipe_next<real, LL, PL, NV, true, false>(U, Tu, nullptr, g, grp, ngroups, b, buf0, buf1, nbr0, nbr1,
-                                                 geo.off0, geo.off4);
+        // the shared offset pass keeps this kernel at 64 registers for n = 5 (74 with the
+        // subtraction in its line loads, one block fewer per SM)
+        pipe_next<real, LL, PL, NV, true, false, true>(U, Tu, nullptr, g, grp, ngroups, b, grp == (int)blockIdx.x,
+                                                       buf0, buf1, nbr0, nbr1, geo.off0, geo.off4);
         const int e = e0 + id.eb;
         const bool live = id.ok && e < g.e_end;
         const real* su = buf + id.eb * NP;
         const real* trn = buf + PL::OFF_TR + id.eb * NF * LL::FST;
         real u[NV][N], dl[NV], dr[NV];
-        prologue_res<real, N, DIM, NV, ST>(geo, id, live, su, trn, vS, u, dl, dr);
+        prologue_res<real, N, DIM, NV, ST, false>(geo, id, live, su, trn, vS, u, dl, dr);
         if (live) {
             real* out = Tg + (size_t)e * NF * GST;
             if (id.d == 0) grad_faces_res<real, N, DIM, NV, 0>(geo, compact, u, dl, dr, vS, out, id.q);
@@ -684,8 +713,6 @@ k_line_grad(const real* __restrict__ U, const real* __restrict__ Tu, real* __res
                 if (id.d == 2) grad_faces_res<real, N, DIM, NV, 2>(geo, compact, u, dl, dr, vS, out, id.q);
             }
         }
-        pipe_tail<LL, PL, true>(g, grp, ngroups, b, nbr0, nbr1);
-        __syncthreads();
     }
 }
 
@@ -920,19 +947,41 @@ k_line_flux(const real* __restrict__ U, const real* __restrict__ Tu, const real*
     const LineId id = line_id<LL>(threadIdx.x);
     constexpr int WPE = FluxWork<LL>::value;                   // work values per element
     real* vS = work + id.eb * WPE;
+    // R of the group before: the three directions' contributions, added in the fixed order
+    // x, y, z (deterministic sums); run one iteration late, after the next group's first
+    // barrier, so that no barrier of its own is needed
+    auto write_r = [&](int pe0, int pnloc) {
+        for (int k = threadIdx.x; k < pnloc * NV * NP; k += blockDim.x) {
+            const int eb = k / (NV * NP);
+            const int rr = k - eb * NV * NP;
+            const int v = rr / NP, pt = rr - v * NP;
+            const real* rd = work + eb * WPE + LL::S_VR + v * NP + pt;
+            real acc = rd[0];
+            if constexpr (DIM == 3) {
+                acc = acc + rd[NV * NP];
+                acc = acc + rd[2 * NV * NP];
+            }
+            R[(size_t)v * g.nelem * NP + (size_t)(pe0 + eb) * NP + pt] = acc;
+        }
+    };
     pipe_start<real, LL, PL, NV, true, true>(U, Tu, Fh, g, grp, ngroups, buf0, nbr0, nbr1);
+    int pe0 = 0, pnloc = 0;                                     // the group whose R is pending
     for (int b = 0; grp < ngroups; grp += gridDim.x, b ^= 1) {
         real* buf = b ? buf1 : buf0;
         const int e0 = grp_first<EB>(g, grp), nloc = grp_count<EB>(g, grp);
-        pipe_next<real, LL, PL, NV, true, true>(U, Tu, Fh, g, grp, ngroups, b, buf0, buf1, nbr0, nbr1,
-                                                geo.off0, geo.off4);
+        pipe_next<real, LL, PL, NV, true, true>(U, Tu, Fh, g, grp, ngroups, b, grp == (int)blockIdx.x, buf0, buf1,
+                                                nbr0, nbr1);
+        write_r(pe0, pnloc);
+        // Navier-Stokes: the barrier in prologue_res orders these reads of the work area
+        // before this group's writes to it; scalars have no such barrier
+        if constexpr (NV != 5) __syncthreads();
         const int e = e0 + id.eb;
         const bool live = id.ok && e < g.e_end;
         const real* su = buf + id.eb * NP;
         const real* trn = buf + PL::OFF_TR + id.eb * NF * LL::FST;
         const real* fh = buf + PL::OFF_FH + id.eb * NF * LL::FST;
         real u[NV][N], dl[NV], dr[NV];
-        prologue_res<real, N, DIM, NV, ST>(geo, id, live, su, trn, vS, u, dl, dr);
+        prologue_res<real, N, DIM, NV, ST, true>(geo, id, live, su, trn, vS, u, dl, dr);
 
         real r[NV][N];
         if (live) {
@@ -942,13 +991,8 @@ k_line_flux(const real* __restrict__ U, const real* __restrict__ Tu, const real*
                 if (id.d == 1) line_flux<real, N, DIM, NV, 1, ST>(fo, P, u, dl, dr, vS, fh, id.q, r, t0);
                 if (id.d == 2) line_flux<real, N, DIM, NV, 2, ST>(fo, P, u, dl, dr, vS, fh, id.q, r, t0);
             }
-        }
-        // every line has read v^S: the work area now takes the three directions'
-        // contributions R_d[v][pt], which are added in the fixed order x, y, z
-        // (deterministic sums) while R is written
-        __syncthreads();
-        if (live) {
-            real* rd = vS + id.d * NV * NP;
+            // this line's contribution R_d[v][pt], in the work area's own region for it
+            real* rd = vS + LL::S_VR + id.d * NV * NP;
 #pragma unroll
             for (int v = 0; v < NV; ++v)
 #pragma unroll
@@ -960,21 +1004,11 @@ k_line_flux(const real* __restrict__ U, const real* __restrict__ Tu, const real*
                     rd[v * NP + pt] = r[v][i];
                 }
         }
-        pipe_tail<LL, PL, true>(g, grp, ngroups, b, nbr0, nbr1);
-        __syncthreads();
-        for (int k = threadIdx.x; k < nloc * NV * NP; k += blockDim.x) {
-            const int eb = k / (NV * NP);
-            const int rr = k - eb * NV * NP;
-            const int v = rr / NP, pt = rr - v * NP;
-            const real* rd = work + eb * WPE + v * NP + pt;
-            real acc = rd[0];
-            if constexpr (DIM == 3) {
-                acc = acc + rd[NV * NP];
-                acc = acc + rd[2 * NV * NP];
-            }
-            R[(size_t)v * g.nelem * NP + (size_t)(e0 + eb) * NP + pt] = acc;
-        }
+        pe0 = e0;
+        pnloc = nloc;
     }
+    __syncthreads();
+    write_r(pe0, pnloc);
 }
 
 }  // namespace sdk
