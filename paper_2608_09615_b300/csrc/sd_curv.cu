@@ -13,7 +13,7 @@
 // identity sum_d M_d S_dm = 0 holds and a uniform flow stays uniform.
 //
 // Kernels (one residual = 4 launches; the element kernels stage one element at a time in
-// shared memory):
+// shared memory; k_cflux is persistent and copies the next element in while it computes):
 //   k_ctrace  face traces of u                         Tc[e][face][v][q]
 //   k_cgrad   v^S = J^-1 sum_d M_d (u^{Fd,C} S_dm), one thread per (line, variable) with the
 //             line in registers, kept in VS[e][v][m][pt], and the own interface gradient of
@@ -253,14 +253,6 @@ struct CSizes {
     static constexpr int G_CR = G_W + 3 * NFP;
     static constexpr int G_C = G_CR + 18 * NQ;
     static constexpr int GRAD = G_C + NGEO;
-    // flux staging: operators, u, v^S, G (one family), R, J^-1, map
-    static constexpr int F_U = OPS_PAD;
-    static constexpr int F_VS = F_U + NV * NP;
-    static constexpr int F_G = F_VS + 3 * NV * NP;
-    static constexpr int F_R = F_G + NV * NFP;
-    static constexpr int F_JI = F_R + NV * NP;
-    static constexpr int F_C = F_JI + NP;
-    static constexpr int FLUX = F_C + NGEO;
 };
 
 // periodic face neighbour of element e across its face (d, side) (no run-time indexed array)
@@ -643,111 +635,176 @@ __global__ void __launch_bounds__(256) k_cface(const real* __restrict__ Tc, cons
     }
 }
 
-// One family of Sec. 2.3 steps 4-5: G = S_D . F at the interior flux points (the stored
-// interface fluxes at the ends), then R -= M_D G. Ends with __syncthreads.
-template <typename real, int N, int NV, int D>
-__device__ __forceinline__ void family_flux(real* sm, const real* __restrict__ Fh, const Mesh& g, int e,
-                                            const Phys<real>& P) {
+// Flux-kernel staging of one element: u as stored (the offsets are removed where u is
+// read), v^S, the interface fluxes of the six faces (face 2D holds block (D, e), the -D face;
+// face 2D + 1 block (D, +D neighbour)) and the map coefficients. Two copies when they fit in
+// shared memory (the next element's copies in flight while this one is computed), else one.
+// After the copies: G at the interior flux points of the three families [D][v][f - 1][q]
+// and J^-1 at the solution points.
+template <typename real, int N, int NV>
+struct CFluxPipe {
     using CS = CSizes<real, N, NV>;
-    constexpr int NP = CS::NP, NQ = CS::NQ, NFP = CS::NFP;
-    const SOps<real, N> op(sm);
-    const real* su = sm + CS::F_U;
-    const real* svs = sm + CS::F_VS;
-    const real* sc = sm + CS::F_C;
-    real* sG = sm + CS::F_G;
-    real* sR = sm + CS::F_R;
-    const int tid = threadIdx.x, T = blockDim.x;
-    for (int k = tid; k < NFP; k += T) {
-        const int f = k / NQ, q = k - f * NQ;
-        if (f == 0 || f == N) {
-            const int ee = f == 0 ? e : cneighbour(g, e, D, 1);
-#pragma unroll
-            for (int v = 0; v < NV; ++v) sG[v * NFP + k] = Fh[(((size_t)D * g.nelem + ee) * NV + v) * NQ + q];
-            continue;
-        }
-        const real* Lr = op.L + f * N;
-        real uF[NV], vF[3 * NV];
-#pragma unroll
-        for (int v = 0; v < NV; ++v) {
-            real acc = Lr[0] * su[v * NP + cpt<N, D>(0, q)];
-#pragma unroll
-            for (int i = 1; i < N; ++i) acc = fma(Lr[i], su[v * NP + cpt<N, D>(i, q)], acc);
-            uF[v] = acc;
-        }
-#pragma unroll
-        for (int vm = 0; vm < 3 * NV; ++vm) {
-            real acc = Lr[0] * svs[vm * NP + cpt<N, D>(0, q)];
-#pragma unroll
-            for (int i = 1; i < N; ++i) acc = fma(Lr[i], svs[vm * NP + cpt<N, D>(i, q)], acc);
-            vF[vm] = acc;
-        }
-        real r[3], S[3];
-        flux_point_coords<real, N, D>(op.xs, op.xf, f, q, r);
-        metric_row<real, D>(sc, r, S);
-        if constexpr (NV == 5) {
-            real Gc[5], Gv[5];
-            cv_convective(uF, S, P, Gc);
-            cv_viscous(uF, vF, S, P, Gv);
-#pragma unroll
-            for (int v = 0; v < 5; ++v) sG[v * NFP + k] = Gc[v] - Gv[v];
-        } else {
-            sG[k] = -sdk::scalar_coef(P, uF[0]) * (S[0] * vF[0] + S[1] * vF[1] + S[2] * vF[2]);
-        }
+    static constexpr int NP = CS::NP, NQ = CS::NQ;
+    static constexpr int NI = (N - 1) * NQ;               // interior flux points of one family
+    static constexpr int S_U = 0;
+    static constexpr int S_VS = S_U + NV * NP;
+    static constexpr int S_FH = S_VS + 3 * NV * NP;
+    static constexpr int S_C = S_FH + 6 * NV * NQ;
+    static constexpr int LOAD = (S_C + NGEO + 3) / 4 * 4;
+    static constexpr int NG_INT = 3 * NV * NI;
+    static constexpr size_t bytes_n(int nbuf) {
+        return sizeof(real) * ((size_t)CS::OPS_PAD + (size_t)nbuf * LOAD + NG_INT + NP);
     }
-    __syncthreads();
-    for (int k = tid; k < NV * NP; k += T) {
+    static constexpr int NBUF = bytes_n(2) <= 227 * 1024 ? 2 : 1;
+    static constexpr size_t BYTES = bytes_n(NBUF);
+};
+
+// issue (do not wait for) the copies of element e into buf
+template <typename real, int N, int NV>
+__device__ __forceinline__ void cflux_issue(const real* __restrict__ U, const real* __restrict__ VS,
+                                            const real* __restrict__ Fh, const real* __restrict__ geo,
+                                            const Mesh& g, int e, real* buf) {
+    using PL = CFluxPipe<real, N, NV>;
+    constexpr int NP = PL::NP, NQ = PL::NQ;
+    for (int k = threadIdx.x; k < NV * NP; k += blockDim.x) {
         const int v = k / NP, pt = k - v * NP;
-        int i, q;
-        line_of<N, D>(pt, i, q);
-        const real* Mr = op.M + i * (N + 1);
-        const real* gq = sG + v * NFP + q;
-        real acc = Mr[0] * gq[0];
-#pragma unroll
-        for (int f = 1; f <= N; ++f) acc = fma(Mr[f], gq[f * NQ], acc);
-        sR[k] -= acc;
+        sdk::cp_async(buf + PL::S_U + k, U + (size_t)v * g.nelem * NP + (size_t)e * NP + pt);
     }
-    __syncthreads();
+    const real* vs = VS + (size_t)e * 3 * NV * NP;
+    for (int k = threadIdx.x; k < 3 * NV * NP; k += blockDim.x) sdk::cp_async(buf + PL::S_VS + k, vs + k);
+    const int nb[3] = {cneighbour(g, e, 0, 1), cneighbour(g, e, 1, 1), cneighbour(g, e, 2, 1)};
+    for (int k = threadIdx.x; k < 6 * NV * NQ; k += blockDim.x) {
+        const int f = k / (NV * NQ), r = k - f * (NV * NQ);
+        const int D = f >> 1;
+        const int ee = (f & 1) ? (D == 0 ? nb[0] : (D == 1 ? nb[1] : nb[2])) : e;
+        sdk::cp_async(buf + PL::S_FH + k, Fh + ((size_t)D * g.nelem + ee) * NV * NQ + r);
+    }
+    for (int k = threadIdx.x; k < NGEO; k += blockDim.x) sdk::cp_async(buf + PL::S_C + k, geo + (size_t)e * NGEO + k);
 }
 
+// Sec. 2.3 step 4 at interior flux point f (1..N-1) of family D on line q: G = S_D . (F_c - F_v)
+// of the extrapolated state and full gradient; writes G[v] at out[v * NI]
+template <typename real, int N, int NV, int D>
+__device__ __forceinline__ void cflux_point(const SOps<real, N>& op, const real* buf, int f, int q,
+                                            const Phys<real>& P, real off0, real off4, real* out) {
+    using PL = CFluxPipe<real, N, NV>;
+    constexpr int NP = PL::NP, NI = PL::NI;
+    const real* su = buf + PL::S_U;
+    const real* svs = buf + PL::S_VS;
+    const real* Lr = op.L + f * N;
+    real uF[NV], vF[3 * NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+        real acc = Lr[0] * sdk::unoffset<real, NV>(su[v * NP + cpt<N, D>(0, q)], v, off0, off4);
+#pragma unroll
+        for (int i = 1; i < N; ++i)
+            acc = fma(Lr[i], sdk::unoffset<real, NV>(su[v * NP + cpt<N, D>(i, q)], v, off0, off4), acc);
+        uF[v] = acc;
+    }
+#pragma unroll
+    for (int vm = 0; vm < 3 * NV; ++vm) {
+        real acc = Lr[0] * svs[vm * NP + cpt<N, D>(0, q)];
+#pragma unroll
+        for (int i = 1; i < N; ++i) acc = fma(Lr[i], svs[vm * NP + cpt<N, D>(i, q)], acc);
+        vF[vm] = acc;
+    }
+    real r[3], S[3];
+    flux_point_coords<real, N, D>(op.xs, op.xf, f, q, r);
+    metric_row<real, D>(buf + PL::S_C, r, S);
+    if constexpr (NV == 5) {
+        real Gc[5], Gv[5];
+        cv_convective(uF, S, P, Gc);
+        cv_viscous(uF, vF, S, P, Gv);
+#pragma unroll
+        for (int v = 0; v < 5; ++v) out[v * NI] = Gc[v] - Gv[v];
+    } else {
+        out[0] = -sdk::scalar_coef(P, uF[0]) * (S[0] * vF[0] + S[1] * vF[1] + S[2] * vF[2]);
+    }
+}
+
+// Sec. 2.3 step 5 for family D at solution point pt of variable v: (M_D G)[pt], the
+// interface fluxes at f = 0 and f = N from the staged face blocks
+template <typename real, int N, int NV, int D>
+__device__ __forceinline__ real cflux_div(const SOps<real, N>& op, const real* buf, const real* sG, int v,
+                                          int pt) {
+    using PL = CFluxPipe<real, N, NV>;
+    constexpr int NQ = PL::NQ, NI = PL::NI;
+    int i, q;
+    line_of<N, D>(pt, i, q);
+    const real* Mr = op.M + i * (N + 1);
+    const real* gi = sG + (D * NV + v) * NI + q;
+    real acc = Mr[0] * buf[PL::S_FH + ((2 * D) * NV + v) * NQ + q];
+#pragma unroll
+    for (int f = 1; f < N; ++f) acc = fma(Mr[f], gi[(f - 1) * NQ], acc);
+    return fma(Mr[N], buf[PL::S_FH + ((2 * D + 1) * NV + v) * NQ + q], acc);
+}
+
+// Persistent: block b handles elements b, b + grid, ... Per element: J^-1 at the solution
+// points and G at the interior flux points of all three families (one pass, so the threads
+// are busy across families), one barrier, then R = -J^-1 sum_d M_d G with the families
+// subtracted in the order x, y, z. Two barriers per element (the copies' wait and the one
+// after G).
 template <typename real, int N, int NV>
 __global__ void __launch_bounds__(CURV_THREADS, sizeof(real) == 4 ? 3 : 1) k_cflux(const real* __restrict__ U, const real* __restrict__ VS,
                                                         const real* __restrict__ Fh, const real* __restrict__ geo,
                                                         real* __restrict__ R, const __grid_constant__ COps<real, N> o,
                                                         Mesh g, Phys<real> P, real off0, real off4) {
     using CS = CSizes<real, N, NV>;
-    constexpr int NP = CS::NP;
+    using PL = CFluxPipe<real, N, NV>;
+    constexpr int NP = CS::NP, NI = PL::NI;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     real* sm = reinterpret_cast<real*>(smem_raw);
-    real* su = sm + CS::F_U;
-    real* svs = sm + CS::F_VS;
-    real* sR = sm + CS::F_R;
-    real* sji = sm + CS::F_JI;
-    real* sc = sm + CS::F_C;
+    real* buf0 = sm + CS::OPS_PAD;
+    real* buf1 = buf0 + (PL::NBUF - 1) * PL::LOAD;
+    real* sG = buf0 + PL::NBUF * PL::LOAD;
+    real* sji = sG + PL::NG_INT;
     const int tid = threadIdx.x, T = blockDim.x;
+    int e = blockIdx.x;
+    if (e >= g.nelem) return;
     stage_ops(o, sm);
-    __syncthreads();
+    if constexpr (PL::NBUF == 2) {
+        cflux_issue<real, N, NV>(U, VS, Fh, geo, g, e, buf0);
+        sdk::cp_async_commit();
+    }
     const SOps<real, N> op(sm);
-    for (int e = blockIdx.x; e < g.nelem; e += gridDim.x) {
-        for (int k = tid; k < NGEO; k += T) sc[k] = geo[(size_t)e * NGEO + k];
-        for (int k = tid; k < NV * NP; k += T) {
-            const int v = k / NP, pt = k - v * NP;
-            su[k] = U[(size_t)v * g.nelem * NP + (size_t)e * NP + pt] - var_offset<real, NV>(v, off0, off4);
-            sR[k] = real(0);
+    for (int b = 0; e < g.nelem; e += gridDim.x, b ^= 1) {
+        real* buf = b ? buf1 : buf0;
+        if constexpr (PL::NBUF == 1) {
+            if (e != (int)blockIdx.x) __syncthreads();      // the previous element's reads are done
+            cflux_issue<real, N, NV>(U, VS, Fh, geo, g, e, buf);
+            sdk::cp_async_commit();
         }
-        for (int k = tid; k < 3 * NV * NP; k += T) svs[k] = VS[(size_t)e * 3 * NV * NP + k];
+        sdk::cp_async_wait_group<0>();
         __syncthreads();
+        if constexpr (PL::NBUF == 2) {
+            const int en = e + gridDim.x;
+            if (en < g.nelem) {
+                cflux_issue<real, N, NV>(U, VS, Fh, geo, g, en, b ? buf0 : buf1);
+                sdk::cp_async_commit();
+            }
+        }
+        const real* sc = buf + PL::S_C;
         for (int pt = tid; pt < NP; pt += T) {
             const real r[3] = {op.xs[pt % N], op.xs[(pt / N) % N], op.xs[pt / (N * N)]};
             sji[pt] = real(1) / jacobian(sc, r);
         }
-        family_flux<real, N, NV, 0>(sm, Fh, g, e, P);
-        family_flux<real, N, NV, 1>(sm, Fh, g, e, P);
-        family_flux<real, N, NV, 2>(sm, Fh, g, e, P);
-        for (int k = tid; k < NV * NP; k += T) {
-            const int v = k / NP, pt = k - v * NP;
-            R[(size_t)v * g.nelem * NP + (size_t)e * NP + pt] = sR[k] * sji[pt];
+        for (int k = tid; k < 3 * NI; k += T) {
+            const int D = k / NI, rr = k - D * NI;
+            const int f = 1 + rr / CS::NQ, q = rr - (f - 1) * CS::NQ;
+            real* out = sG + D * NV * NI + rr;
+            if (D == 0) cflux_point<real, N, NV, 0>(op, buf, f, q, P, off0, off4, out);
+            else if (D == 1) cflux_point<real, N, NV, 1>(op, buf, f, q, P, off0, off4, out);
+            else cflux_point<real, N, NV, 2>(op, buf, f, q, P, off0, off4, out);
         }
         __syncthreads();
+        for (int k = tid; k < NV * NP; k += T) {
+            const int v = k / NP, pt = k - v * NP;
+            real r = real(0);
+            r -= cflux_div<real, N, NV, 0>(op, buf, sG, v, pt);
+            r -= cflux_div<real, N, NV, 1>(op, buf, sG, v, pt);
+            r -= cflux_div<real, N, NV, 2>(op, buf, sG, v, pt);
+            R[(size_t)v * g.nelem * NP + (size_t)e * NP + pt] = r * sji[pt];
+        }
     }
 }
 
@@ -877,7 +934,7 @@ static sd_status residual_impl(sd_ctx* c, const real* U, real* R, int offset_in)
     const real* geo = static_cast<const real*>(c->cgeo);
     const real* ih = static_cast<const real*>(c->cih);
     const size_t sg = (size_t)CS::GRAD * sizeof(real);
-    const size_t sf = (size_t)CS::FLUX * sizeof(real);
+    const size_t sf = CFluxPipe<real, N, NV>::BYTES;
     if (!sdk::set_smem(k_cgrad<real, N, NV>, sg) || !sdk::set_smem(k_cflux<real, N, NV>, sf)) {
         sdi_set_error("curvilinear kernels need %zu / %zu bytes of shared memory", sg, sf);
         return SD_EUNSUPPORTED;
@@ -897,7 +954,8 @@ static sd_status residual_impl(sd_ctx* c, const real* U, real* R, int offset_in)
                                                                                      eta_n2);
     sdi_prof_end(c, SD_K_FACE);
     sdi_prof_begin(c, SD_K_FLUX);
-    k_cflux<real, N, NV><<<eb, th, sf, c->stream>>>(U, VS, Fh, geo, R, o, g, P, off0, off4);
+    const int fb = sdk::persistent_grid(k_cflux<real, N, NV>, th, sf, c->nelem, c->device);
+    k_cflux<real, N, NV><<<fb, th, sf, c->stream>>>(U, VS, Fh, geo, R, o, g, P, off0, off4);
     sdi_prof_end(c, SD_K_FLUX);
     const cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) {
