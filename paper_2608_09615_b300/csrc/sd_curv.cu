@@ -244,13 +244,14 @@ struct CSizes {
     static constexpr int OPS = (N + 1) * N + N * (N + 1) + N + (N + 1);   // L, M, xs, xf
     static constexpr int OPS_PAD = (OPS + 3) / 4 * 4;
     // gradient staging: operators, u, face corrections, J^-1, v^S, row D of S at the flux
-    // points of one family, the compact corrections of the face gradients, the map
+    // points of family D for the three families, the compact corrections of the face
+    // gradients, the map
     static constexpr int G_U = OPS_PAD;
     static constexpr int G_DL = G_U + NV * NP;
     static constexpr int G_JI = G_DL + 6 * NV * NQ;
     static constexpr int G_VS = G_JI + NP;
     static constexpr int G_W = G_VS + 3 * NV * NP;
-    static constexpr int G_CR = G_W + 3 * NFP;
+    static constexpr int G_CR = G_W + 9 * NFP;
     static constexpr int G_C = G_CR + 18 * NQ;
     static constexpr int GRAD = G_C + NGEO;
 };
@@ -360,31 +361,68 @@ __global__ void __launch_bounds__(128) k_ctrace(const real* __restrict__ U, real
     }
 }
 
-// One family of Sec. 2.3 step 3. Row D of S at the family's flux points goes to shared
-// memory; then one thread per (line q, variable v) forms u^{FD,C} at the line's n + 1 flux
-// points in registers, the flux vectors H_m = u^{FD,C} S_Dm, and adds M_D H_m to v^S_m at the
-// line's n solution points. Ends with __syncthreads.
+// row D of S at the n + 1 flux points of family D, point k = f * NQ + q: sf[m * NFP + k]
+template <typename real, int N, int D>
+__device__ __forceinline__ void metric_rows(const SOps<real, N>& op, const real* sc, int k, real* sf) {
+    constexpr int NQ = N * N, NFP = (N + 1) * NQ;
+    const int f = k / NQ, q = k - f * NQ;
+    real r[3], S[3];
+    flux_point_coords<real, N, D>(op.xs, op.xf, f, q, r);
+    metric_row<real, D>(sc, r, S);
+#pragma unroll
+    for (int m = 0; m < 3; ++m) sf[m * NFP + k] = S[m];
+}
+
+// compact scheme, face point q of face 2D + s: the one-sided gradient removes the derivative
+// of the opposite face's correction, extrapolated to this face (Eqs. aux:v:cmp:l-t):
+//   L_s (J^-1 M[:, opp]) delta_opp S_Dm(opp);  cr[m] = (L_s J^-1 M[:, opp]) S_Dm(opp)
 template <typename real, int N, int NV, int D>
-__device__ __forceinline__ void family_gradient(real* sm) {
+__device__ __forceinline__ void face_correction(const real* sm, int s, int q, real* cr) {
+    using CS = CSizes<real, N, NV>;
+    const SOps<real, N> op(sm);
+    const real* sji = sm + CS::G_JI;
+    const real* sc = sm + CS::G_C;
+    const int fo = s ? 0 : N;
+    const real* Lr = op.L + (s ? N * N : 0);
+    real kap = real(0);
+#pragma unroll
+    for (int i = 0; i < N; ++i) kap = fma(Lr[i] * sji[cpt<N, D>(i, q)], op.M[i * (N + 1) + fo], kap);
+    real r[3], S[3];
+    flux_point_coords<real, N, D>(op.xs, op.xf, fo, q, r);
+    metric_row<real, D>(sc, r, S);
+#pragma unroll
+    for (int m = 0; m < 3; ++m) cr[m] = kap * S[m];
+}
+
+// One family of Sec. 2.3 step 3: one thread per (line q, variable v) forms u^{FD,C} at the
+// line's n + 1 flux points in registers, the flux vectors H_m = u^{FD,C} S_Dm (rows of S
+// from shared memory), and adds M_D H_m to v^S_m at the line's n solution points. Family 0
+// starts the sums (0 + its term), family 2 applies J^-1 and, with VSe, writes v^S out. With
+// `compact`, family 0 also forms the compact face coefficients (G_CR). Ends with
+// __syncthreads.
+template <typename real, int N, int NV, int D>
+__device__ __forceinline__ void family_gradient(real* sm, real* __restrict__ VSe, int compact) {
     using CS = CSizes<real, N, NV>;
     constexpr int NP = CS::NP, NQ = CS::NQ, NFP = CS::NFP;
     const SOps<real, N> op(sm);
     const real* su = sm + CS::G_U;
     const real* sdl = sm + CS::G_DL;
-    const real* sc = sm + CS::G_C;
+    const real* sji = sm + CS::G_JI;
     real* svs = sm + CS::G_VS;
-    real* ssf = sm + CS::G_W;
+    const real* ssf = sm + CS::G_W + D * 3 * NFP;
+    real* scr = sm + CS::G_CR;
     const int tid = threadIdx.x, T = blockDim.x;
-    for (int k = tid; k < NFP; k += T) {
-        const int f = k / NQ, q = k - f * NQ;
-        real r[3], S[3];
-        flux_point_coords<real, N, D>(op.xs, op.xf, f, q, r);
-        metric_row<real, D>(sc, r, S);
-#pragma unroll
-        for (int m = 0; m < 3; ++m) ssf[m * NFP + k] = S[m];
-    }
-    __syncthreads();
-    for (int k = tid; k < NV * NQ; k += T) {
+    const int nitem = NV * NQ + (D == 0 && compact ? 6 * NQ : 0);
+    for (int k = tid; k < nitem; k += T) {
+        if (D == 0 && k >= NV * NQ) {
+            const int kf = k - NV * NQ, f = kf / NQ, q = kf - f * NQ;
+            switch (f >> 1) {
+                case 0: face_correction<real, N, NV, 0>(sm, f & 1, q, scr + 3 * kf); break;
+                case 1: face_correction<real, N, NV, 1>(sm, f & 1, q, scr + 3 * kf); break;
+                default: face_correction<real, N, NV, 2>(sm, f & 1, q, scr + 3 * kf); break;
+            }
+            continue;
+        }
         const int v = k / NQ, q = k - v * NQ;
         real ul[N];
 #pragma unroll
@@ -410,7 +448,16 @@ __device__ __forceinline__ void family_gradient(real* sm) {
                 real acc = op.M[i * (N + 1)] * h[0];
 #pragma unroll
                 for (int f = 1; f <= N; ++f) acc = fma(op.M[i * (N + 1) + f], h[f], acc);
-                vs[cpt<N, D>(i, q)] += acc;
+                const int pt = cpt<N, D>(i, q);
+                if (D == 0) {
+                    vs[pt] = real(0) + acc;
+                } else if (D == 1) {
+                    vs[pt] += acc;
+                } else {
+                    const real x = (vs[pt] + acc) * sji[pt];
+                    vs[pt] = x;
+                    if (VSe) VSe[(v * 3 + m) * NP + pt] = x;
+                }
             }
         }
     }
@@ -418,13 +465,14 @@ __device__ __forceinline__ void family_gradient(real* sm) {
 }
 
 // Stage element e and form v^S (Sec. 2.3 step 3): on return sm + G_VS holds v^S[v][m][pt]
-// (J^-1 applied), sm + G_DL the face corrections delta = (u_nb - u_own)/2 [face][v][q],
-// sm + G_JI the values of J^-1. The operators must already be staged. Ends with
+// (J^-1 applied; also written to VSe unless it is null), sm + G_DL the face corrections
+// delta = (u_nb - u_own)/2 [face][v][q], sm + G_JI the values of J^-1, and with `compact`
+// sm + G_CR the compact face coefficients. The operators must already be staged. Ends with
 // __syncthreads.
 template <typename real, int N, int NV>
 __device__ void element_gradient(const real* __restrict__ U, const real* __restrict__ Tc,
                                  const real* __restrict__ geo, const Mesh& g, int e, real off0, real off4,
-                                 real* sm) {
+                                 real* sm, real* __restrict__ VSe, int compact) {
     using CS = CSizes<real, N, NV>;
     constexpr int NP = CS::NP, NQ = CS::NQ;
     const SOps<real, N> op(sm);
@@ -432,7 +480,6 @@ __device__ void element_gradient(const real* __restrict__ U, const real* __restr
     real* su = sm + CS::G_U;
     real* sdl = sm + CS::G_DL;
     real* sji = sm + CS::G_JI;
-    real* svs = sm + CS::G_VS;
     real* sc = sm + CS::G_C;
     for (int k = tid; k < NGEO; k += T) sc[k] = geo[(size_t)e * NGEO + k];
     for (int k = tid; k < NV * NP; k += T) {
@@ -446,38 +493,23 @@ __device__ void element_gradient(const real* __restrict__ U, const real* __restr
         const real nb = Tc[((size_t)en * 6 + (f ^ 1)) * NV * NQ + rem];
         sdl[k] = real(0.5) * (nb - own);
     }
-    for (int k = tid; k < 3 * NV * NP; k += T) svs[k] = real(0);
     __syncthreads();
+    // J^-1 at the solution points and the S rows of all three families at their flux points
     for (int pt = tid; pt < NP; pt += T) {
         const real r[3] = {op.xs[pt % N], op.xs[(pt / N) % N], op.xs[pt / (N * N)]};
         sji[pt] = real(1) / jacobian(sc, r);
     }
-    family_gradient<real, N, NV, 0>(sm);
-    family_gradient<real, N, NV, 1>(sm);
-    family_gradient<real, N, NV, 2>(sm);
-    for (int k = tid; k < 3 * NV * NP; k += T) svs[k] *= sji[k % NP];
+    real* ssf = sm + CS::G_W;
+    for (int k = tid; k < 3 * CS::NFP; k += T) {
+        const int D = k / CS::NFP, kk = k - D * CS::NFP;
+        if (D == 0) metric_rows<real, N, 0>(op, sc, kk, ssf);
+        else if (D == 1) metric_rows<real, N, 1>(op, sc, kk, ssf + 3 * CS::NFP);
+        else metric_rows<real, N, 2>(op, sc, kk, ssf + 6 * CS::NFP);
+    }
     __syncthreads();
-}
-
-// compact scheme, face point q of face 2D + s: the one-sided gradient removes the derivative
-// of the opposite face's correction, extrapolated to this face (Eqs. aux:v:cmp:l-t):
-//   L_s (J^-1 M[:, opp]) delta_opp S_Dm(opp);  cr[m] = (L_s J^-1 M[:, opp]) S_Dm(opp)
-template <typename real, int N, int NV, int D>
-__device__ __forceinline__ void face_correction(const real* sm, int s, int q, real* cr) {
-    using CS = CSizes<real, N, NV>;
-    const SOps<real, N> op(sm);
-    const real* sji = sm + CS::G_JI;
-    const real* sc = sm + CS::G_C;
-    const int fo = s ? 0 : N;
-    const real* Lr = op.L + (s ? N * N : 0);
-    real kap = real(0);
-#pragma unroll
-    for (int i = 0; i < N; ++i) kap = fma(Lr[i] * sji[cpt<N, D>(i, q)], op.M[i * (N + 1) + fo], kap);
-    real r[3], S[3];
-    flux_point_coords<real, N, D>(op.xs, op.xf, fo, q, r);
-    metric_row<real, D>(sc, r, S);
-#pragma unroll
-    for (int m = 0; m < 3; ++m) cr[m] = kap * S[m];
+    family_gradient<real, N, NV, 0>(sm, VSe, compact);
+    family_gradient<real, N, NV, 1>(sm, VSe, compact);
+    family_gradient<real, N, NV, 2>(sm, VSe, compact);
 }
 
 template <typename real, int N, int NV>
@@ -494,22 +526,10 @@ __global__ void __launch_bounds__(CURV_THREADS) k_cgrad(const real* __restrict__
     __syncthreads();
     const SOps<real, N> op(sm);
     for (int e = blockIdx.x; e < g.nelem; e += gridDim.x) {
-        element_gradient<real, N, NV>(U, Tc, geo, g, e, off0, off4, sm);
+        element_gradient<real, N, NV>(U, Tc, geo, g, e, off0, off4, sm, VS + (size_t)e * 3 * NV * NP, compact);
         const real* svs = sm + CS::G_VS;
         const real* sdl = sm + CS::G_DL;
-        real* scr = sm + CS::G_CR;
-        for (int k = tid; k < 3 * NV * NP; k += T) VS[(size_t)e * 3 * NV * NP + k] = svs[k];
-        if (compact) {
-            for (int k = tid; k < 6 * NQ; k += T) {
-                const int f = k / NQ, q = k - f * NQ;
-                switch (f >> 1) {
-                    case 0: face_correction<real, N, NV, 0>(sm, f & 1, q, scr + 3 * k); break;
-                    case 1: face_correction<real, N, NV, 1>(sm, f & 1, q, scr + 3 * k); break;
-                    default: face_correction<real, N, NV, 2>(sm, f & 1, q, scr + 3 * k); break;
-                }
-            }
-            __syncthreads();
-        }
+        const real* scr = sm + CS::G_CR;
         // both faces of each line of direction d: the -d face (2d) and the +d face (2d+1)
         for (int k = tid; k < 3 * 3 * NV * NQ; k += T) {
             const int d = k / (3 * NV * NQ), rem = k - d * 3 * NV * NQ;
@@ -829,7 +849,7 @@ __global__ void __launch_bounds__(CURV_THREADS) k_cdiag(const double* __restrict
     for (int le = 0; le < epb; ++le) {
         const int e = blockIdx.x * epb + le;
         if (e >= g.nelem) break;
-        element_gradient<double, N, NV>(U, Tc, geo, g, e, 0.0, 0.0, sm);
+        element_gradient<double, N, NV>(U, Tc, geo, g, e, 0.0, 0.0, sm, nullptr, 0);
         const double* su = sm + CS::G_U;
         const double* vS = sm + CS::G_VS;
         const double* sji = sm + CS::G_JI;
