@@ -644,19 +644,23 @@ k_line_trace(const real* __restrict__ U, real* __restrict__ Tu, LineGeo<real> ge
     for (int b = 0; grp < ngroups; grp += gridDim.x, b ^= 1) {
         real* buf = b ? buf1 : buf0;
         const int e0 = grp_first<LL::EB>(g, grp);
-        pipe_next<real, LL, PL, NV, false, false>(U, nullptr, nullptr, g, grp, ngroups, b, grp == (int)blockIdx.x,
-                                                  buf0, buf1, nullptr, nullptr);
+        // FP32: offsets removed per line (no shared pass, no second barrier); FP64: in one
+        // shared pass (B300's FP64 rate makes the three-fold per-line subtraction the dearer)
+        constexpr bool LOFF = sizeof(real) == 4;
+        pipe_next<real, LL, PL, NV, false, false, !LOFF>(U, nullptr, nullptr, g, grp, ngroups, b,
+                                                         grp == (int)blockIdx.x, buf0, buf1, nullptr, nullptr,
+                                                         geo.off0, geo.off4);
         const int e = e0 + id.eb;
         if (id.ok && e < g.e_end) {
             const real* su = buf + id.eb * NP;
             real* out = Tu + (size_t)e * NF * FST + id.q;
             const real o0 = geo.off0, o4 = geo.off4;
-            if (id.d == 0) line_traces<real, N, NQ, NV, 0, ST, true>(su, id.q, out, out + FST, NQ, o0, o4);
+            if (id.d == 0) line_traces<real, N, NQ, NV, 0, ST, LOFF>(su, id.q, out, out + FST, NQ, o0, o4);
             if constexpr (DIM == 3) {
                 if (id.d == 1)
-                    line_traces<real, N, NQ, NV, 1, ST, true>(su, id.q, out + 2 * FST, out + 3 * FST, NQ, o0, o4);
+                    line_traces<real, N, NQ, NV, 1, ST, LOFF>(su, id.q, out + 2 * FST, out + 3 * FST, NQ, o0, o4);
                 if (id.d == 2)
-                    line_traces<real, N, NQ, NV, 2, ST, true>(su, id.q, out + 4 * FST, out + 5 * FST, NQ, o0, o4);
+                    line_traces<real, N, NQ, NV, 2, ST, LOFF>(su, id.q, out + 4 * FST, out + 5 * FST, NQ, o0, o4);
             }
             if constexpr (NV == 1) {
                 if (P.pme_sol) {
@@ -969,8 +973,10 @@ k_line_flux(const real* __restrict__ U, const real* __restrict__ Tu, const real*
     for (int b = 0; grp < ngroups; grp += gridDim.x, b ^= 1) {
         real* buf = b ? buf1 : buf0;
         const int e0 = grp_first<EB>(g, grp), nloc = grp_count<EB>(g, grp);
-        pipe_next<real, LL, PL, NV, true, true>(U, Tu, Fh, g, grp, ngroups, b, grp == (int)blockIdx.x, buf0, buf1,
-                                                nbr0, nbr1);
+        // offsets: per line in FP32, one shared pass in FP64 (as in k_line_trace)
+        constexpr bool LOFF = sizeof(real) == 4;
+        pipe_next<real, LL, PL, NV, true, true, !LOFF>(U, Tu, Fh, g, grp, ngroups, b, grp == (int)blockIdx.x, buf0,
+                                                       buf1, nbr0, nbr1, geo.off0, geo.off4);
         write_r(pe0, pnloc);
         // Navier-Stokes: the barrier in prologue_res orders these reads of the work area
         // before this group's writes to it; scalars have no such barrier
@@ -981,7 +987,7 @@ k_line_flux(const real* __restrict__ U, const real* __restrict__ Tu, const real*
         const real* trn = buf + PL::OFF_TR + id.eb * NF * LL::FST;
         const real* fh = buf + PL::OFF_FH + id.eb * NF * LL::FST;
         real u[NV][N], dl[NV], dr[NV];
-        prologue_res<real, N, DIM, NV, ST, true>(geo, id, live, su, trn, vS, u, dl, dr);
+        prologue_res<real, N, DIM, NV, ST, LOFF>(geo, id, live, su, trn, vS, u, dl, dr);
 
         real r[NV][N];
         if (live) {
