@@ -359,7 +359,7 @@ sd_status sdi_setup(const sd_mesh* mesh, int p, sd_scheme scheme, const sd_physi
         const int n = c->n, NV = c->nvar, DIM = c->dim;
         const size_t per = (size_t)(NV * np + 2 * 2 * DIM * NV * nq + NV * DIM * np + 2 * DIM * c->ngrad * nq);
         const int nqv = nq, epw = nqv <= 32 ? 32 / nqv : 1, wpd = nqv <= 32 ? 1 : (nqv + 31) / 32;
-        const int unit = DIM * wpd * 32, upb = unit >= 192 ? 1 : 192 / unit;
+        const int unit = DIM * wpd * 32, upb = unit >= SD_LINE_THREADS ? 1 : SD_LINE_THREADS / unit;
         const size_t blk = per * (size_t)(upb * epw) * c->esize;
         const size_t diag = (size_t)(NV * np + 2 * 2 * DIM * NV * nq + NV * DIM * np) * sizeof(double);
         if (blk > 227 * 1024 || diag > 227 * 1024) {

@@ -31,15 +31,17 @@
 
 #include "sd_kernels.cuh"
 
-// Threads per block the line kernels aim for (whole element groups of DIM warps): 192 for
-// the trace and gradient kernels, 96 for k_line_flux, with a register cap of 136 for the
-// latter (further limited to what one block of the layout can use). For the FP32
-// Navier-Stokes n = 5 case on B300 this gives 5 resident flux blocks per SM without
-// spills; it measured fastest among the layouts tried (on an earlier form of the kernel,
-// per launch at 48^3: 192 threads / 143 registers 1.24 ms, 96 / 136 1.11 ms, 192 / 112
-// 1.25 ms).
+// Threads per block the line kernels aim for (whole element groups of DIM warps): 96 for
+// the trace and gradient kernels (one element group per block at n = 5, so a barrier waits
+// for three warps; at 48^3 the gradient kernel measured 0.284 ms against 0.300 with 192
+// threads and 0.307 with 384, the trace kernel 0.133 against 0.136), and 96 for
+// k_line_flux with a register cap of 136 (further limited to what one block of the layout
+// can use). For the FP32 Navier-Stokes n = 5 case on B300 this gives 5 resident flux
+// blocks per SM without spills; it measured fastest among the layouts tried (on an
+// earlier form of the kernel, per launch at 48^3: 192 threads / 143 registers 1.24 ms,
+// 96 / 136 1.11 ms, 192 / 112 1.25 ms).
 #ifndef SD_LINE_THREADS
-#define SD_LINE_THREADS 192
+#define SD_LINE_THREADS 96
 #endif
 #ifndef SD_FLUX_THREADS
 #define SD_FLUX_THREADS 96

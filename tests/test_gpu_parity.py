@@ -385,6 +385,26 @@ def test_full_size_fp64_sampled(full_tgv, scheme):
 
 
 @pytest.mark.parametrize("scheme", ["compact", "br1"])
+def test_fp64_p8_many_groups_per_block_sampled(scheme):
+    # FP64 Navier-Stokes at p = 8 is the one configuration whose flux kernel holds a single
+    # staging copy (two do not fit in shared memory) and issues each group's copies behind
+    # a barrier. 336 elements are more than the resident blocks, so each block runs that
+    # path for several groups. Sampled elements against the oracle on their periodic 5^3
+    # blocks (an element's residual depends only on elements within distance 2).
+    ne, p, h = (8, 7, 6), 8, 0.35
+    prm, phys = ns_phys(Re=300.0)
+    U = inputs.random_state(ne, p, seed=8)
+    Rg = gpu_residual(U, 3, ne, (0.0,) * 3, tuple(h * n for n in ne), p, scheme, phys, "f64")
+    scale = np.abs(Rg).reshape(5, -1).max(axis=1)
+    for c in [(0, 0, 0), (7, 6, 5), (3, 2, 4)]:
+        idx = [np.arange(ci - 2, ci + 3) % n for ci, n in zip(c, ne)]
+        B = np.ascontiguousarray(U[:, idx[2]][:, :, idx[1]][:, :, :, idx[0]])
+        Rb = ext_residual(B, 3, (5, 5, 5), (0.0,) * 3, (5 * h,) * 3, p, scheme, NavierStokes(prm))
+        err = np.abs(Rg[:, c[2], c[1], c[0]] - Rb[:, 2, 2, 2]).reshape(5, -1).max(axis=1) / scale
+        assert err.max() <= 1e-12, (c, err)
+
+
+@pytest.mark.parametrize("scheme", ["compact", "br1"])
 def test_full_size_fp32_sampled_within_rounding_floor(full_tgv, scheme, capsys):
     # The FP32 residual of the benchmark grid (48^3 p4, the launch configuration the bench
     # times) at the sampled elements, against the oracle on their 5^3 blocks (FP32-rounded
