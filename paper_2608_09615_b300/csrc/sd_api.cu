@@ -981,7 +981,7 @@ static sd_status diag_impl_r(sd_ctx* c, const double* U, real* Tu) {
     const Mesh g = make_mesh(c);
     double off0 = 0.0, off4 = 0.0;
     if (sizeof(real) == 4) stage_offsets(c, off0, off4);
-    const long long ntr = (long long)g.nelem * FP::NF * NV * FP::NQ;
+    const long long ntr = (long long)g.nelem * DIM * NV * FP::NQ;       // one thread per line
     sdi_prof_begin(c, SD_K_OTHER);
     k_trace_staged<real, N, DIM, NV><<<trace_blocks(ntr), 256, 0, c->stream>>>(U, Tu, ops, g, off0, off4);
     sdi_prof_end(c, SD_K_OTHER);
@@ -991,10 +991,14 @@ static sd_status diag_impl_r(sd_ctx* c, const double* U, real* Tu) {
     if (!set_smem(k_diag<real, N, DIM, NV>, smem)) return smem_fail(smem);
     const int nb = (g.nelem + epb - 1) / epb;
     if (nb != c->diag_blocks) return SD_EINVAL;
+    // persistent: as many blocks as are resident at once (fixed for a device, so the order
+    // of the sums, and the result, are the same on every call)
+    const int nbp = persistent_grid(k_diag<real, N, DIM, NV>, threads, smem, nb, c->device);
     sdi_prof_begin(c, SD_K_OTHER);
-    k_diag<real, N, DIM, NV><<<nb, threads, smem, c->stream>>>(U, Tu, ops, g, c->dW, c->J, c->partial, off0, off4);
+    k_diag<real, N, DIM, NV><<<nbp, threads, smem, c->stream>>>(U, Tu, ops, g, c->dW, c->J, c->partial, off0,
+                                                                off4);
     sdi_prof_end(c, SD_K_OTHER);
-    return diag_reduce(c, nb);
+    return diag_reduce(c, nbp);
 }
 
 template <int N, int DIM, int NV>

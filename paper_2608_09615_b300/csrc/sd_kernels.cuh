@@ -394,27 +394,6 @@ __device__ __forceinline__ void stage_element(const real* __restrict__ U,
 }
 
 // ------------------------------------------------------------------ kernels
-template <typename real, int N, int DIM, int NV>
-__global__ void k_trace(const real* __restrict__ U, real* __restrict__ Tu, Ops<real, N> ops,
-                        Mesh g) {
-    constexpr int NP = ipow(N, DIM), NQ = ipow(N, DIM - 1), NF = 2 * DIM;
-    const long long total = (long long)g.nelem * NF * NV * NQ;
-    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-         idx += (long long)gridDim.x * blockDim.x) {
-        const int q = (int)(idx % NQ);
-        long long r = idx / NQ;
-        const int v = (int)(r % NV);
-        r /= NV;
-        if (NV == 5 && v == 4) continue;      // the diagnostics use no trace of rho E
-        const int f = (int)(r % NF);
-        const int e = (int)(r / NF);
-        const int d = f >> 1, s = f & 1;
-        Tu[idx] = line_dot<real, N>(ops.L + (s ? N * N : 0),
-                                    U + (size_t)v * g.nelem * NP + (size_t)e * NP + pt_of<N>(d, 0, q),
-                                    npow<N>(d));
-    }
-}
-
 // ------------------------------------------------------------------ diagnostics (FP64)
 // Sums, per block, of the Gauss-weighted integrands of Sec. 4.4 plus conserved totals;
 // k_diag_final adds the block partials in a fixed order (deterministic).
@@ -425,12 +404,13 @@ constexpr int DIAG_L1 = 256;   // blocks of the first level of the partials' red
 // is; FP32 contexts stage (U - offsets) rounded to FP32 (the offsets of rho and rho E, as the
 // residual kernels do) and evaluate the kinetic-energy and enstrophy integrands in FP32. Every
 // sum is FP64 and the conserved totals are taken from the FP64 state itself.
-// The face traces for the diagnostics: k_trace over the staged values.
+// The face traces for the diagnostics: one thread per line (element, direction d, variable,
+// line q) extrapolates the staged values to both faces of direction d.
 template <typename real, int N, int DIM, int NV>
 __global__ void k_trace_staged(const double* __restrict__ U, real* __restrict__ Tu, Ops<real, N> ops, Mesh g,
                                double off0, double off4) {
     constexpr int NP = ipow(N, DIM), NQ = ipow(N, DIM - 1), NF = 2 * DIM;
-    const long long total = (long long)g.nelem * NF * NV * NQ;
+    const long long total = (long long)g.nelem * DIM * NV * NQ;
     for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
          idx += (long long)gridDim.x * blockDim.x) {
         const int q = (int)(idx % NQ);
@@ -438,15 +418,16 @@ __global__ void k_trace_staged(const double* __restrict__ U, real* __restrict__ 
         const int v = (int)(r % NV);
         r /= NV;
         if (NV == 5 && v == 4) continue;      // the diagnostics use no trace of rho E
-        const int f = (int)(r % NF);
-        const int e = (int)(r / NF);
-        const int d = f >> 1, s = f & 1;
+        const int d = (int)(r % DIM);
+        const int e = (int)(r / DIM);
         const double off = (NV == 5 && v == 0) ? off0 : 0.0;
         const double* src = U + (size_t)v * g.nelem * NP + (size_t)e * NP + pt_of<N>(d, 0, q);
         real x[N];
 #pragma unroll
         for (int i = 0; i < N; ++i) x[i] = (real)(src[i * npow<N>(d)] - off);
-        Tu[idx] = line_dot<real, N>(ops.L + (s ? N * N : 0), x, 1);
+        real* out = Tu + (((size_t)e * NF + 2 * d) * NV + v) * NQ + q;
+        out[0] = line_dot<real, N>(ops.L, x, 1);
+        out[NV * NQ] = line_dot<real, N>(ops.L + N * N, x, 1);
     }
 }
 
@@ -460,69 +441,74 @@ __global__ void __launch_bounds__(Footprint<N, DIM, NV>::MAXT) k_diag(const doub
     real* sm = reinterpret_cast<real*>(smem_raw);
     const int le = threadIdx.x / TPE, tid = threadIdx.x - le * TPE;
     const int epb = blockDim.x / TPE;
-    const int e = blockIdx.x * epb + le;
-    const bool valid = e < g.nelem;
     real* base = sm + le * FP::grad;
     real* su = base;
     real* tro = su + FP::U;
     real* trn = tro + FP::TR;
     real* vS = trn + FP::TR;
-    // stage_element reads the state in `real`: give it the staged values through shared memory
-    if (valid) {
-        for (int k = tid; k < NV * NP; k += TPE) {
-            const int v = k / NP, pt = k - v * NP;
-            const double off = (NV == 5 && v == 0) ? off0 : ((NV == 5 && v == 4) ? off4 : 0.0);
-            su[k] = (real)(U[(size_t)v * g.nelem * NP + (size_t)e * NP + pt] - off);
-        }
-    }
-    stage_element<real, N, DIM, NV>(nullptr, Tu, ops, g, e, valid, tid, su, tro, trn, vS);
+    // persistent: block b handles the element groups b, b + grid, ...; each thread adds its
+    // points' integrands over all of them in FP64, and the block's threads are summed once
     double acc[NDIAG];
 #pragma unroll
     for (int k = 0; k < NDIAG; ++k) acc[k] = 0.0;
-    if (valid && owned(g, e)) {
-        for (int pt = tid; pt < NP; pt += TPE) {
-            double w = J;
-            int r = pt;
-#pragma unroll
-            for (int d = 0; d < DIM; ++d) {
-                w *= wq[r % N];
-                r /= N;
-            }
-            const double* Ue = U + (size_t)e * NP + pt;
-            bool bad = false;
-#pragma unroll
-            for (int v = 0; v < NV; ++v) bad |= !isfinite(Ue[(size_t)v * g.nelem * NP]);
-            acc[9] += bad ? 1.0 : 0.0;
-            if constexpr (NV == 5) {
-                const real rho = su[pt] + (real)off0;
-                const real vel[3] = {su[NP + pt] / rho, su[2 * NP + pt] / rho, su[3 * NP + pt] / rho};
-                const real q2 = vel[0] * vel[0] + vel[1] * vel[1] + vel[2] * vel[2];
-                real du[3][3] = {};   // du[k][i] = d u_i / d x_k, off-diagonal (the vorticity)
-#pragma unroll
-                for (int k = 0; k < 3; ++k)
-#pragma unroll
-                    for (int i = 0; i < 3; ++i)
-                        if (i != k)
-                            du[k][i] = (vS[((1 + i) * DIM + k) * NP + pt] - vel[i] * vS[(0 * DIM + k) * NP + pt]) / rho;
-                const real o0 = du[1][2] - du[2][1], o1 = du[2][0] - du[0][2], o2 = du[0][1] - du[1][0];
-                acc[0] += w * (0.5 * (double)q2);
-                acc[1] += w * (0.5 * (double)rho * (double)q2);
-                acc[2] += w * (double)(o0 * o0 + o1 * o1 + o2 * o2);
-                const size_t S = (size_t)g.nelem * NP;
-                acc[3] += w * Ue[0];
-                acc[4] += w * Ue[S];
-                acc[5] += w * Ue[2 * S];
-                acc[6] += w * Ue[3 * S];
-                acc[7] += w * Ue[4 * S];
-            } else {
-                const double u = Ue[0];
-                acc[3] += w * u;
-                acc[8] += w * u * u;
+    const int ngroups = (g.nelem + epb - 1) / epb;
+    for (int grp = blockIdx.x; grp < ngroups; grp += gridDim.x) {
+        const int e = grp * epb + le;
+        const bool valid = e < g.nelem;
+        // stage_element reads the state in `real`: give it the staged values through shared memory
+        if (valid) {
+            for (int k = tid; k < NV * NP; k += TPE) {
+                const int v = k / NP, pt = k - v * NP;
+                const double off = (NV == 5 && v == 0) ? off0 : ((NV == 5 && v == 4) ? off4 : 0.0);
+                su[k] = (real)(U[(size_t)v * g.nelem * NP + (size_t)e * NP + pt] - off);
             }
         }
+        stage_element<real, N, DIM, NV>(nullptr, Tu, ops, g, e, valid, tid, su, tro, trn, vS);
+        if (valid && owned(g, e)) {
+            for (int pt = tid; pt < NP; pt += TPE) {
+                double w = J;
+                int r = pt;
+#pragma unroll
+                for (int d = 0; d < DIM; ++d) {
+                    w *= wq[r % N];
+                    r /= N;
+                }
+                const double* Ue = U + (size_t)e * NP + pt;
+                bool bad = false;
+#pragma unroll
+                for (int v = 0; v < NV; ++v) bad |= !isfinite(Ue[(size_t)v * g.nelem * NP]);
+                acc[9] += bad ? 1.0 : 0.0;
+                if constexpr (NV == 5) {
+                    const real rho = su[pt] + (real)off0;
+                    const real vel[3] = {su[NP + pt] / rho, su[2 * NP + pt] / rho, su[3 * NP + pt] / rho};
+                    const real q2 = vel[0] * vel[0] + vel[1] * vel[1] + vel[2] * vel[2];
+                    real du[3][3] = {};   // du[k][i] = d u_i / d x_k, off-diagonal (the vorticity)
+#pragma unroll
+                    for (int k = 0; k < 3; ++k)
+#pragma unroll
+                        for (int i = 0; i < 3; ++i)
+                            if (i != k)
+                                du[k][i] = (vS[((1 + i) * DIM + k) * NP + pt] - vel[i] * vS[(0 * DIM + k) * NP + pt]) / rho;
+                    const real o0 = du[1][2] - du[2][1], o1 = du[2][0] - du[0][2], o2 = du[0][1] - du[1][0];
+                    acc[0] += w * (0.5 * (double)q2);
+                    acc[1] += w * (0.5 * (double)rho * (double)q2);
+                    acc[2] += w * (double)(o0 * o0 + o1 * o1 + o2 * o2);
+                    const size_t S = (size_t)g.nelem * NP;
+                    acc[3] += w * Ue[0];
+                    acc[4] += w * Ue[S];
+                    acc[5] += w * Ue[2 * S];
+                    acc[6] += w * Ue[3 * S];
+                    acc[7] += w * Ue[4 * S];
+                } else {
+                    const double u = Ue[0];
+                    acc[3] += w * u;
+                    acc[8] += w * u * u;
+                }
+            }
+        }
+        __syncthreads();   // the group's staged values are read before the next group
     }
     // deterministic block reduction (fixed tree over the threads), in FP64
-    __syncthreads();
     double* red = reinterpret_cast<double*>(smem_raw);   // NDIAG * blockDim doubles fit (host sizes it)
     for (int k = 0; k < NDIAG; ++k) red[k * blockDim.x + threadIdx.x] = acc[k];
     __syncthreads();
