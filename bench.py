@@ -109,11 +109,9 @@ def curv_flops_per_element(n, nv=5):
 
 # DRAM traffic of one k_line_flux launch at 48^3 p=4 (FP32, compact), from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum of that kernel), valid only while the kernel
-# sources hash to the value recorded with it. (Recorded against the sources in which the
-# FP64 trace and flux kernels went back to the shared offset pass: that change leaves the
-# FP32 kernel's code as captured, same time and bitwise the same output.)
-FLUX_TRAFFIC = {"ne": 48, "bytes": 804297728 + 251342080,
-                "sources_sha256": "725621f28b4a73023a9dd94a6a31ee89e00ea2842d5d624977c4ebe05b17228c"}
+# sources hash to the value recorded with it.
+FLUX_TRAFFIC = {"ne": 48, "bytes": 804369408 + 251354368,
+                "sources_sha256": "2d87acc2ca415aa08809c8ae76fd8d37b5560b5ac071bb1c00c78d1b364ac64c"}
 FLUX_SOURCES = ("paper_2608_09615_b300/csrc/sd_line.cuh", "paper_2608_09615_b300/csrc/sd_kernels.cuh")
 
 
