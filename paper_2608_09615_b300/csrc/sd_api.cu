@@ -565,12 +565,26 @@ static sd_status residual_phase_any(sd_ctx* c, int phase, int e0, int e1) {
 // and its z neighbours'); R goes back slab by slab on a third stream as each slab's flux
 // phase ends. Phases of one slab: trace <- copy in; grad <- trace of slabs k-1, k, k+1;
 // face <- grad of k, k+1 (+z faces); flux <- face of k-1, k. The slabs are copied in the
-// order S-1, 0, 1, ..., S-2, so slab 0's periodic neighbour arrives first.
+// order S-1, 0, 1, ..., S-2, so slab 0's periodic neighbour arrives first. The flux phases
+// of slabs S-3, S-2, S-1 and 0 need the last slab copied in (through grad of S-2 and the
+// periodic wrap), so their results are the ones still to go back when the copies in end:
+// with at least two layers per slab to spare those four slabs are one element layer
+// thick and the others share the rest.
 static sd_status residual_host_slabs(sd_ctx* c, const void* U_host, void* R_host) {
     const int S = std::min(c->ne[2], SDI_MAX_SLABS);
     const int layer = c->ne[0] * c->ne[1];
     const size_t ppe = c->npts / c->nelem;
-    auto first = [&](int k) { return (int)((long long)k * c->ne[2] / S) * layer; };
+    int lay[SDI_MAX_SLABS + 1];                  // first element layer of each slab
+    const bool thin = S >= 8 && c->ne[2] >= 2 * S;
+    lay[0] = 0;
+    for (int k = 0; k < S; ++k) {
+        int n;
+        if (!thin) n = (int)((long long)(k + 1) * c->ne[2] / S - (long long)k * c->ne[2] / S);
+        else if (k == 0 || k >= S - 3) n = 1;
+        else n = (c->ne[2] - 4) * k / (S - 4) - (c->ne[2] - 4) * (k - 1) / (S - 4);
+        lay[k + 1] = lay[k] + n;
+    }
+    auto first = [&](int k) { return lay[k] * layer; };
     auto copy_slab = [&](int k, bool in) -> cudaError_t {
         const size_t e0 = first(k), e1 = first(k + 1);
         const size_t bytes = (e1 - e0) * ppe * c->esize;

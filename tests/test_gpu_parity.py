@@ -169,6 +169,8 @@ def test_fp32_error_tgv_within_rounding_floor(scheme, capsys):
 @pytest.mark.parametrize("ne,precision,scheme", [((4, 3, 2), "f32", "compact"),     # one pass
                                                    ((4, 3, 7), "f32", "compact"),     # 7 z-slabs
                                                    ((3, 5, 20), "f32", "br1"),        # 16 uneven slabs
+                                                   ((2, 3, 40), "f32", "compact"),    # thin wrap slabs
+                                                   ((2, 2, 33), "f64", "br1"),        # thin wrap slabs
                                                    ((3, 2, 9), "f64", "compact")])
 def test_host_path_equals_device_path(ne, precision, scheme):
     # sd_residual_host: whole-grid copies for thin grids, the slab pipeline (copies on
