@@ -263,14 +263,14 @@ def test_rk_step_equals_stage_by_stage(case):
 
 
 @pytest.mark.parametrize("precision", ["f64", "f32"])
-@pytest.mark.parametrize("p", [2, 4])
-def test_diagnostics_parity_ns(p, precision):
+@pytest.mark.parametrize("p,ne", [(2, (4, 3, 5)), (4, (4, 3, 5)), (2, (24, 20, 18))])
+def test_diagnostics_parity_ns(p, ne, precision):
     # FP64 contexts: every integrand in FP64 (1e-12). FP32 contexts form the kinetic-energy
     # and enstrophy integrands in FP32 from the offset state and sum them in FP64 (FP32
     # rounding of each point's value: 1e-6 relative on the sums); the conserved totals come
-    # from the FP64 state in both (1e-12).
+    # from the FP64 state in both (1e-12). The 24 x 20 x 18 grid has more element groups
+    # than the persistent diagnostics kernel has blocks, so each block sums several.
     prm, phys = ns_phys()
-    ne = (4, 3, 5)
     lo, hi = (0.0,) * 3, (TWO_PI,) * 3
     g = Grid(3, ne, lo, hi, p)
     U = inputs.tgv_3d(ne, p, perturb_seed=4)
