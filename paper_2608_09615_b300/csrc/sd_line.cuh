@@ -25,8 +25,9 @@
 // are deterministic. The interface flux is computed once per interface point, so it is
 // single-valued and conservation holds to round-off.
 //
-// Navier-Stokes states are staged with the reference offsets removed from rho and rho E
-// (see ns_convective); Tu holds traces of the offset state.
+// Navier-Stokes states enter the arithmetic with the reference offsets removed from rho and
+// rho E (see ns_convective): as each lane loads its line, or in one pass over the staged
+// values (see pipe_next); Tu holds traces of the offset state.
 #pragma once
 
 #include "sd_kernels.cuh"
