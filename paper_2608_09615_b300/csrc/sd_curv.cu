@@ -339,10 +339,23 @@ __global__ void __launch_bounds__(128) k_ctrace(const real* __restrict__ U, real
         sL[tid] = o.L[tid];
         sL[N + tid] = o.L[N * N + tid];
     }
+    constexpr int LPT = (NV * NP + 127) / 128;   // loads per thread (blockDim.x = 128)
     for (int e = blockIdx.x; e < g.nelem; e += gridDim.x) {
-        for (int k = tid; k < NV * NP; k += T) {
-            const int v = k / NP, pt = k - v * NP;
-            su[k] = U[(size_t)v * g.nelem * NP + (size_t)e * NP + pt] - var_offset<real, NV>(v, off0, off4);
+        // all of a thread's loads are issued before the first store (one load in flight per
+        // thread left the kernel at a third of the copy bandwidth)
+        real x[LPT];
+#pragma unroll
+        for (int j = 0; j < LPT; ++j) {
+            const int k = tid + j * T;
+            if (k < NV * NP) {
+                const int v = k / NP, pt = k - v * NP;
+                x[j] = U[(size_t)v * g.nelem * NP + (size_t)e * NP + pt];
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < LPT; ++j) {
+            const int k = tid + j * T;
+            if (k < NV * NP) su[k] = x[j] - var_offset<real, NV>(k / NP, off0, off4);
         }
         __syncthreads();
         for (int k = tid; k < 3 * NV * NQ; k += T) {
@@ -482,16 +495,41 @@ __device__ void element_gradient(const real* __restrict__ U, const real* __restr
     real* sji = sm + CS::G_JI;
     real* sc = sm + CS::G_C;
     for (int k = tid; k < NGEO; k += T) sc[k] = geo[(size_t)e * NGEO + k];
-    for (int k = tid; k < NV * NP; k += T) {
-        const int v = k / NP, pt = k - v * NP;
-        su[k] = U[(size_t)v * g.nelem * NP + (size_t)e * NP + pt] - var_offset<real, NV>(v, off0, off4);
+    // W values per thread per pass, all loads issued before the stores (more loads in flight)
+    constexpr int W = 4;
+    for (int k0 = tid; k0 < NV * NP; k0 += W * T) {
+        real x[W];
+#pragma unroll
+        for (int j = 0; j < W; ++j) {
+            const int k = k0 + j * T;
+            if (k < NV * NP) {
+                const int v = k / NP, pt = k - v * NP;
+                x[j] = U[(size_t)v * g.nelem * NP + (size_t)e * NP + pt];
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < W; ++j) {
+            const int k = k0 + j * T;
+            if (k < NV * NP) su[k] = x[j] - var_offset<real, NV>(k / NP, off0, off4);
+        }
     }
-    for (int k = tid; k < 6 * NV * NQ; k += T) {
-        const int f = k / (NV * NQ), rem = k - f * NV * NQ;
-        const int en = cneighbour(g, e, f >> 1, f & 1);
-        const real own = Tc[((size_t)e * 6 + f) * NV * NQ + rem];
-        const real nb = Tc[((size_t)en * 6 + (f ^ 1)) * NV * NQ + rem];
-        sdl[k] = real(0.5) * (nb - own);
+    for (int k0 = tid; k0 < 6 * NV * NQ; k0 += W * T) {
+        real own[W], nb[W];
+#pragma unroll
+        for (int j = 0; j < W; ++j) {
+            const int k = k0 + j * T;
+            if (k < 6 * NV * NQ) {
+                const int f = k / (NV * NQ), rem = k - f * NV * NQ;
+                const int en = cneighbour(g, e, f >> 1, f & 1);
+                own[j] = Tc[((size_t)e * 6 + f) * NV * NQ + rem];
+                nb[j] = Tc[((size_t)en * 6 + (f ^ 1)) * NV * NQ + rem];
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < W; ++j) {
+            const int k = k0 + j * T;
+            if (k < 6 * NV * NQ) sdl[k] = real(0.5) * (nb[j] - own[j]);
+        }
     }
     __syncthreads();
     // J^-1 at the solution points and the S rows of all three families at their flux points
