@@ -702,16 +702,17 @@ k_line_grad(const real* __restrict__ U, const real* __restrict__ Tu, real* __res
     for (int b = 0; grp < ngroups; grp += gridDim.x, b ^= 1) {
         real* buf = b ? buf1 : buf0;
         const int e0 = grp_first<LL::EB>(g, grp);
-        // the shared offset pass keeps this kernel at 64 registers for n = 5 (74 with the
-        // subtraction in its line loads, one block fewer per SM)
-        pipe_next<real, LL, PL, NV, true, false, true>(U, Tu, nullptr, g, grp, ngroups, b, grp == (int)blockIdx.x,
-                                                       buf0, buf1, nbr0, nbr1, geo.off0, geo.off4);
+        // offsets: per line in FP32 (one barrier fewer per group: 0.280 against 0.285 ms
+        // per launch at 48^3), one shared pass in FP64
+        constexpr bool LOFF = sizeof(real) == 4;
+        pipe_next<real, LL, PL, NV, true, false, !LOFF>(U, Tu, nullptr, g, grp, ngroups, b, grp == (int)blockIdx.x,
+                                                        buf0, buf1, nbr0, nbr1, geo.off0, geo.off4);
         const int e = e0 + id.eb;
         const bool live = id.ok && e < g.e_end;
         const real* su = buf + id.eb * NP;
         const real* trn = buf + PL::OFF_TR + id.eb * NF * LL::FST;
         real u[NV][N], dl[NV], dr[NV];
-        prologue_res<real, N, DIM, NV, ST, false>(geo, id, live, su, trn, vS, u, dl, dr);
+        prologue_res<real, N, DIM, NV, ST, LOFF>(geo, id, live, su, trn, vS, u, dl, dr);
         if (live) {
             real* out = Tg + (size_t)e * NF * GST;
             if (id.d == 0) grad_faces_res<real, N, DIM, NV, 0>(geo, compact, u, dl, dr, vS, out, id.q);
