@@ -309,17 +309,21 @@ template <typename real, class LL>
 using TracePipe = Pipe<LL, false, false, real, 0>;
 template <typename real, class LL>
 using GradPipe = Pipe<LL, true, false, real, LL::S_VR>;
-template <class LL>
+template <typename real, class LL>
 struct FluxWork;
 template <typename real, class LL>
-using FluxPipe = Pipe<LL, true, true, real, FluxWork<LL>::value>;
+using FluxPipe = Pipe<LL, true, true, real, FluxWork<real, LL>::value>;
 
-// work values per element of the flux kernel: the kept v^S, then the per-direction
-// contributions R_d in a region of their own (so that writing them needs no barrier after
-// the flux loops have read v^S)
-template <class LL>
+// work values per element of the flux kernel: the kept v^S and the per-direction
+// contributions R_d. FP32: R_d in a region of its own (SEP), so that writing it needs no
+// barrier after the flux loops have read v^S and R can be written one iteration late. FP64:
+// R_d over v^S behind one more barrier, which keeps the block's shared memory, and the
+// resident blocks per SM, of the single-region layout.
+template <typename real, class LL>
 struct FluxWork {
-    static constexpr int value = LL::S_VR + LL::S_RD;
+    static constexpr bool SEP = sizeof(real) == 4;
+    static constexpr int RD0 = SEP ? LL::S_VR : 0;           // offset of R_d in the work area
+    static constexpr int value = SEP ? LL::S_VR + LL::S_RD : (LL::S_VR > LL::S_RD ? LL::S_VR : LL::S_RD);
 };
 
 template <class LL>
@@ -953,17 +957,19 @@ k_line_flux(const real* __restrict__ U, const real* __restrict__ Tu, const real*
     int grp = blockIdx.x;
     if (grp >= ngroups) return;
     const LineId id = line_id<LL>(threadIdx.x);
-    constexpr int WPE = FluxWork<LL>::value;                   // work values per element
+    using FW = FluxWork<real, LL>;
+    constexpr int WPE = FW::value;                             // work values per element
     real* vS = work + id.eb * WPE;
-    // R of the group before: the three directions' contributions, added in the fixed order
-    // x, y, z (deterministic sums); run one iteration late, after the next group's first
-    // barrier, so that no barrier of its own is needed
+    // R of a group: the three directions' contributions, added in the fixed order x, y, z
+    // (deterministic sums). FP32 (FW::SEP): run one iteration late, after the next group's
+    // first barrier, so that no barrier of its own is needed; FP64: at the end of the group
+    // behind a barrier.
     auto write_r = [&](int pe0, int pnloc) {
         for (int k = threadIdx.x; k < pnloc * NV * NP; k += blockDim.x) {
             const int eb = k / (NV * NP);
             const int rr = k - eb * NV * NP;
             const int v = rr / NP, pt = rr - v * NP;
-            const real* rd = work + eb * WPE + LL::S_VR + v * NP + pt;
+            const real* rd = work + eb * WPE + FW::RD0 + v * NP + pt;
             real acc = rd[0];
             if constexpr (DIM == 3) {
                 acc = acc + rd[NV * NP];
@@ -981,10 +987,12 @@ k_line_flux(const real* __restrict__ U, const real* __restrict__ Tu, const real*
         constexpr bool LOFF = sizeof(real) == 4;
         pipe_next<real, LL, PL, NV, true, true, !LOFF>(U, Tu, Fh, g, grp, ngroups, b, grp == (int)blockIdx.x, buf0,
                                                        buf1, nbr0, nbr1, geo.off0, geo.off4);
-        write_r(pe0, pnloc);
-        // Navier-Stokes: the barrier in prologue_res orders these reads of the work area
-        // before this group's writes to it; scalars have no such barrier
-        if constexpr (NV != 5) __syncthreads();
+        if constexpr (FW::SEP) {
+            write_r(pe0, pnloc);
+            // Navier-Stokes: the barrier in prologue_res orders these reads of the work area
+            // before this group's writes to it; scalars have no such barrier
+            if constexpr (NV != 5) __syncthreads();
+        }
         const int e = e0 + id.eb;
         const bool live = id.ok && e < g.e_end;
         const real* su = buf + id.eb * NP;
@@ -1001,8 +1009,11 @@ k_line_flux(const real* __restrict__ U, const real* __restrict__ Tu, const real*
                 if (id.d == 1) line_flux<real, N, DIM, NV, 1, ST>(fo, P, u, dl, dr, vS, fh, id.q, r, t0);
                 if (id.d == 2) line_flux<real, N, DIM, NV, 2, ST>(fo, P, u, dl, dr, vS, fh, id.q, r, t0);
             }
-            // this line's contribution R_d[v][pt], in the work area's own region for it
-            real* rd = vS + LL::S_VR + id.d * NV * NP;
+        }
+        if constexpr (!FW::SEP) __syncthreads();                // every line has read v^S
+        if (live) {
+            // this line's contribution R_d[v][pt] in the work area
+            real* rd = vS + FW::RD0 + id.d * NV * NP;
 #pragma unroll
             for (int v = 0; v < NV; ++v)
 #pragma unroll
@@ -1014,11 +1025,18 @@ k_line_flux(const real* __restrict__ U, const real* __restrict__ Tu, const real*
                     rd[v * NP + pt] = r[v][i];
                 }
         }
-        pe0 = e0;
-        pnloc = nloc;
+        if constexpr (FW::SEP) {
+            pe0 = e0;
+            pnloc = nloc;
+        } else {
+            __syncthreads();
+            write_r(e0, nloc);
+        }
     }
-    __syncthreads();
-    write_r(pe0, pnloc);
+    if constexpr (FW::SEP) {
+        __syncthreads();
+        write_r(pe0, pnloc);
+    }
 }
 
 }  // namespace sdk

@@ -388,11 +388,11 @@ def test_full_size_fp64_sampled(full_tgv, scheme):
 
 @pytest.mark.parametrize("scheme", ["compact", "br1"])
 def test_fp64_p8_many_groups_per_block_sampled(scheme):
-    # FP64 Navier-Stokes at p = 8 is the one configuration whose flux kernel holds a single
-    # staging copy (two do not fit in shared memory) and issues each group's copies behind
-    # a barrier. 336 elements are more than the resident blocks, so each block runs that
-    # path for several groups. Sampled elements against the oracle on their periodic 5^3
-    # blocks (an element's residual depends only on elements within distance 2).
+    # FP64 Navier-Stokes at p = 8 has the largest shared-memory staging of the line kernels
+    # (one or two resident blocks per SM). 336 elements are more than the resident blocks,
+    # so each block runs its staging pipeline over several groups. Sampled elements against
+    # the oracle on their periodic 5^3 blocks (an element's residual depends only on
+    # elements within distance 2).
     ne, p, h = (8, 7, 6), 8, 0.35
     prm, phys = ns_phys(Re=300.0)
     U = inputs.random_state(ne, p, seed=8)
