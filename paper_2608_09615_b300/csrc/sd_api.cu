@@ -683,7 +683,7 @@ __global__ void k_ssp_inc(int k, double* __restrict__ U, float* __restrict__ A, 
             if (i >= n) continue;
             kk[w] = K[i];
             if (k < 4) x[w] = X[i];
-            if (k == 1 || k == 2 || k == 3) b[w] = B[i];
+            if (k == 2 || k == 3) b[w] = B[i];          // stage 1 only writes B
             if (k == 1 || k >= 3) a[w] = A[i];
             if (k == 4) { cc[w] = C[i]; u[w] = U[i]; }
         }

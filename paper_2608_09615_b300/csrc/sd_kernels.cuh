@@ -538,13 +538,13 @@ __device__ __forceinline__ double stage_offset(const StageOff& o, size_t i) {
     return i < o.npts ? o.off0 : (i >= 4 * o.npts ? o.off4 : 0.0);
 }
 
-// y = x - offsets, rounded to real. Each thread handles 4 values spaced one grid apart per
+// y = x - offsets, rounded to real. Each thread handles 8 values spaced one grid apart per
 // iteration and issues their loads together (one load in flight per thread reached only
 // half the copy bandwidth). FP64 subtraction only in the first and last variable (FP64
 // issue is scarce; the test is on the index, not on the offset's value).
 template <typename real>
 __global__ void k_to_real(const double* __restrict__ x, real* __restrict__ y, size_t n, StageOff o) {
-    constexpr int W = 4;
+    constexpr int W = 8;
     const size_t stride = (size_t)gridDim.x * blockDim.x;
     for (size_t base = (size_t)blockIdx.x * blockDim.x + threadIdx.x; base < n; base += W * stride) {
         double v[W];
