@@ -405,7 +405,7 @@ extern "C" sd_status sd_init(const sd_mesh* mesh, int p, sd_scheme scheme, const
     alloc(&c->K, S * c->esize);
     alloc(&c->rA, S * c->esize);
     alloc(&c->rB, S * c->esize);
-    alloc(&c->rC, S * c->esize);
+    if (prec == SD_F64) alloc(&c->rC, S * c->esize);           // FP32 increments need two registers
     if (prec == SD_F32) alloc(&c->rX, S * c->esize);
     alloc((void**)&c->dW, SD_MAX_N * sizeof(double));
     alloc((void**)&c->cl_tmode, (SD_MAX_N * SD_MAX_N + SD_MAX_N) * sizeof(double));
@@ -669,29 +669,29 @@ namespace sdk {
 constexpr int EWB = 4;
 
 __global__ void k_ssp_inc(int k, double* __restrict__ U, float* __restrict__ A, float* __restrict__ B,
-                          float* __restrict__ C, const float* __restrict__ K, const float* __restrict__ X,
-                          float* __restrict__ S, SSPInc c, size_t n) {
+                          const float* __restrict__ K, const float* __restrict__ X, float* __restrict__ S,
+                          SSPInc c, size_t n) {
     const size_t stride = (size_t)gridDim.x * blockDim.x;
     for (size_t base = (size_t)blockIdx.x * blockDim.x + threadIdx.x; base < n; base += EWB * stride) {
-        float kk[EWB], x[EWB], a[EWB], b[EWB], cc[EWB];
+        float kk[EWB], x[EWB], a[EWB], b[EWB];
         double u[EWB];
 #pragma unroll
         for (int w = 0; w < EWB; ++w) {
             const size_t i = base + w * stride;
-            a[w] = b[w] = cc[w] = x[w] = 0.0f;
+            a[w] = b[w] = x[w] = 0.0f;
             u[w] = 0.0;
             if (i >= n) continue;
             kk[w] = K[i];
             if (k < 4) x[w] = X[i];
             if (k == 2 || k == 3) b[w] = B[i];          // stage 1 only writes B
             if (k == 1 || k >= 3) a[w] = A[i];
-            if (k == 4) { cc[w] = C[i]; u[w] = U[i]; }
+            if (k == 4) u[w] = U[i];
         }
 #pragma unroll
         for (int w = 0; w < EWB; ++w) {
             const size_t i = base + w * stride;
             if (i >= n) continue;
-            const float s = ssp_inc_point(c, k, kk[w], x[w], a[w], b[w], cc[w], u[w]);
+            const float s = ssp_inc_point(c, k, kk[w], x[w], a[w], b[w], u[w]);
             if (k == 4) {
                 U[i] = u[w];
                 continue;
@@ -699,7 +699,6 @@ __global__ void k_ssp_inc(int k, double* __restrict__ U, float* __restrict__ A, 
             S[i] = s;
             if (k == 1) B[i] = b[w];
             else A[i] = a[w];
-            if (k == 3) C[i] = cc[w];
         }
     }
 }
@@ -844,7 +843,7 @@ static sd_status rk_stage(sd_ctx* c, double* U, int k, double dt, sd_rk rk) {
         float* S = (float*)c->S;
         float* K = (float*)c->K;
         float* X = (float*)c->rX;
-        float *rA = (float*)c->rA, *rB = (float*)c->rB, *rC = (float*)c->rC;
+        float *rA = (float*)c->rA, *rB = (float*)c->rB;
         const int gi = grid_for((n + sdk::EWB - 1) / sdk::EWB);
         const sdk::SSPCoef& a = kSSP;
         const sdk::SSPInc ci = {(float)(a.a10 * dt), (float)a.a21, (float)(a.b21 * dt), (float)a.a32,
@@ -854,7 +853,7 @@ static sd_status rk_stage(sd_ctx* c, double* U, int k, double dt, sd_rk rk) {
         if (rk == SD_RK4)
             sdk::k_rk4_inc<<<gi, 256, 0, st>>>(k, U, rA, K, X, S, c4, n);
         else if (rk == SD_SSPRK54)
-            sdk::k_ssp_inc<<<gi, 256, 0, st>>>(k, U, rA, rB, rC, K, X, S, ci, n);
+            sdk::k_ssp_inc<<<gi, 256, 0, st>>>(k, U, rA, rB, K, X, S, ci, n);
         else
             sdk::k_lsrk_inc<<<gi, 256, 0, st>>>(k, k == 4, U, rA, rB, K, X, S, (float)kLSA[k], (float)dt,
                                                 (float)kLSB[k], n);

@@ -655,11 +655,13 @@ struct SSPInc {
 };
 
 // One point of stage k of that form: kk is the stage residual, x the step-start value minus
-// the offsets, a / b / cc the increment registers A, B, C at the point (updated in place).
-// Stages 0-3 return the next stage input x + d; stage 4 updates the FP64 state u. Every
-// operation is explicitly rounded (no contraction into other operations).
+// the offsets, a / b the increment registers A, B at the point (updated in place). Stages
+// 0-3 return the next stage input x + d; stage 4 updates the FP64 state u. Stage 3 leaves in
+// A not its increment d_4 but a54 d_4 + (a52 d_2 + a53 d_3 + b53 K_3), the only form in
+// which stage 4 uses d_4, so no third register is needed. Every operation is explicitly
+// rounded (no contraction into other operations).
 __device__ __forceinline__ float ssp_inc_point(const SSPInc& c, int k, float kk, float x, float& a, float& b,
-                                               float& cc, double& u) {
+                                               double& u) {
     if (k == 0) {
         const float d = __fmul_rn(c.b10, kk);
         a = d;
@@ -676,19 +678,19 @@ __device__ __forceinline__ float ssp_inc_point(const SSPInc& c, int k, float kk,
         return __fadd_rn(x, d);
     }
     if (k == 3) {
-        cc = __fmaf_rn(c.a52, b, __fmaf_rn(c.a53, a, __fmul_rn(c.b53, kk)));
+        const float cc = __fmaf_rn(c.a52, b, __fmaf_rn(c.a53, a, __fmul_rn(c.b53, kk)));
         const float d = __fmaf_rn(c.a43, a, __fmul_rn(c.b43, kk));
-        a = d;
+        a = __fmaf_rn(c.a54, d, cc);
         return __fadd_rn(x, d);
     }
-    u = __dadd_rn(u, (double)__fmaf_rn(c.a54, a, __fmaf_rn(c.b54, kk, cc)));
+    u = __dadd_rn(u, (double)__fmaf_rn(c.b54, kk, a));
     return 0.0f;
 }
 
 
 __global__ void k_ssp_inc(int k, double* __restrict__ U, float* __restrict__ A, float* __restrict__ B,
-                          float* __restrict__ C, const float* __restrict__ K, const float* __restrict__ X,
-                          float* __restrict__ S, SSPInc c, size_t n);
+                          const float* __restrict__ K, const float* __restrict__ X, float* __restrict__ S,
+                          SSPInc c, size_t n);
 
 struct RK4Inc {
     float h2, h1, h6, h3;     // dt/2, dt, dt/6, dt/3
