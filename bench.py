@@ -110,8 +110,8 @@ def curv_flops_per_element(n, nv=5):
 # DRAM traffic of one k_line_flux launch at 48^3 p=4 (FP32, compact), from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum of that kernel), valid only while the kernel
 # code (flux_sources_digest) hashes to the value recorded with it.
-FLUX_TRAFFIC = {"ne": 48, "bytes": 804389632 + 251666432,
-                "sources_sha256": "099cf3ce4efcfd2f807d0984471f75626c28ee59ea2cf18dbb15385007d24a63"}
+FLUX_TRAFFIC = {"ne": 48, "bytes": 804013056 + 251464448,
+                "sources_sha256": "1ac4637e33b082623f91bdf5580b78002788772fbd56f851c4ca29f93184a6f7"}
 FLUX_SOURCES = ("paper_2608_09615_b300/csrc/sd_line.cuh", "paper_2608_09615_b300/csrc/sd_kernels.cuh")
 
 
