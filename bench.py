@@ -115,19 +115,26 @@ FLUX_TRAFFIC = {"ne": 48, "bytes": 804013056 + 251464448,
 FLUX_SOURCES = ("paper_2608_09615_b300/csrc/sd_line.cuh", "paper_2608_09615_b300/csrc/sd_kernels.cuh")
 
 
-def flux_sources_digest():
-    """sha256 of the flux kernel's sources with comments and blank lines removed (a change
-    of the code changes it; a change of a comment does not)."""
+def code_digest(texts):
+    """sha256 of C/CUDA source texts with comments, trailing blanks and blank lines removed
+    (a change of the code changes it; a change of a comment does not)."""
     import hashlib
     import re
     h = hashlib.sha256()
-    for f in FLUX_SOURCES:
-        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), f)) as fh:
-            text = fh.read()
+    for text in texts:
         text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
         lines = [re.sub(r"//.*$", "", ln).rstrip() for ln in text.splitlines()]
         h.update("\n".join(ln for ln in lines if ln.strip()).encode())
     return h.hexdigest()
+
+
+def flux_sources_digest():
+    """code_digest of the flux kernel's sources."""
+    texts = []
+    for f in FLUX_SOURCES:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), f)) as fh:
+            texts.append(fh.read())
+    return code_digest(texts)
 
 
 def flux_traffic(ne):
