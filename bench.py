@@ -283,6 +283,13 @@ def oracle_step_sample(sample_ne, steps, warmup):
     return STAGES * npts / dt, dt, npts
 
 
+def workload_name(ne, scheme):
+    """The workload both arms report: the Taylor-Green SSPRK(5,4) step of the benchmark."""
+    npts = int(np.prod(ne)) * (P + 1) ** 3
+    return ("TGV Re=1600 Ma=0.1 Pr=0.71, %dx%dx%d hex p=4 (%d DOF, 5 vars), %s scheme, Roe + Sutherland, "
+            "FP32 residual, SSPRK(5,4) with FP64 state, dt=%g" % (tuple(ne) + (npts, scheme, DT)))
+
+
 def run_reference(args, world):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -295,8 +302,9 @@ def run_reference(args, world):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": "TGV Re=1600 Ma=0.1, 48^3 hex p=4 (240^3 DOF), compact, SSPRK(5,4)",
-                   "sample": "%dx%dx%d elements p=4 (%d DOF) per step" % (sample + (npts,)),
+        "config": {"workload": workload_name((args.ne,) * 3, args.scheme),
+                   "sample": "the FP64 oracle (numpy, host cores) on %dx%dx%d elements p=4 (%d DOF) of "
+                             "that workload per step" % (sample + (npts,)),
                    "parallelism": "none (host cores)"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": "one SSPRK(5,4) step of the FP64 numpy oracle on a %dx%dx%d p=4 "
@@ -619,9 +627,7 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": "TGV Re=1600 Ma=0.1 Pr=0.71, %dx%dx%d hex p=4 (%d DOF, 5 vars), "
-                                   "%s scheme, Roe + Sutherland, FP32 residual, SSPRK(5,4) with FP64 state, "
-                                   "dt=%g" % (ne + (npts, args.scheme, DT)),
+            "config": {"workload": workload_name(ne, args.scheme),
                        "step": "one SSPRK(5,4) step = 5 residuals + 5 stage updates (FP32 stage "
                                "increments, FP64 state update once per step); diagnostics (FP64 sums) "
                                "once per timed window",
